@@ -1,0 +1,539 @@
+/*
+ * FP64 CPU oracle for the BOA Constrictor hot path -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow statement of what the compressor computes, in double
+ * precision, one stream and one step at a time:
+ *   - the next-byte predictor Q (paper Alg. 1 "Forward Pass"; App. A,
+ *     Eqs. for the selective SSM and its discretisation),
+ *   - softmax and the strictly positive integer histogram / CDF
+ *     (section "Range coding", paragraph "Probabilities and integer CDF"),
+ *   - the w = 32 bit range encoder and decoder (paragraphs "Encoder",
+ *     "Decoder"), with the first byte of each stream stored raw
+ *     (section "Coders & Parallelisation").
+ * Only the test suite, the package smoke check and the benchmark's CPU
+ * baseline leg may call this file.  It shares no code with the CUDA library.
+ *
+ * Readings taken where the paper is silent or loose (same ids as the design
+ * notes):
+ *   R1  block:  u = x + Mamba(LN_a(x));  x = LN_b(u + FFN(u)) when an FFN is
+ *       present (FFN = Linear(d,F) -> exact-erf GELU -> Linear(F,d)), else
+ *       x = LN_b(u).  Logits = head(x) after the last block.
+ *   R2  Mamba-1 internals: in_proj (no bias) -> [xi, z]; depthwise causal
+ *       conv (bias) + SiLU -> u; x_proj (no bias) -> [delta(r), B(N), C(N)];
+ *       Delta = softplus(dt_proj(delta) + b); A = -exp(A_log);
+ *       y = scan + D*u; out = out_proj(y * SiLU(z)).
+ *   R3  B-bar = Delta*B (Euler), A-bar = exp(Delta*A).
+ *   R7  conv window and h start at zero for every stream.
+ *   R8  softplus(v) = v for v > 20 else log1p(exp(v)); SiLU(v) = v/(1+e^-v);
+ *       GELU(v) = v/2 (1 + erf(v/sqrt 2)); LayerNorm eps 1e-5, biased variance.
+ *   R9  f_a = 1 + floor(p_a (M - 256)); the signed remainder M - sum f goes
+ *       to the most probable symbol (lowest index on ties); M = 2^16.
+ *   R10 L in [0, 2^32), R in [1, 2^32] held in 64 bits, L + R <= 2^32; no
+ *       modulo on R (the literal "mod 2^w" would zero R = 2^24).
+ *   R11 emit the top byte of L while floor(L/2^24) == floor((L+R-1)/2^24).
+ *   R12 straddle: if the top bytes differ and R < 2^16, R <- 2^16 - (L mod 2^16)
+ *       (carry-less underflow rule), which forces two emissions.
+ *   R13 flush = the 4 bytes of L, most significant first; the decoder loads
+ *       its code value from the first 4 coded bytes.
+ *   R15 byte 0 of a stream is stored raw; the model consumes bytes 0..n-2
+ *       and predicts bytes 1..n-1.
+ *
+ * Parity status: the coder, quantiser, conv, scan, LayerNorm and softmax are
+ * pinned by closed forms, brute force and special cases in the tests; the
+ * composed forward is pinned by special cases (zero out_proj, memoryless
+ * scan) and a materialised whole-sequence re-derivation at tiny sizes.
+ */
+#include "boa_oracle.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_M 65536u           /* M = 2^B, B = 16 */
+#define ORC_TOP (1ull << 24)   /* 2^(w-8), w = 32 */
+#define ORC_BOT (1ull << 16)
+#define ORC_MASK 0xFFFFFFFFull
+
+typedef struct {
+    double *ln_a_w, *ln_a_b, *in_w, *conv_w, *conv_b, *x_w, *dt_w, *dt_b, *A_log, *D, *out_w;
+    double *A;  /* A = -exp(A_log), App. A state matrix (diagonal per channel) */
+    double *ffn_w1, *ffn_b1, *ffn_w2, *ffn_b2, *ln_b_w, *ln_b_b;
+} orc_layer;
+
+struct orc_model {
+    int vocab, d, nl, N, K, expand, E, r, ffn_mult, F;
+    double *embed, *head_w, *head_b;
+    orc_layer* layers;
+    double* blob;
+};
+
+struct orc_state {
+    double* conv;   /* [nl][E][K-1]: the last K-1 conv inputs, oldest first */
+    double* h;      /* [nl][E][N] */
+};
+
+/* ------------------------------------------------------------ weight file */
+
+static double* take(double** cur, size_t n) { double* p = *cur; *cur += n; return p; }
+
+int orc_model_load(const char* path, orc_model** out) {
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return 1;
+    char magic[4];
+    uint32_t hdr[9];
+    if (fread(magic, 1, 4, fp) != 4 || memcmp(magic, "BOAW", 4) != 0 ||
+        fread(hdr, 4, 9, fp) != 9 || hdr[0] != 1) { fclose(fp); return 2; }
+    orc_model* m = (orc_model*)calloc(1, sizeof(orc_model));
+    m->vocab = (int)hdr[1]; m->d = (int)hdr[2]; m->nl = (int)hdr[3]; m->N = (int)hdr[4];
+    m->K = (int)hdr[5]; m->expand = (int)hdr[6]; m->r = (int)hdr[7]; m->ffn_mult = (int)hdr[8];
+    m->E = m->expand * m->d;
+    m->F = m->ffn_mult * m->d;
+    if (m->vocab != 256 || m->d <= 0 || m->nl <= 0 || m->K < 1) { free(m); fclose(fp); return 2; }
+    const size_t d = m->d, E = m->E, N = m->N, K = m->K, r = m->r, F = m->F;
+    size_t per_layer = 2 * d + 2 * E * d + E * K + E + (r + 2 * N) * E + E * r + E + E * N + E + d * E
+                       + (F ? F * d + F + d * F + d : 0) + 2 * d;
+    size_t total = 256 * d + m->nl * per_layer + 256 * d + 256;
+    float* raw = (float*)malloc(total * sizeof(float));
+    size_t got = fread(raw, sizeof(float), total, fp);
+    int extra = fgetc(fp);
+    fclose(fp);
+    if (got != total || extra != EOF) { free(raw); free(m); return 3; }
+    m->blob = (double*)malloc(total * sizeof(double));
+    for (size_t i = 0; i < total; i++) m->blob[i] = (double)raw[i];
+    free(raw);
+    double* cur = m->blob;
+    m->embed = take(&cur, 256 * d);
+    m->layers = (orc_layer*)calloc(m->nl, sizeof(orc_layer));
+    for (int l = 0; l < m->nl; l++) {
+        orc_layer* L = &m->layers[l];
+        L->ln_a_w = take(&cur, d); L->ln_a_b = take(&cur, d);
+        L->in_w = take(&cur, 2 * E * d);
+        L->conv_w = take(&cur, E * K); L->conv_b = take(&cur, E);
+        L->x_w = take(&cur, (r + 2 * N) * E);
+        L->dt_w = take(&cur, E * r); L->dt_b = take(&cur, E);
+        L->A_log = take(&cur, E * N);
+        L->A = (double*)malloc(sizeof(double) * E * N);
+        for (size_t i = 0; i < E * N; i++) L->A[i] = -exp(L->A_log[i]);
+        L->D = take(&cur, E);
+        L->out_w = take(&cur, d * E);
+        if (F) {
+            L->ffn_w1 = take(&cur, F * d); L->ffn_b1 = take(&cur, F);
+            L->ffn_w2 = take(&cur, d * F); L->ffn_b2 = take(&cur, d);
+        }
+        L->ln_b_w = take(&cur, d); L->ln_b_b = take(&cur, d);
+    }
+    m->head_w = take(&cur, 256 * d);
+    m->head_b = take(&cur, 256);
+    *out = m;
+    return 0;
+}
+
+void orc_model_free(orc_model* m) {
+    if (!m) return;
+    for (int l = 0; l < m->nl; l++) free(m->layers[l].A);
+    free(m->layers); free(m->blob); free(m);
+}
+
+int orc_model_dims(const orc_model* m, int* o) {
+    o[0] = m->vocab; o[1] = m->d; o[2] = m->nl; o[3] = m->N;
+    o[4] = m->K; o[5] = m->E; o[6] = m->r; o[7] = m->ffn_mult;
+    return 0;
+}
+
+orc_state* orc_state_new(const orc_model* m) {
+    orc_state* s = (orc_state*)malloc(sizeof(orc_state));
+    s->conv = (double*)calloc((size_t)m->nl * m->E * (m->K > 1 ? m->K - 1 : 1), sizeof(double));
+    s->h = (double*)calloc((size_t)m->nl * m->E * m->N, sizeof(double));
+    return s;
+}
+
+void orc_state_free(orc_state* s) {
+    if (!s) return;
+    free(s->conv); free(s->h); free(s);
+}
+
+/* ------------------------------------------------------ elementary blocks */
+
+static double softplus(double v) { return v > 20.0 ? v : log1p(exp(v)); }
+static double silu(double v) { return v / (1.0 + exp(-v)); }
+static double gelu(double v) { return 0.5 * v * (1.0 + erf(v / sqrt(2.0))); }
+
+/* y = W x (+ b); W is [rows][cols] row-major (nn.Linear layout). */
+static void linear(int rows, int cols, const double* W, const double* b, const double* x, double* y) {
+    for (int i = 0; i < rows; i++) {
+        double acc = 0.0;
+        for (int j = 0; j < cols; j++) acc += W[(size_t)i * cols + j] * x[j];
+        y[i] = b ? acc + b[i] : acc;
+    }
+}
+
+/* LayerNorm over d features: (x - mean) / sqrt(var + 1e-5) * g + b. */
+void orc_layernorm(int d, const double* x, const double* g, const double* b, double* y) {
+    double mean = 0.0, var = 0.0;
+    for (int i = 0; i < d; i++) mean += x[i];
+    mean /= d;
+    for (int i = 0; i < d; i++) var += (x[i] - mean) * (x[i] - mean);
+    var /= d;
+    double inv = 1.0 / sqrt(var + 1e-5);
+    for (int i = 0; i < d; i++) y[i] = (x[i] - mean) * inv * g[i] + b[i];
+}
+
+/* One causal depthwise-conv step for channel data xi[E]: window holds the
+ * previous K-1 inputs (oldest first); tap K-1 multiplies the newest input. */
+static void conv_step(int E, int K, double* window, const double* xi, const double* w,
+                      const double* b, double* out) {
+    for (int c = 0; c < E; c++) {
+        double* win = window + (size_t)c * (K - 1);
+        double acc = b ? b[c] : 0.0;
+        for (int k = 0; k < K - 1; k++) acc += w[(size_t)c * K + k] * win[k];
+        acc += w[(size_t)c * K + K - 1] * xi[c];
+        out[c] = acc;
+        for (int k = 0; k + 1 < K - 1; k++) win[k] = win[k + 1];
+        if (K > 1) win[K - 2] = xi[c];
+    }
+}
+
+void orc_causal_conv(int T, int E, int K, const double* x, const double* w, const double* b,
+                     double* out) {
+    double* window = (double*)calloc((size_t)E * (K > 1 ? K - 1 : 1), sizeof(double));
+    for (int t = 0; t < T; t++)
+        conv_step(E, K, window, x + (size_t)t * E, w, b, out + (size_t)t * E);
+    free(window);
+}
+
+/* One selective-scan step (App. A): for every channel c and state n,
+ *   h[c][n] <- exp(delta_c A[c][n]) h[c][n] + delta_c B[n] u_c
+ *   y_c     =  sum_n C[n] h[c][n] + D_c u_c                              */
+static void scan_step(int E, int N, double* h, const double* u, const double* delta,
+                      const double* A, const double* B, const double* C, const double* D,
+                      double* y) {
+    for (int c = 0; c < E; c++) {
+        double acc = 0.0;
+        for (int n = 0; n < N; n++) {
+            double* hc = &h[(size_t)c * N + n];
+            *hc = exp(delta[c] * A[(size_t)c * N + n]) * (*hc) + delta[c] * B[n] * u[c];
+            acc += C[n] * (*hc);
+        }
+        y[c] = acc + D[c] * u[c];
+    }
+}
+
+void orc_selective_scan(int T, int E, int N, const double* u, const double* delta,
+                        const double* A, const double* B, const double* C, const double* D,
+                        double* y) {
+    double* h = (double*)calloc((size_t)E * N, sizeof(double));
+    for (int t = 0; t < T; t++)
+        scan_step(E, N, h, u + (size_t)t * E, delta + (size_t)t * E, A, B + (size_t)t * N,
+                  C + (size_t)t * N, D, y + (size_t)t * E);
+    free(h);
+}
+
+void orc_softmax(const double* l, double* p) {
+    double m = l[0], Z = 0.0;
+    for (int a = 1; a < 256; a++) if (l[a] > m) m = l[a];
+    for (int a = 0; a < 256; a++) { p[a] = exp(l[a] - m); Z += p[a]; }
+    for (int a = 0; a < 256; a++) p[a] /= Z;
+}
+
+void orc_log2_softmax(const double* l, double* lp) {
+    double m = l[0], Z = 0.0;
+    for (int a = 1; a < 256; a++) if (l[a] > m) m = l[a];
+    for (int a = 0; a < 256; a++) Z += exp(l[a] - m);
+    double lz = log(Z);
+    for (int a = 0; a < 256; a++) lp[a] = (l[a] - m - lz) / log(2.0);
+}
+
+/* ---------------------------------------------------- the step function */
+
+void orc_step(const orc_model* m, orc_state* st, int byte, double* logits) {
+    const int d = m->d, E = m->E, N = m->N, K = m->K, r = m->r, F = m->F;
+    double* x = (double*)malloc(sizeof(double) * d);
+    double* xn = (double*)malloc(sizeof(double) * d);
+    double* xz = (double*)malloc(sizeof(double) * 2 * E);
+    double* u = (double*)malloc(sizeof(double) * E);
+    double* dbc = (double*)malloc(sizeof(double) * (r + 2 * N));
+    double* delta = (double*)malloc(sizeof(double) * E);
+    double* y = (double*)malloc(sizeof(double) * E);
+    double* o = (double*)malloc(sizeof(double) * (F > d ? F : d));
+    double* hid = (double*)malloc(sizeof(double) * (F ? F : 1));
+
+    /* ByteEmbed */
+    memcpy(x, m->embed + (size_t)byte * d, sizeof(double) * d);
+    for (int l = 0; l < m->nl; l++) {
+        const orc_layer* L = &m->layers[l];
+        /* Mamba mixer on LN_a(x) */
+        orc_layernorm(d, x, L->ln_a_w, L->ln_a_b, xn);
+        linear(2 * E, d, L->in_w, NULL, xn, xz);          /* xi = xz[0:E], z = xz[E:2E] */
+        conv_step(E, K, st->conv + (size_t)l * E * (K > 1 ? K - 1 : 1), xz, L->conv_w, L->conv_b, u);
+        for (int c = 0; c < E; c++) u[c] = silu(u[c]);
+        linear(r + 2 * N, E, L->x_w, NULL, u, dbc);       /* delta(r), B(N), C(N) */
+        linear(E, r, L->dt_w, L->dt_b, dbc, delta);
+        for (int c = 0; c < E; c++) delta[c] = softplus(delta[c]);
+        scan_step(E, N, st->h + (size_t)l * E * N, u, delta, L->A, dbc + r, dbc + r + N, L->D, y);
+        for (int c = 0; c < E; c++) y[c] *= silu(xz[E + c]);
+        linear(d, E, L->out_w, NULL, y, o);
+        for (int i = 0; i < d; i++) x[i] += o[i];          /* residual */
+        if (F) {
+            linear(F, d, L->ffn_w1, L->ffn_b1, x, hid);
+            for (int i = 0; i < F; i++) hid[i] = gelu(hid[i]);
+            linear(d, F, L->ffn_w2, L->ffn_b2, hid, o);
+            for (int i = 0; i < d; i++) x[i] += o[i];
+        }
+        orc_layernorm(d, x, L->ln_b_w, L->ln_b_b, xn);
+        memcpy(x, xn, sizeof(double) * d);
+    }
+    linear(256, d, m->head_w, m->head_b, x, logits);
+    free(x); free(xn); free(xz); free(u); free(dbc); free(delta); free(y); free(o); free(hid);
+}
+
+/* ------------------------------------------------ quantiser (R9) and CDF */
+
+void orc_quantise(const double* p, uint32_t* f) {
+    int64_t sum = 0;
+    int best = 0;
+    for (int a = 0; a < 256; a++) {
+        double q = floor(p[a] * (double)(ORC_M - 256));
+        int64_t fa = 1 + (int64_t)q;
+        if (fa < 1) fa = 1;
+        if (fa > (int64_t)ORC_M) fa = ORC_M;
+        f[a] = (uint32_t)fa;
+        sum += fa;
+        if (p[a] > p[best]) best = a;
+    }
+    f[best] = (uint32_t)((int64_t)f[best] + ((int64_t)ORC_M - sum));
+}
+
+void orc_quantise_f32(const float* p, uint32_t* f) {
+    int64_t sum = 0;
+    int best = 0;
+    for (int a = 0; a < 256; a++) {
+        float q = floorf(p[a] * 65280.0f);
+        int64_t fa = 1 + (int64_t)q;
+        if (fa < 1) fa = 1;
+        if (fa > (int64_t)ORC_M) fa = ORC_M;
+        f[a] = (uint32_t)fa;
+        sum += fa;
+        if (p[a] > p[best]) best = a;
+    }
+    f[best] = (uint32_t)((int64_t)f[best] + ((int64_t)ORC_M - sum));
+}
+
+void orc_cdf_from_hist(const uint32_t* f, uint32_t* cdf) {
+    cdf[0] = 0;
+    for (int a = 0; a < 256; a++) cdf[a + 1] = cdf[a] + f[a];
+}
+
+/* ------------------------------------------------------ range coder */
+
+typedef struct {
+    uint64_t L, R;
+    uint8_t* out;
+    size_t cap, n;
+    int overflow;
+    uint64_t straddles;
+} orc_enc;
+
+static void enc_emit(orc_enc* e, uint8_t b) {
+    if (e->n < e->cap) e->out[e->n] = b; else e->overflow = 1;
+    e->n++;
+}
+
+static void enc_init(orc_enc* e, uint8_t* out, size_t cap) {
+    e->L = 0; e->R = 1ull << 32; e->out = out; e->cap = cap; e->n = 0; e->overflow = 0; e->straddles = 0;
+}
+
+/* Encoder update (paragraph "Encoder"), then renormalisation R11/R12. */
+static void enc_put(orc_enc* e, uint32_t c_lo, uint32_t freq) {
+    e->L = e->L + (e->R * c_lo) / ORC_M;
+    e->R = (e->R * freq) / ORC_M;
+    for (;;) {
+        uint64_t E = e->L + e->R - 1;
+        if (e->L / ORC_TOP == E / ORC_TOP) {
+            enc_emit(e, (uint8_t)(e->L / ORC_TOP));
+            e->L = (e->L * 256) % (1ull << 32);
+            e->R = e->R * 256;
+        } else if (e->R < ORC_BOT) {
+            e->R = ORC_BOT - (e->L % ORC_BOT);
+            e->straddles++;
+        } else {
+            break;
+        }
+    }
+}
+
+static void enc_finish(orc_enc* e) {
+    for (int i = 3; i >= 0; i--) enc_emit(e, (uint8_t)(e->L >> (8 * i)));
+}
+
+typedef struct {
+    uint64_t L, R, C;
+    const uint8_t* in;
+    size_t size, pos;
+    int corrupt;
+} orc_dec;
+
+static uint8_t dec_byte(orc_dec* d) {
+    if (d->pos < d->size) return d->in[d->pos++];
+    d->pos++;
+    d->corrupt = 1;
+    return 0;
+}
+
+static void dec_init(orc_dec* d, const uint8_t* in, size_t size) {
+    d->L = 0; d->R = 1ull << 32; d->in = in; d->size = size; d->pos = 0; d->corrupt = 0; d->C = 0;
+    for (int i = 0; i < 4; i++) d->C = d->C * 256 + dec_byte(d);
+}
+
+/* Decoder (paragraph "Decoder"): target x, unique symbol with
+ * C(s) <= x < C(s+1), the encoder's update, and the same renormalisation
+ * with C <- ((C << 8) + b) mod 2^w on every emitted byte. */
+static int dec_get(orc_dec* d, const uint32_t* cdf) {
+    if (d->C < d->L || d->C - d->L >= d->R) {     /* impossible on a valid stream */
+        d->corrupt = 1;
+        d->C = d->L;
+    }
+    uint64_t x = ((d->C - d->L + 1) * ORC_M - 1) / d->R;
+    int s = 0;
+    for (int a = 0; a < 256; a++)
+        if (cdf[a] <= x && x < cdf[a + 1]) { s = a; break; }
+    d->L = d->L + (d->R * cdf[s]) / ORC_M;
+    d->R = (d->R * (cdf[s + 1] - cdf[s])) / ORC_M;
+    for (;;) {
+        uint64_t E = d->L + d->R - 1;
+        if (d->L / ORC_TOP == E / ORC_TOP) {
+            d->L = (d->L * 256) % (1ull << 32);
+            d->R = d->R * 256;
+            d->C = (d->C * 256 + dec_byte(d)) % (1ull << 32);
+        } else if (d->R < ORC_BOT) {
+            d->R = ORC_BOT - (d->L % ORC_BOT);
+        } else {
+            break;
+        }
+    }
+    return s;
+}
+
+size_t orc_coded_bound(size_t n_symbols) { return 5 * n_symbols + 4; }
+
+int orc_encode_cdfs(size_t n, const uint32_t* cdfs, const uint8_t* syms, uint8_t* out, size_t cap,
+                    size_t* size, uint64_t* straddles) {
+    orc_enc e;
+    enc_init(&e, out, cap);
+    for (size_t t = 0; t < n; t++) {
+        const uint32_t* c = cdfs + t * 257;
+        enc_put(&e, c[syms[t]], c[syms[t] + 1] - c[syms[t]]);
+    }
+    enc_finish(&e);
+    *size = e.n;
+    if (straddles) *straddles = e.straddles;
+    return e.overflow ? 1 : 0;
+}
+
+int orc_decode_cdfs(size_t n, const uint32_t* cdfs, const uint8_t* in, size_t size, uint8_t* syms) {
+    orc_dec d;
+    dec_init(&d, in, size);
+    for (size_t t = 0; t < n; t++) syms[t] = (uint8_t)dec_get(&d, cdfs + t * 257);
+    return (d.corrupt || d.pos != size) ? 1 : 0;
+}
+
+/* ------------------------------------------------- whole-stream method */
+
+size_t orc_max_compressed_size(size_t len) {
+    if (len == 0) return 0;
+    if (len == 1) return 1;
+    return 1 + orc_coded_bound(len - 1);
+}
+
+/* Probabilities -> histogram -> CDF for one set of logits. */
+static void logits_to_cdf(const double* logits, uint32_t* cdf) {
+    double p[256];
+    uint32_t f[256];
+    orc_softmax(logits, p);
+    orc_quantise(p, f);
+    orc_cdf_from_hist(f, cdf);
+}
+
+int orc_compress_stream(const orc_model* m, const uint8_t* in, size_t len, uint8_t* out, size_t cap,
+                        size_t* size) {
+    *size = 0;
+    if (len == 0) return 0;
+    if (cap < 1) return 1;
+    out[0] = in[0];                               /* first byte stored raw */
+    *size = 1;
+    if (len == 1) return 0;
+    orc_state* st = orc_state_new(m);
+    orc_enc e;
+    enc_init(&e, out + 1, cap - 1);
+    double logits[256];
+    uint32_t cdf[257];
+    for (size_t t = 0; t + 1 < len; t++) {
+        orc_step(m, st, in[t], logits);           /* predicts in[t+1] */
+        logits_to_cdf(logits, cdf);
+        enc_put(&e, cdf[in[t + 1]], cdf[in[t + 1] + 1] - cdf[in[t + 1]]);
+    }
+    enc_finish(&e);
+    orc_state_free(st);
+    *size = 1 + e.n;
+    return e.overflow ? 1 : 0;
+}
+
+int orc_decompress_stream(const orc_model* m, const uint8_t* in, size_t size, size_t len,
+                          uint8_t* out) {
+    if (len == 0) return size == 0 ? 0 : 1;
+    if (size < 1) return 1;
+    out[0] = in[0];
+    if (len == 1) return size == 1 ? 0 : 1;
+    orc_state* st = orc_state_new(m);
+    orc_dec d;
+    dec_init(&d, in + 1, size - 1);
+    double logits[256];
+    uint32_t cdf[257];
+    for (size_t t = 0; t + 1 < len; t++) {
+        orc_step(m, st, out[t], logits);
+        logits_to_cdf(logits, cdf);
+        out[t + 1] = (uint8_t)dec_get(&d, cdf);
+    }
+    orc_state_free(st);
+    return (d.corrupt || d.pos != size - 1) ? 1 : 0;
+}
+
+int orc_logprobs(const orc_model* m, const uint8_t* in, size_t len, double* log2p) {
+    if (len < 2) return 0;
+    orc_state* st = orc_state_new(m);
+    double logits[256];
+    for (size_t t = 0; t + 1 < len; t++) {
+        orc_step(m, st, in[t], logits);
+        orc_log2_softmax(logits, log2p + t * 256);
+    }
+    orc_state_free(st);
+    return 0;
+}
+
+int orc_cdfs(const orc_model* m, const uint8_t* in, size_t len, uint32_t* cdfs) {
+    if (len < 2) return 0;
+    orc_state* st = orc_state_new(m);
+    double logits[256];
+    for (size_t t = 0; t + 1 < len; t++) {
+        orc_step(m, st, in[t], logits);
+        logits_to_cdf(logits, cdfs + t * 257);
+    }
+    orc_state_free(st);
+    return 0;
+}
+
+int orc_compress_batch(const orc_model* m, size_t n, const uint8_t* const* ins, const size_t* lens,
+                       uint8_t* const* outs, const size_t* caps, size_t* sizes, int n_threads) {
+    int bad = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+#endif
+    for (long i = 0; i < (long)n; i++)
+        bad |= orc_compress_stream(m, ins[i], lens[i], outs[i], caps[i], &sizes[i]);
+    (void)n_threads;
+    return bad;
+}
