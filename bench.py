@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""BOA Constrictor round-trip throughput on one B300 (or N replicas).
+
+Workload: a 64 MiB synthetic ATLAS-like jet table (row-major 5 x f32 rows,
+Poisson(6) jets per event) cut into 4096 streams of 16 KB, compressed and
+decompressed with a random-init Mamba predictor (d_model 256, 3 layers,
+d_state 16, expand 2), FP32 throughout.  One step = compress all streams +
+decompress all streams (the whole hot path); value = uncompressed MB
+(10^6 bytes) / step time, inputs resident in HBM.  The L2 is flushed (a
+256 MiB write) before every timed step.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2511_11337_b300 import synth  # noqa: E402
+
+METRIC = "compress & decompress MB/s on 1 B300 at <=0.5% code-length gap vs FP64 oracle"
+UNIT = "MB/s"
+N_STREAMS, STREAM_LEN = 4096, 16384
+WORKLOAD = "ATLAS-like jet table, 64 MiB as 4096 x 16 KB streams; Mamba d_model=256, 3 layers, d_state=16, expand=2 (1.45 M params), FP32"
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    source is unchanged since it was captured (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    ent = t.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != ent["source_sha256"]:
+        return None
+    return ent
+
+
+# ---------------------------------------------------------------- oracle leg
+
+def oracle_sample(streams: list[bytes], prefix: int):
+    """Time the FP64 oracle (compress + decompress) on the first `prefix`
+    bytes of each given stream, one OpenMP thread per stream."""
+    from oracle import oracle as O
+    path = os.path.join(tempfile.mkdtemp(), "paper.boaw")
+    synth.make_model_file(path, synth.PAPER_SCALE, seed=2)
+    m = O.Model(path)
+    sample = [s[:prefix] for s in streams]
+    threads = len(sample)
+    t0 = time.perf_counter()
+    comp = m.compress_batch(sample, n_threads=threads)
+    dec, ok = m.decompress_batch(comp, [len(s) for s in sample], n_threads=threads)
+    dt = time.perf_counter() - t0
+    assert ok and dec == sample
+    nbytes = sum(map(len, sample))
+    return nbytes / 1e6 / dt, dt, nbytes, threads
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    buf = synth.atlas_workload(N_STREAMS, STREAM_LEN, seed=2000)
+    streams = synth.split_equal(buf, N_STREAMS)[:cores]
+    prefix = 2048
+    for _ in range(args.warmup):
+        oracle_sample(streams, 256)
+    times, nb = [], 0
+    for _ in range(args.steps):
+        _, dt, nb, threads = oracle_sample(streams, prefix)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    v = nb / 1e6 / (ms / 1e3)
+    sample = f"first {prefix} B of {len(streams)} of the 4096 streams ({nb} B), compress + decompress"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def run_boa(args):
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2511_11337_b300 import api
+
+    tmpd = tempfile.mkdtemp()
+    path = synth.make_model_file(os.path.join(tmpd, "paper.boaw"), synth.PAPER_SCALE, seed=2)
+    buf = synth.atlas_workload(N_STREAMS, STREAM_LEN, seed=2000 + rank)
+    streams = synth.split_equal(buf, N_STREAMS)
+    total = len(buf)
+
+    stream = torch.cuda.Stream()
+    model = api.Model(path, device=local, cuda_stream=stream.cuda_stream)
+    flat, in_off = api.pack(streams)
+    lens = np.diff(in_off)
+    out_off = api.compressed_slot_offsets(lens)
+    d_in = torch.from_numpy(flat.copy()).cuda()
+    d_out = torch.zeros(int(out_off[-1]), dtype=torch.uint8, device="cuda")
+    d_dec = torch.zeros(total, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        sizes = model.compress_device(d_in.data_ptr(), in_off, d_out.data_ptr(), out_off)
+        n1 = model.last_launch_count
+        model.decompress_device(d_out.data_ptr(), out_off, lens, d_dec.data_ptr(), in_off, in_sizes=sizes)
+        return sizes, n1 + model.last_launch_count
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert torch.equal(d_dec, d_in), "round trip failed in warm-up"
+
+    # timed region
+    model.profile(True, decode_step_stride=8)
+    model.profile_reset()
+    evs = []
+    launches = 0
+    sizes = None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sizes, n = step()
+            b.record(stream)
+            evs.append((a, b))
+            launches += n
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    model.profile(False)
+    prof = model.profile_read()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    assert torch.equal(d_dec, d_in), "round trip failed in timed region"
+    comp_total = int(np.sum(sizes))
+
+    # end to end through the host API (pinned staging, H2D, compute, D2H)
+    host_streams = streams
+    e2e_times = []
+    for _ in range(max(args.e2e_steps, 1)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        comp = model.compress(host_streams)
+        dec = model.decompress(comp, [len(s) for s in host_streams])
+        e2e_times.append(time.perf_counter() - t0)
+    assert dec == host_streams
+    e2e_comp = sum(map(len, comp))
+    e2e_s = statistics.mean(e2e_times)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    value = world * total / 1e6 / (ms / 1e3)
+    peaks, peak_src = measured_peaks()
+    # dominant kernel class over the step
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"] / kv[1]["launches"] * (kv[1]["launches"]))[0] if prof else None
+    roof = None
+    if dom:
+        p = prof[dom]
+        if dom.startswith("gemm"):
+            achieved = p["flops"] / (p["ms"] / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_PEAK_TFLOPS, "kernel": dom,
+                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz (FP32 FFMA, no tensor cores)"}
+        else:
+            achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "kernel": dom, "peak_source": f"hbm_gbs ({peak_src})"}
+        tr = traffic_for(dom)
+        roof["traffic"] = tr["bytes_per_launch"] if tr else None
+        roof["avg_launch_ms"] = p["ms"] / p["launches"]
+        roof["algorithmic_per_launch"] = (p["flops"] if dom.startswith("gemm") else p["bytes"]) / p["launches"]
+    step_ms = sum(v["ms"] for v in prof.values())
+    breakdown = {k: {"launches_timed": v["launches"], "ms": round(v["ms"], 3),
+                     "share_of_timed": round(v["ms"] / step_ms, 4) if step_ms else None} for k, v in prof.items()}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v_cpu, dt, nb, threads = oracle_sample(streams[:cores], args.cpu_prefix)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {args.cpu_prefix} B of {threads} of the 4096 streams ({nb} B), compress + decompress, {dt:.1f} s"}
+
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "streams": N_STREAMS, "stream_len": STREAM_LEN, "bytes_per_gpu": total,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "compression_ratio": total / comp_total,
+        "compressed_bytes": comp_total,
+        "wall_s_timed": t_wall,
+        "e2e": {"value": world * total / 1e6 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": total + e2e_comp,
+                "d2h_bytes_per_step": e2e_comp + total},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernel_breakdown": breakdown,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="boa", choices=["boa", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-prefix", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_boa(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * boa.h -- C-ABI of the B300 BOA Constrictor library (libboa.so).
+ *
+ * BOA Constrictor (arXiv 2511.11337) compresses bytes losslessly by pairing a
+ * small autoregressive Mamba next-byte predictor with a range coder.  The
+ * input is split into independent streams; all active streams are stepped
+ * together on the GPU, each with its own coder, and the first byte of every
+ * stream is stored raw (paper, section "Coders & Parallelisation").
+ *
+ * Conventions for every call:
+ *   - Return value: BOA_OK (0) or an error code; on error the thread-local
+ *     message from boa_last_error() says what went wrong.  A failed call
+ *     leaves caller buffers in an unspecified state but never writes past
+ *     the capacities it was given.
+ *   - Ownership: every buffer is owned by the caller; the library keeps no
+ *     pointer to it after the call returns.  A boa_model owns its device
+ *     weights and its device workspace (grown on demand, freed by
+ *     boa_free_model).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the model's device.
+ *   - Calls on one model are serialised on that model's CUDA stream; use one
+ *     model object per host thread for concurrency.
+ *   - Per-stream byte format: out[0] = the stream's first byte (raw), then
+ *     the range coder's bytes including its 4-byte flush.  A stream of
+ *     length 0 compresses to 0 bytes and a stream of length 1 to 1 byte.
+ */
+#ifndef BOA_H
+#define BOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BOA_OK = 0,
+    BOA_ERR_ARG = 1,                /* invalid argument (null pointer, bad size) */
+    BOA_ERR_IO = 2,                 /* weight file could not be read */
+    BOA_ERR_FORMAT = 3,             /* weight file malformed or unsupported shape */
+    BOA_ERR_CUDA = 4,               /* CUDA runtime error or no usable GPU */
+    BOA_ERR_OOM = 5,                /* device allocation failed */
+    BOA_ERR_OUTPUT_TOO_SMALL = 6,   /* an output capacity is below boa_max_compressed_size */
+    BOA_ERR_CORRUPT = 7,            /* a coded stream did not decode cleanly */
+    BOA_ERR_FINGERPRINT = 8         /* data was produced by a different model */
+} boa_status;
+
+typedef enum {
+    BOA_PREC_FP32 = 0               /* all projections in FP32 on the CUDA cores */
+} boa_precision;
+
+typedef struct {
+    int device;                     /* CUDA device ordinal */
+    int precision;                  /* boa_precision */
+    void* cuda_stream;              /* cudaStream_t to run on; NULL = library-owned stream */
+} boa_opts;
+
+typedef struct boa_model boa_model; /* opaque; owned by the library */
+
+/* Load a weight file and upload it to the GPU.
+ * Paper: the predictor Q is an embedding, n_l Mamba blocks and a linear head
+ * (Alg. 1 "Forward Pass"; section "Range coding", paragraph "Alphabet,
+ * sequence, and model").  The file is a 40-byte header (magic "BOAW",
+ * version 1, then u32 vocab=256, d_model, n_layer, d_state, d_conv, expand,
+ * dt_rank, ffn_mult) followed by little-endian float32 tensors in the fixed
+ * order embed, per layer {ln_a.w, ln_a.b, in_proj.w[2E][d], conv.w[E][K],
+ * conv.b, x_proj.w[r+2N][E], dt_proj.w[E][r], dt_proj.b, A_log[E][N], D,
+ * out_proj.w[d][E], (ffn.w1[F][d], ffn.b1, ffn.w2[d][F], ffn.b2 when
+ * ffn_mult > 0), ln_b.w, ln_b.b}, head.w[256][d], head.b.
+ * opts may be NULL (device 0, FP32, library stream).  Errors: BOA_ERR_IO,
+ * BOA_ERR_FORMAT, BOA_ERR_CUDA, BOA_ERR_OOM.  *out is set only on success. */
+boa_status boa_load_model(const char* path, const boa_opts* opts, boa_model** out);
+
+/* Release the model, its device weights and workspace.  NULL is a no-op. */
+void boa_free_model(boa_model* model);
+
+/* 64-bit FNV-1a hash of the weight file bytes: the model fingerprint that
+ * the paper's container records (section "Coders & Parallelisation"). */
+uint64_t boa_model_fingerprint(const boa_model* model);
+
+/* Worst-case compressed size of a stream of len bytes: 1 raw byte plus at
+ * most 5 coder bytes per coded symbol plus the 4-byte flush
+ * (0 -> 0, 1 -> 1, n -> 1 + 5 (n - 1) + 4). */
+size_t boa_max_compressed_size(size_t len);
+
+/* Compress n_streams independent streams (host memory in and out).
+ * Paper: section "Range coding" (softmax, integer CDF, encoder update and
+ * renormalisation) driven by the step function of paragraph "Alphabet,
+ * sequence, and model", all streams stepped together (section "Coders &
+ * Parallelisation").  streams[i] holds lens[i] bytes; out[i] has room for
+ * out_caps[i] bytes; out_sizes[i] receives the bytes written.  Errors:
+ * BOA_ERR_ARG, BOA_ERR_OUTPUT_TOO_SMALL (checked before any work, against
+ * boa_max_compressed_size), BOA_ERR_CUDA, BOA_ERR_OOM. */
+boa_status boa_compress(boa_model* model, size_t n_streams, const uint8_t* const* streams,
+                        const size_t* lens, uint8_t* const* out, const size_t* out_caps,
+                        size_t* out_sizes);
+
+/* Decompress streams produced by boa_compress with the same model.
+ * Paper: section "Range coding", paragraph "Decoder" (target value x,
+ * symbol search, identical update, code-value shift-in), streams that have
+ * finished are masked out of each step (section "Coders & Parallelisation").
+ * bitstreams[i] holds sizes[i] bytes and decodes to lens[i] bytes in out[i]
+ * (caller-sized to lens[i]).  Errors: BOA_ERR_ARG, BOA_ERR_CORRUPT (a stream
+ * read past its end or left bytes unread; its output is then unreliable),
+ * BOA_ERR_CUDA, BOA_ERR_OOM. */
+boa_status boa_decompress(boa_model* model, size_t n_streams, const uint8_t* const* bitstreams,
+                          const size_t* sizes, const size_t* lens, uint8_t* const* out);
+
+/* Device-resident forms of the two calls above: each batch lives in one
+ * device buffer cut into slots.
+ * d_in: device; stream i occupies slot [in_offsets[i], in_offsets[i+1]).
+ * d_out: device; stream i may write slot [out_offsets[i], out_offsets[i+1]).
+ * in_offsets, out_offsets: host arrays of n_streams + 1 non-decreasing
+ * offsets.  Compression: slot i of d_in is the whole stream; out_sizes (host)
+ * receives each stream's byte count.  Decompression: in_sizes (host, may be
+ * NULL = whole slot) gives the coded bytes at the start of each input slot,
+ * so the compressor's output buffer can be decoded in place; lens (host)
+ * gives each stream's decoded length and output slot i must hold lens[i]
+ * bytes.  Same errors as the host forms. */
+boa_status boa_compress_device(boa_model* model, size_t n_streams, const uint8_t* d_in,
+                               const uint64_t* in_offsets, uint8_t* d_out,
+                               const uint64_t* out_offsets, uint64_t* out_sizes);
+boa_status boa_decompress_device(boa_model* model, size_t n_streams, const uint8_t* d_in,
+                                 const uint64_t* in_offsets, const uint64_t* in_sizes,
+                                 const uint64_t* lens, uint8_t* d_out, const uint64_t* out_offsets);
+
+/* Number of kernel launches the last compress / decompress call issued
+ * (counted by the host as it enqueues them). */
+uint64_t boa_last_launch_count(const boa_model* model);
+
+/* Kernel classes for boa_profile_read. */
+typedef enum {
+    BOA_KC_EMBED_LN = 0,    /* byte embedding + first LayerNorm */
+    BOA_KC_GEMM_IN = 1,     /* in_proj */
+    BOA_KC_CONV = 2,        /* causal depthwise conv + SiLU */
+    BOA_KC_GEMM_X = 3,      /* x_proj */
+    BOA_KC_SCAN = 4,        /* dt_proj + softplus + selective scan + gate */
+    BOA_KC_GEMM_OUT = 5,    /* out_proj + residual */
+    BOA_KC_GEMM_FFN = 6,    /* FFN projections (paper-shape blocks) */
+    BOA_KC_LN = 7,          /* block-output LayerNorm (+ next block's input norm) */
+    BOA_KC_GEMM_HEAD = 8,   /* head */
+    BOA_KC_ENCODE = 9,      /* softmax -> CDF -> range encoder */
+    BOA_KC_DECODE = 10,     /* softmax -> CDF -> range decoder */
+    BOA_KC_OTHER = 11,      /* set-up, flush, compaction */
+    BOA_KC_COUNT = 12
+} boa_kernel_class;
+
+/* Benchmark hook: when on, every kernel launch of compress / decompress is
+ * bracketed by a pair of CUDA events on the model's stream (decompression:
+ * only every decode_step_stride-th step), and per-class totals accumulate:
+ * launches timed, summed device milliseconds, and the algorithmic FLOPs and
+ * DRAM bytes those launches must at least perform.  Reset clears totals. */
+boa_status boa_profile_enable(boa_model* model, int on, int decode_step_stride);
+boa_status boa_profile_reset(boa_model* model);
+boa_status boa_profile_read(const boa_model* model, int kernel_class, uint64_t* launches, double* total_ms,
+                            double* flops, double* bytes);
+
+/* Thread-local message describing the last error on this thread. */
+const char* boa_last_error(void);
+
+/* ----------------------------------------------------------- test hooks
+ * Exposed for parity tests; not part of the compression API. */
+
+/* Range-code given integer CDFs on the GPU (section "Range coding",
+ * paragraphs "Encoder" and "Decoder").  n_seq independent sequences; sequence
+ * i has n_syms[i] symbols, its CDF rows start at row sum_{j<i} n_syms[j] of
+ * cdfs ([rows][257] u32, cdf[0] = 0, cdf[256] = 65536, strictly increasing)
+ * and its symbols at the same offset of syms.  Encoder output for sequence i
+ * goes to out + i * out_stride (capacity out_stride >= 5 n + 4), its size to
+ * sizes[i].  The decoder reads in + i * in_stride (in_sizes[i] bytes) and
+ * writes n_syms[i] symbols.  All pointers are host memory.  Errors:
+ * BOA_ERR_ARG, BOA_ERR_CORRUPT (decoder), BOA_ERR_CUDA. */
+boa_status boa_debug_encode_cdfs(size_t n_seq, const size_t* n_syms, const uint32_t* cdfs,
+                                 const uint8_t* syms, uint8_t* out, size_t out_stride,
+                                 size_t* sizes);
+boa_status boa_debug_decode_cdfs(size_t n_seq, const size_t* n_syms, const uint32_t* cdfs,
+                                 const uint8_t* in, size_t in_stride, const size_t* in_sizes,
+                                 uint8_t* syms);
+
+/* Integer histogram from float32 probabilities with the kernel's quantiser
+ * (paper "Probabilities and integer CDF": f >= 1, sum f = 2^16):
+ * f_a = 1 + floor(p_a * 65280) in float32, remainder to the most probable
+ * symbol (lowest index on ties).  p: host [n_rows][256]; f: host [n_rows][256]. */
+boa_status boa_debug_quantise(size_t n_rows, const float* p, uint32_t* f);
+
+/* Teacher-forced log2 next-byte probabilities of one stream from the
+ * compression path: out (host) [(len-1)][256], row t predicting byte t+1. */
+boa_status boa_debug_logprobs(boa_model* model, const uint8_t* stream, size_t len, float* out);
+
+/* When on, the next compress / decompress calls record a 64-bit hash of the
+ * integer CDF used at every coded step; boa_debug_read_cdf_trace copies the
+ * hashes of the last call, stream-major ([stream][step], sum(len-1) values). */
+boa_status boa_debug_enable_cdf_trace(boa_model* model, int on);
+boa_status boa_debug_read_cdf_trace(boa_model* model, uint64_t* out, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BOA_H */

@@ -537,3 +537,16 @@ int orc_compress_batch(const orc_model* m, size_t n, const uint8_t* const* ins, 
     (void)n_threads;
     return bad;
 }
+
+int orc_decompress_batch(const orc_model* m, size_t n, const uint8_t* const* ins, const size_t* sizes,
+                         const size_t* lens, uint8_t* const* outs, int n_threads) {
+    int bad = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+#endif
+    for (long i = 0; i < (long)n; i++)
+        bad |= orc_decompress_stream(m, ins[i], sizes[i], lens[i], outs[i]);
+    (void)n_threads;
+    return bad;
+}

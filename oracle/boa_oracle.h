@@ -65,6 +65,9 @@ int orc_cdfs(const orc_model* m, const uint8_t* in, size_t len, uint32_t* cdfs);
 int orc_compress_batch(const orc_model* m, size_t n, const uint8_t* const* ins, const size_t* lens,
                        uint8_t* const* outs, const size_t* caps, size_t* sizes, int n_threads);
 
+int orc_decompress_batch(const orc_model* m, size_t n, const uint8_t* const* ins, const size_t* sizes,
+                         const size_t* lens, uint8_t* const* outs, int n_threads);
+
 #ifdef __cplusplus
 }
 #endif

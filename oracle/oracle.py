@@ -44,6 +44,7 @@ def lib():
         L.orc_logprobs.argtypes = [vp, vp, sz, vp]
         L.orc_cdfs.argtypes = [vp, vp, sz, vp]
         L.orc_compress_batch.argtypes = [vp, sz, vp, vp, vp, vp, vp, i32]
+        L.orc_decompress_batch.argtypes = [vp, sz, vp, vp, vp, vp, i32]
     return _lib
 
 
@@ -123,6 +124,18 @@ class Model:
         if rc:
             raise RuntimeError("oracle batch compress overflow")
         return [o[:int(z)].tobytes() for o, z in zip(outs, sizes)]
+
+
+    def decompress_batch(self, comps: list[bytes], lens: list[int], n_threads: int = 0) -> tuple[list[bytes], bool]:
+        n = len(comps)
+        ins = [np.frombuffer(c, np.uint8).copy() if len(c) else np.zeros(1, np.uint8) for c in comps]
+        sizes = np.array([len(c) for c in comps], np.uint64)
+        l = np.array(lens, np.uint64)
+        outs = [np.zeros(max(int(x), 1), np.uint8) for x in lens]
+        in_ptrs = np.array([a.ctypes.data for a in ins], np.uint64)
+        out_ptrs = np.array([a.ctypes.data for a in outs], np.uint64)
+        rc = lib().orc_decompress_batch(self.h, n, _p(in_ptrs), _p(sizes), _p(l), _p(out_ptrs), n_threads)
+        return [o[:int(x)].tobytes() for o, x in zip(outs, lens)], rc == 0
 
 
 class _State:

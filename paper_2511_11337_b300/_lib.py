@@ -1,0 +1,66 @@
+"""ctypes loader for libboa.so (argument marshalling only).
+
+The library is the product: there is no Python or CPU fallback.  If the
+shared object is missing or no GPU is usable, calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_PKG, "libboa.so")
+
+# Every symbol include/boa.h declares, with its ctypes signature.
+vp, sz, u64, i32 = C.c_void_p, C.c_size_t, C.c_uint64, C.c_int
+SIGNATURES = {
+    "boa_load_model": (i32, [C.c_char_p, vp, C.POINTER(vp)]),
+    "boa_free_model": (None, [vp]),
+    "boa_model_fingerprint": (u64, [vp]),
+    "boa_max_compressed_size": (sz, [sz]),
+    "boa_compress": (i32, [vp, sz, vp, vp, vp, vp, vp]),
+    "boa_decompress": (i32, [vp, sz, vp, vp, vp, vp]),
+    "boa_compress_device": (i32, [vp, sz, vp, vp, vp, vp, vp]),
+    "boa_decompress_device": (i32, [vp, sz, vp, vp, vp, vp, vp, vp]),
+    "boa_last_launch_count": (u64, [vp]),
+    "boa_last_error": (C.c_char_p, []),
+    "boa_profile_enable": (i32, [vp, i32, i32]),
+    "boa_profile_reset": (i32, [vp]),
+    "boa_profile_read": (i32, [vp, i32, vp, vp, vp, vp]),
+    "boa_debug_encode_cdfs": (i32, [sz, vp, vp, vp, vp, sz, vp]),
+    "boa_debug_decode_cdfs": (i32, [sz, vp, vp, vp, sz, vp, vp]),
+    "boa_debug_quantise": (i32, [sz, vp, vp]),
+    "boa_debug_logprobs": (i32, [vp, vp, sz, vp]),
+    "boa_debug_enable_cdf_trace": (i32, [vp, i32]),
+    "boa_debug_read_cdf_trace": (i32, [vp, vp, sz]),
+}
+
+STATUS = {0: "BOA_OK", 1: "BOA_ERR_ARG", 2: "BOA_ERR_IO", 3: "BOA_ERR_FORMAT", 4: "BOA_ERR_CUDA",
+          5: "BOA_ERR_OOM", 6: "BOA_ERR_OUTPUT_TOO_SMALL", 7: "BOA_ERR_CORRUPT", 8: "BOA_ERR_FINGERPRINT"}
+
+_lib = None
+
+
+class BoaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(SO_PATH):
+            raise ImportError(f"libboa.so is not built ({SO_PATH}); run paper_2511_11337_b300.build.build()")
+        lib = C.CDLL(SO_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(code: int) -> None:
+    if code != 0:
+        raise BoaError(code, load().boa_last_error().decode(errors="replace"))

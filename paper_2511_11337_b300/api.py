@@ -1,0 +1,200 @@
+"""Python API over libboa.so: names follow include/boa.h; marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._lib import BoaError, check, load
+
+PREC_FP32 = 0
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def max_compressed_size(n: int) -> int:
+    return int(load().boa_max_compressed_size(n))
+
+
+class _Opts(C.Structure):
+    _fields_ = [("device", C.c_int), ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class Model:
+    """A predictor loaded on the GPU (boa_load_model)."""
+
+    def __init__(self, path: str, device: int = 0, precision: int = PREC_FP32, cuda_stream: int | None = None):
+        self._h = C.c_void_p()
+        opts = _Opts(device, precision, cuda_stream)
+        check(load().boa_load_model(os.fsencode(path), C.byref(opts), C.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            load().boa_free_model(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def fingerprint(self) -> int:
+        return int(load().boa_model_fingerprint(self._h))
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(load().boa_last_launch_count(self._h))
+
+    # ----------------------------------------------------------- host API
+    def compress(self, streams: list[bytes]) -> list[bytes]:
+        n = len(streams)
+        if n == 0:
+            return []
+        bufs = [np.frombuffer(s, np.uint8) if len(s) else np.zeros(1, np.uint8) for s in streams]
+        lens = np.array([len(s) for s in streams], np.uintp)
+        caps = np.array([max_compressed_size(len(s)) for s in streams], np.uintp)
+        outs = [np.zeros(max(int(c), 1), np.uint8) for c in caps]
+        in_ptrs = np.array([b.ctypes.data for b in bufs], np.uintp)
+        out_ptrs = np.array([o.ctypes.data for o in outs], np.uintp)
+        sizes = np.zeros(n, np.uintp)
+        check(load().boa_compress(self._h, n, _p(in_ptrs), _p(lens), _p(out_ptrs), _p(caps), _p(sizes)))
+        return [o[:int(z)].tobytes() for o, z in zip(outs, sizes)]
+
+    def decompress(self, comps: list[bytes], lens: list[int]) -> list[bytes]:
+        n = len(comps)
+        if n == 0:
+            return []
+        bufs = [np.frombuffer(c, np.uint8) if len(c) else np.zeros(1, np.uint8) for c in comps]
+        sizes = np.array([len(c) for c in comps], np.uintp)
+        l = np.array(lens, np.uintp)
+        outs = [np.zeros(max(int(x), 1), np.uint8) for x in lens]
+        in_ptrs = np.array([b.ctypes.data for b in bufs], np.uintp)
+        out_ptrs = np.array([o.ctypes.data for o in outs], np.uintp)
+        check(load().boa_decompress(self._h, n, _p(in_ptrs), _p(sizes), _p(l), _p(out_ptrs)))
+        return [o[:int(x)].tobytes() for o, x in zip(outs, lens)]
+
+    # ----------------------------------------------------------- device API
+    def compress_device(self, d_in_ptr: int, in_offsets: np.ndarray, d_out_ptr: int,
+                        out_offsets: np.ndarray) -> np.ndarray:
+        """d_in_ptr / d_out_ptr: device addresses (e.g. torch tensor data_ptr())."""
+        in_offsets = np.ascontiguousarray(in_offsets, np.uint64)
+        out_offsets = np.ascontiguousarray(out_offsets, np.uint64)
+        n = len(in_offsets) - 1
+        sizes = np.zeros(max(n, 1), np.uint64)
+        check(load().boa_compress_device(self._h, n, C.c_void_p(d_in_ptr), _p(in_offsets), C.c_void_p(d_out_ptr),
+                                         _p(out_offsets), _p(sizes)))
+        return sizes[:n]
+
+    def decompress_device(self, d_in_ptr: int, in_offsets: np.ndarray, lens: np.ndarray, d_out_ptr: int,
+                          out_offsets: np.ndarray, in_sizes: np.ndarray | None = None) -> None:
+        """in_sizes: coded bytes at the start of each input slot (None = whole slot)."""
+        in_offsets = np.ascontiguousarray(in_offsets, np.uint64)
+        out_offsets = np.ascontiguousarray(out_offsets, np.uint64)
+        lens = np.ascontiguousarray(lens, np.uint64)
+        n = len(in_offsets) - 1
+        sz = None
+        if in_sizes is not None:
+            in_sizes = np.ascontiguousarray(in_sizes, np.uint64)
+            sz = _p(in_sizes)
+        check(load().boa_decompress_device(self._h, n, C.c_void_p(d_in_ptr), _p(in_offsets), sz, _p(lens),
+                                           C.c_void_p(d_out_ptr), _p(out_offsets)))
+
+    # ----------------------------------------------------------- benchmark hooks
+    KERNEL_CLASSES = ["embed_ln", "gemm_in_proj", "conv_silu", "gemm_x_proj", "scan", "gemm_out_proj",
+                      "gemm_ffn", "layernorm", "gemm_head", "encode", "decode", "other"]
+
+    def profile(self, on: bool = True, decode_step_stride: int = 1) -> None:
+        check(load().boa_profile_enable(self._h, int(on), int(decode_step_stride)))
+
+    def profile_reset(self) -> None:
+        check(load().boa_profile_reset(self._h))
+
+    def profile_read(self) -> dict:
+        out = {}
+        for i, name in enumerate(self.KERNEL_CLASSES):
+            n, ms, fl, by = C.c_uint64(), C.c_double(), C.c_double(), C.c_double()
+            check(load().boa_profile_read(self._h, i, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
+            if n.value:
+                out[name] = {"launches": int(n.value), "ms": ms.value, "flops": fl.value, "bytes": by.value}
+        return out
+
+    # ----------------------------------------------------------- test hooks
+    def logprobs(self, data: bytes) -> np.ndarray:
+        n = len(data)
+        out = np.zeros((max(n - 1, 1), 256), np.float32)
+        buf = np.frombuffer(data, np.uint8) if n else np.zeros(1, np.uint8)
+        check(load().boa_debug_logprobs(self._h, _p(buf), n, _p(out)))
+        return out[:max(n - 1, 0)]
+
+    def enable_cdf_trace(self, on: bool = True) -> None:
+        check(load().boa_debug_enable_cdf_trace(self._h, int(on)))
+
+    def read_cdf_trace(self, n: int) -> np.ndarray:
+        out = np.zeros(max(n, 1), np.uint64)
+        check(load().boa_debug_read_cdf_trace(self._h, _p(out), n))
+        return out[:n]
+
+
+def encode_cdfs(cdf_list: list[np.ndarray], sym_list: list[np.ndarray]) -> list[bytes]:
+    """GPU range encoder fed caller CDFs ([n][257] u32 per sequence)."""
+    n_seq = len(cdf_list)
+    n_syms = np.array([len(s) for s in sym_list], np.uintp)
+    cdfs = np.ascontiguousarray(np.concatenate([np.asarray(c, np.uint32).reshape(-1, 257) for c in cdf_list]), np.uint32)
+    syms = np.ascontiguousarray(np.concatenate([np.asarray(s, np.uint8) for s in sym_list]), np.uint8)
+    stride = int(5 * max(n_syms.max(initial=0), 1) + 4)
+    out = np.zeros(n_seq * stride, np.uint8)
+    sizes = np.zeros(n_seq, np.uintp)
+    check(load().boa_debug_encode_cdfs(n_seq, _p(n_syms), _p(cdfs), _p(syms), _p(out), stride, _p(sizes)))
+    return [out[i * stride:i * stride + int(sizes[i])].tobytes() for i in range(n_seq)]
+
+
+def decode_cdfs(cdf_list: list[np.ndarray], coded: list[bytes]) -> list[np.ndarray]:
+    n_seq = len(cdf_list)
+    n_syms = np.array([np.asarray(c).reshape(-1, 257).shape[0] for c in cdf_list], np.uintp)
+    cdfs = np.ascontiguousarray(np.concatenate([np.asarray(c, np.uint32).reshape(-1, 257) for c in cdf_list]), np.uint32)
+    stride = max(max(len(c) for c in coded), 1)
+    inb = np.zeros(n_seq * stride, np.uint8)
+    for i, c in enumerate(coded):
+        inb[i * stride:i * stride + len(c)] = np.frombuffer(c, np.uint8)
+    in_sizes = np.array([len(c) for c in coded], np.uintp)
+    syms = np.zeros(max(int(n_syms.sum()), 1), np.uint8)
+    check(load().boa_debug_decode_cdfs(n_seq, _p(n_syms), _p(cdfs), _p(inb), stride, _p(in_sizes), _p(syms)))
+    out, o = [], 0
+    for k in n_syms:
+        out.append(syms[o:o + int(k)].copy())
+        o += int(k)
+    return out
+
+
+def quantise(p: np.ndarray) -> np.ndarray:
+    p = np.ascontiguousarray(p, np.float32).reshape(-1, 256)
+    f = np.zeros_like(p, dtype=np.uint32)
+    check(load().boa_debug_quantise(p.shape[0], _p(p), _p(f)))
+    return f
+
+
+def pack(streams: list[bytes]) -> tuple[np.ndarray, np.ndarray]:
+    """Concatenate streams into one byte array plus n+1 offsets."""
+    offs = np.zeros(len(streams) + 1, np.uint64)
+    offs[1:] = np.cumsum([len(s) for s in streams], dtype=np.uint64)
+    flat = np.frombuffer(b"".join(streams), np.uint8) if offs[-1] else np.zeros(0, np.uint8)
+    return flat, offs
+
+
+def slot_offsets(caps) -> np.ndarray:
+    """n+1 offsets of consecutive output slots with the given capacities."""
+    offs = np.zeros(len(caps) + 1, np.uint64)
+    offs[1:] = np.cumsum(np.asarray(caps, np.uint64), dtype=np.uint64)
+    return offs
+
+
+def compressed_slot_offsets(lens) -> np.ndarray:
+    return slot_offsets([max_compressed_size(int(n)) for n in lens])
+
+
+__all__ = ["pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32"]

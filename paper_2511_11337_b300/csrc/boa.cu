@@ -1,0 +1,910 @@
+// libboa.so: C-ABI of the B300 BOA Constrictor library (declared in include/boa.h).
+//
+// Host side: weight loading, device workspace, and the two step loops.
+//   compress   -- teacher-forced: the predictor runs over (streams x time
+//                 chunk) rows at once, then one warp per stream range-codes
+//                 the chunk's steps in order.
+//   decompress -- one step of every stream per pass (each byte feeds the next
+//                 step); same kernels with a chunk of one step.
+// Both sides evaluate every row with the same kernels, so the integer CDFs
+// agree bit for bit (paper, "Determinism and synchronisation").
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "boa.h"
+#include "common.cuh"
+#include "gemm_fp32.cuh"
+#include "kernels.cuh"
+
+using namespace boa;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+static boa_status fail(boa_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CU(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? BOA_ERR_OOM : BOA_ERR_CUDA,          \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define TRY(call)                         \
+    do {                                  \
+        boa_status s_ = (call);           \
+        if (s_ != BOA_OK) return s_;      \
+    } while (0)
+
+// ------------------------------------------------------------------ model
+
+struct DevLayer {
+    float *ln_a_w, *ln_a_b, *in_wt, *conv_w, *conv_b, *x_wt, *dt_w, *dt_b, *A2, *D, *out_wt;
+    float *w1t, *b1, *w2t, *b2, *ln_b_w, *ln_b_b;
+};
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    boa_status ensure(size_t want) {
+        if (want <= n) return BOA_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(want, 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(BOA_ERR_OOM, "cudaMalloc(%zu bytes): %s", want * sizeof(T), cudaGetErrorString(e));
+        }
+        n = want;
+        return BOA_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+template <typename T>
+struct HostBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    boa_status ensure(size_t want) {
+        if (want <= n) return BOA_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMallocHost(&p, std::max<size_t>(want, 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(BOA_ERR_OOM, "cudaMallocHost(%zu bytes): %s", want * sizeof(T), cudaGetErrorString(e));
+        }
+        n = want;
+        return BOA_OK;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+struct boa_model {
+    int device = 0;
+    int precision = BOA_PREC_FP32;
+    int d = 0, nl = 0, N = 0, K = 0, E = 0, r = 0, ffn_mult = 0, F = 0, R2 = 0;
+    uint64_t fingerprint = 0;
+    int num_sms = 148;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    float* weights = nullptr;   // one device allocation
+    float *embed = nullptr, *head_wt = nullptr, *head_b = nullptr;
+    std::vector<DevLayer> layers;
+
+    // workspace
+    DevBuf<float> x, xn, xz, u, dbc, yg, logits, hid, h, conv;
+    DevBuf<CoderState> st;
+    DevBuf<uint8_t> tokens, d_in, d_out, d_pack;
+    DevBuf<uint32_t> flags;
+    DevBuf<uint64_t> in_off, out_off, lens, sizes, trace_off, trace, pack_off;
+    HostBuf<uint8_t> h_in, h_out;
+    HostBuf<uint64_t> h_u64;
+    HostBuf<uint32_t> h_u32;
+
+    bool trace_on = false;
+    size_t trace_n = 0;
+    uint64_t launches = 0;
+
+    // Kernel-class timing with CUDA events on the model's stream (bench only).
+    bool prof_on = false;
+    int prof_stride = 1;            // time every prof_stride-th step of the decode loop
+    bool prof_step = true;          // is the current step timed?
+    struct ProfRec { int cls; cudaEvent_t a, b; double flops, bytes; };
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<ProfRec> prof_pending;
+    uint64_t prof_launches[BOA_KC_COUNT] = {};
+    double prof_ms[BOA_KC_COUNT] = {}, prof_flops[BOA_KC_COUNT] = {}, prof_bytes[BOA_KC_COUNT] = {};
+};
+
+static uint64_t fnv1a64(const uint8_t* p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; i++) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// ---- kernel-class profiling: an event pair around each timed launch.
+static const size_t kMaxProfEvents = 1u << 17;
+
+static cudaEvent_t prof_event(boa_model* m) {
+    if (m->ev_used == m->ev_pool.size()) {
+        if (m->ev_pool.size() >= kMaxProfEvents) return nullptr;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        m->ev_pool.push_back(e);
+    }
+    return m->ev_pool[m->ev_used++];
+}
+
+struct ProfScope {
+    boa_model* m;
+    int cls;
+    double flops, bytes;
+    cudaEvent_t a = nullptr;
+    ProfScope(boa_model* m_, int cls_, double flops_, double bytes_) : m(m_), cls(cls_), flops(flops_), bytes(bytes_) {
+        if (m->prof_on && m->prof_step) {
+            a = prof_event(m);
+            if (a) cudaEventRecord(a, m->stream);
+        }
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b = prof_event(m);
+        if (!b) return;
+        cudaEventRecord(b, m->stream);
+        m->prof_pending.push_back({cls, a, b, flops, bytes});
+    }
+};
+
+// Called after the stream is synchronised: fold the pending pairs into totals.
+static void prof_collect(boa_model* m) {
+    for (auto& r : m->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            m->prof_launches[r.cls]++;
+            m->prof_ms[r.cls] += ms;
+            m->prof_flops[r.cls] += r.flops;
+            m->prof_bytes[r.cls] += r.bytes;
+        }
+    }
+    m->prof_pending.clear();
+    m->ev_used = 0;
+}
+
+static bool supported_scan(int N, int r) {
+    return N == 16 && (r == 1 || r == 2 || r == 4 || r == 8 || r == 16);
+}
+
+static bool supported_d(int d) { return d == 64 || d == 128 || d == 256; }
+
+extern "C" size_t boa_max_compressed_size(size_t len) {
+    if (len == 0) return 0;
+    if (len == 1) return 1;
+    return 1 + 5 * (len - 1) + 4;
+}
+
+extern "C" const char* boa_last_error(void) { return g_err.c_str(); }
+
+extern "C" uint64_t boa_model_fingerprint(const boa_model* m) { return m ? m->fingerprint : 0; }
+
+extern "C" uint64_t boa_last_launch_count(const boa_model* m) { return m ? m->launches : 0; }
+
+static void free_workspace(boa_model* m) {
+    m->x.release(); m->xn.release(); m->xz.release(); m->u.release(); m->dbc.release();
+    m->yg.release(); m->logits.release(); m->hid.release(); m->h.release(); m->conv.release();
+    m->st.release(); m->tokens.release(); m->d_in.release(); m->d_out.release(); m->flags.release();
+    m->in_off.release(); m->out_off.release(); m->lens.release(); m->sizes.release();
+    m->trace_off.release(); m->trace.release(); m->d_pack.release(); m->pack_off.release();
+    m->h_in.release(); m->h_out.release(); m->h_u64.release(); m->h_u32.release();
+}
+
+extern "C" void boa_free_model(boa_model* m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    free_workspace(m);
+    for (auto e : m->ev_pool) cudaEventDestroy(e);
+    if (m->weights) cudaFree(m->weights);
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+// Transpose a row-major [rows][cols] matrix into [cols][rows].
+static void transpose(const float* src, int rows, int cols, float* dst) {
+    for (int i = 0; i < rows; i++)
+        for (int j = 0; j < cols; j++) dst[(size_t)j * rows + i] = src[(size_t)i * cols + j];
+}
+
+extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa_model** out) {
+    if (!path || !out) return fail(BOA_ERR_ARG, "boa_load_model: null argument");
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(BOA_ERR_IO, "cannot open weight file %s", path);
+    std::vector<uint8_t> buf;
+    {
+        fseek(fp, 0, SEEK_END);
+        long sz = ftell(fp);
+        fseek(fp, 0, SEEK_SET);
+        if (sz < 40) { fclose(fp); return fail(BOA_ERR_FORMAT, "weight file too short"); }
+        buf.resize((size_t)sz);
+        size_t got = fread(buf.data(), 1, buf.size(), fp);
+        fclose(fp);
+        if (got != buf.size()) return fail(BOA_ERR_IO, "short read on %s", path);
+    }
+    if (memcmp(buf.data(), "BOAW", 4) != 0) return fail(BOA_ERR_FORMAT, "bad magic");
+    uint32_t hdr[9];
+    memcpy(hdr, buf.data() + 4, sizeof hdr);
+    if (hdr[0] != 1) return fail(BOA_ERR_FORMAT, "unsupported version %u", hdr[0]);
+    const int vocab = (int)hdr[1], d = (int)hdr[2], nl = (int)hdr[3], N = (int)hdr[4], K = (int)hdr[5];
+    const int expand = (int)hdr[6], r = (int)hdr[7], ffn = (int)hdr[8];
+    const int E = expand * d, F = ffn * d, R2 = r + 2 * N;
+    if (vocab != 256 || nl < 1 || nl > 64 || expand < 1 || expand > 4 || r != (d + 15) / 16)
+        return fail(BOA_ERR_FORMAT, "unsupported header (vocab %d, layers %d, expand %d, dt_rank %d)", vocab, nl, expand, r);
+    if (!supported_d(d) || !supported_scan(N, r) || K < 2 || K > 4 || (ffn != 0 && ffn != 2 && ffn != 4))
+        return fail(BOA_ERR_FORMAT, "unsupported shape d=%d N=%d r=%d K=%d ffn=%d", d, N, r, K, ffn);
+
+    const size_t per_layer = 2 * (size_t)d + 2 * (size_t)E * d + (size_t)E * K + E + (size_t)R2 * E +
+                             (size_t)E * r + E + (size_t)E * N + E + (size_t)d * E +
+                             (F ? (size_t)F * d + F + (size_t)d * F + d : 0) + 2 * (size_t)d;
+    const size_t total = 256 * (size_t)d + nl * per_layer + 256 * (size_t)d + 256;
+    if (buf.size() != 40 + total * 4) return fail(BOA_ERR_FORMAT, "weight file size %zu, expected %zu", buf.size(), 40 + total * 4);
+
+    boa_opts o = {0, BOA_PREC_FP32, nullptr};
+    if (opts) o = *opts;
+    if (o.precision != BOA_PREC_FP32) return fail(BOA_ERR_ARG, "precision %d not supported", o.precision);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(BOA_ERR_CUDA, "no CUDA device available");
+    if (o.device < 0 || o.device >= ndev) return fail(BOA_ERR_ARG, "bad device %d", o.device);
+    CU(cudaSetDevice(o.device));
+
+    // Host-side rearrangement: weight matrices K-major, A pre-scaled by log2(e).
+    const float* src = reinterpret_cast<const float*>(buf.data() + 40);
+    std::vector<float> dev(total);
+    size_t so = 0, dof = 0;
+    auto copy = [&](size_t n) { size_t at = dof; memcpy(&dev[dof], src + so, n * 4); so += n; dof += n; return at; };
+    auto copy_t = [&](int rows, int cols) { size_t at = dof; transpose(src + so, rows, cols, &dev[dof]); so += (size_t)rows * cols; dof += (size_t)rows * cols; return at; };
+    struct Off { size_t ln_a_w, ln_a_b, in_wt, conv_w, conv_b, x_wt, dt_w, dt_b, A2, D, out_wt, w1t, b1, w2t, b2, ln_b_w, ln_b_b; };
+    std::vector<Off> lo(nl);
+    size_t embed_o = copy(256 * (size_t)d);
+    for (int l = 0; l < nl; l++) {
+        Off& q = lo[l];
+        q.ln_a_w = copy(d); q.ln_a_b = copy(d);
+        q.in_wt = copy_t(2 * E, d);
+        q.conv_w = copy((size_t)E * K); q.conv_b = copy(E);
+        q.x_wt = copy_t(R2, E);
+        q.dt_w = copy((size_t)E * r); q.dt_b = copy(E);
+        q.A2 = dof;
+        for (size_t i = 0; i < (size_t)E * N; i++)
+            dev[dof + i] = (float)(-std::exp((double)src[so + i]) * 1.4426950408889634);
+        so += (size_t)E * N; dof += (size_t)E * N;
+        q.D = copy(E);
+        q.out_wt = copy_t(d, E);
+        q.w1t = q.b1 = q.w2t = q.b2 = 0;
+        if (F) { q.w1t = copy_t(F, d); q.b1 = copy(F); q.w2t = copy_t(d, F); q.b2 = copy(d); }
+        q.ln_b_w = copy(d); q.ln_b_b = copy(d);
+    }
+    size_t head_o = copy_t(256, d);
+    size_t head_b_o = copy(256);
+
+    boa_model* m = new boa_model();
+    m->device = o.device;
+    m->d = d; m->nl = nl; m->N = N; m->K = K; m->E = E; m->r = r; m->ffn_mult = ffn; m->F = F; m->R2 = R2;
+    m->fingerprint = fnv1a64(buf.data(), buf.size());
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, o.device);
+    if (o.cuda_stream) {
+        m->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete m;
+            return fail(BOA_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        m->own_stream = true;
+    }
+    if (cudaMalloc(&m->weights, total * 4) != cudaSuccess ||
+        cudaMemcpy(m->weights, dev.data(), total * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        boa_free_model(m);
+        return fail(BOA_ERR_OOM, "weight upload failed");
+    }
+    float* w = m->weights;
+    m->embed = w + embed_o;
+    m->head_wt = w + head_o;
+    m->head_b = w + head_b_o;
+    m->layers.resize(nl);
+    for (int l = 0; l < nl; l++) {
+        const Off& q = lo[l];
+        DevLayer& L = m->layers[l];
+        L.ln_a_w = w + q.ln_a_w; L.ln_a_b = w + q.ln_a_b; L.in_wt = w + q.in_wt;
+        L.conv_w = w + q.conv_w; L.conv_b = w + q.conv_b; L.x_wt = w + q.x_wt;
+        L.dt_w = w + q.dt_w; L.dt_b = w + q.dt_b; L.A2 = w + q.A2; L.D = w + q.D; L.out_wt = w + q.out_wt;
+        L.w1t = F ? w + q.w1t : nullptr; L.b1 = F ? w + q.b1 : nullptr;
+        L.w2t = F ? w + q.w2t : nullptr; L.b2 = F ? w + q.b2 : nullptr;
+        L.ln_b_w = w + q.ln_b_w; L.ln_b_b = w + q.ln_b_b;
+    }
+    *out = m;
+    return BOA_OK;
+}
+
+// ------------------------------------------------------------ launchers
+
+static boa_status check_launch(boa_model* m, const char* what) {
+    m->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(BOA_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    return BOA_OK;
+}
+
+template <int EPI>
+static boa_status gemm(boa_model* m, int cls, const float* A, const float* Wt, const float* bias, float* C, long long M,
+                       int N, int K) {
+    if (M <= 0) return BOA_OK;
+    const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
+    ProfScope ps(m, cls, 2.0 * M * N * K, 4.0 * ((double)M * K + (double)K * N + (double)M * N * (resid ? 2 : 1)));
+    if (N % 4 != 0 || K % kGemmBK != 0) return fail(BOA_ERR_FORMAT, "gemm shape N=%d K=%d unsupported", N, K);
+    const long long t128 = ((M + 127) / 128) * ((N + 127) / 128);
+    const long long t12864 = ((M + 127) / 128) * ((N + 63) / 64);
+    const long long waves = 2LL * m->num_sms;
+    if (N >= 128 && t128 >= waves) {
+        dim3 grid((N + 127) / 128, (unsigned)((M + 127) / 128));
+        k_gemm_fp32<128, 128, EPI><<<grid, kGemmThreads, 0, m->stream>>>(A, Wt, bias, C, (int)M, N, K);
+    } else if (t12864 >= waves) {
+        dim3 grid((N + 63) / 64, (unsigned)((M + 127) / 128));
+        k_gemm_fp32<128, 64, EPI><<<grid, kGemmThreads, 0, m->stream>>>(A, Wt, bias, C, (int)M, N, K);
+    } else {
+        dim3 grid((N + 63) / 64, (unsigned)((M + 63) / 64));
+        k_gemm_fp32<64, 64, EPI><<<grid, kGemmThreads, 0, m->stream>>>(A, Wt, bias, C, (int)M, N, K);
+    }
+    return check_launch(m, "gemm");
+}
+
+template <int VPT>
+static void launch_embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc, const DevLayer& L0) {
+    const long long rows = (long long)S * Tc;
+    k_embed_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->stream>>>(ts, S, Tc, m->embed, L0.ln_a_w, L0.ln_a_b,
+                                                                      m->x.p, m->xn.p);
+}
+
+template <int VPT>
+static void launch_ln_ln(boa_model* m, long long rows, const DevLayer& L, const DevLayer* next) {
+    k_ln_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->stream>>>(
+        rows, m->x.p, L.ln_b_w, L.ln_b_b, next ? next->ln_a_w : nullptr, next ? next->ln_a_b : nullptr, m->xn.p);
+}
+
+static boa_status embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc) {
+    const double rows = (double)S * Tc;
+    ProfScope ps(m, BOA_KC_EMBED_LN, rows * m->d * 8.0, rows * (1.0 + 8.0 * m->d));
+    switch (m->d) {
+        case 64: launch_embed_ln<2>(m, ts, S, Tc, m->layers[0]); break;
+        case 128: launch_embed_ln<4>(m, ts, S, Tc, m->layers[0]); break;
+        case 256: launch_embed_ln<8>(m, ts, S, Tc, m->layers[0]); break;
+    }
+    return check_launch(m, "embed_ln");
+}
+
+static boa_status ln_ln(boa_model* m, long long rows, int l) {
+    const DevLayer& L = m->layers[l];
+    const DevLayer* next = (l + 1 < m->nl) ? &m->layers[l + 1] : nullptr;
+    ProfScope ps(m, BOA_KC_LN, (double)rows * m->d * (next ? 16.0 : 8.0), (double)rows * m->d * 4.0 * (next ? 3 : 2));
+    switch (m->d) {
+        case 64: launch_ln_ln<2>(m, rows, L, next); break;
+        case 128: launch_ln_ln<4>(m, rows, L, next); break;
+        case 256: launch_ln_ln<8>(m, rows, L, next); break;
+    }
+    return check_launch(m, "ln_ln");
+}
+
+static boa_status conv(boa_model* m, int l, int S, int Tc) {
+    const DevLayer& L = m->layers[l];
+    dim3 grid((m->E + 127) / 128, S);
+    float* win = m->conv.p + (size_t)l * S * (m->K - 1) * m->E;
+    const double rows = (double)S * Tc;
+    ProfScope ps(m, BOA_KC_CONV, rows * m->E * (2.0 * m->K + 4), 4.0 * (2 * rows * m->E + 2.0 * S * (m->K - 1) * m->E));
+    switch (m->K) {
+        case 2: k_conv_silu<2><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, S, Tc); break;
+        case 3: k_conv_silu<3><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, S, Tc); break;
+        case 4: k_conv_silu<4><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, S, Tc); break;
+    }
+    return check_launch(m, "conv");
+}
+
+static boa_status scan(boa_model* m, int l, int S, int Tc) {
+    const DevLayer& L = m->layers[l];
+    dim3 grid((m->E + kScanThreads - 1) / kScanThreads, S);
+    float* hs = m->h.p + (size_t)l * S * m->N * m->E;
+    const double rows = (double)S * Tc;
+    ProfScope ps(m, BOA_KC_SCAN, rows * m->E * (2.0 * m->r + 5.0 * m->N + 12),
+                 4.0 * (rows * (3.0 * m->E + m->R2) + 2.0 * S * m->N * m->E));
+#define SCAN_CASE(RR)                                                                                           \
+    case RR:                                                                                                    \
+        k_scan<16, RR><<<grid, kScanThreads, 0, m->stream>>>(m->u.p, m->xz.p, m->dbc.p, L.dt_w, L.dt_b, L.A2, L.D, \
+                                                             hs, m->yg.p, m->E, S, Tc);                         \
+        break;
+    switch (m->r) {
+        SCAN_CASE(1)
+        SCAN_CASE(2)
+        SCAN_CASE(4)
+        SCAN_CASE(8)
+        SCAN_CASE(16)
+    }
+#undef SCAN_CASE
+    return check_launch(m, "scan");
+}
+
+// The predictor over S x Tc rows: embedding, n_l blocks, head (Alg. 1).
+static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc) {
+    const long long rows = (long long)S * Tc;
+    const int d = m->d, E = m->E;
+    TRY(embed_ln(m, ts, S, Tc));
+    for (int l = 0; l < m->nl; l++) {
+        const DevLayer& L = m->layers[l];
+        TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn.p, L.in_wt, nullptr, m->xz.p, rows, 2 * E, d));
+        TRY(conv(m, l, S, Tc));
+        TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_X, m->u.p, L.x_wt, nullptr, m->dbc.p, rows, m->R2, E));
+        TRY(scan(m, l, S, Tc));
+        TRY(gemm<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg.p, L.out_wt, nullptr, m->x.p, rows, d, E));
+        if (m->F) {
+            TRY(gemm<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x.p, L.w1t, L.b1, m->hid.p, rows, m->F, d));
+            TRY(gemm<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid.p, L.w2t, L.b2, m->x.p, rows, d, m->F));
+        }
+        TRY(ln_ln(m, rows, l));
+    }
+    return gemm<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_wt, m->head_b, m->logits.p, rows, 256, d);
+}
+
+static const size_t kRowsTarget = 1u << 18;
+
+static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
+    const size_t d = m->d, E = m->E;
+    TRY(m->x.ensure(rows * d));
+    TRY(m->xn.ensure(rows * d));
+    TRY(m->xz.ensure(rows * 2 * E));
+    TRY(m->u.ensure(rows * E));
+    TRY(m->dbc.ensure(rows * m->R2));
+    TRY(m->yg.ensure(rows * E));
+    TRY(m->logits.ensure(rows * 256));
+    if (m->F) TRY(m->hid.ensure(rows * m->F));
+    TRY(m->h.ensure((size_t)m->nl * S * m->N * E));
+    TRY(m->conv.ensure((size_t)m->nl * S * (m->K - 1) * E));
+    TRY(m->st.ensure(S));
+    TRY(m->tokens.ensure(S));
+    TRY(m->flags.ensure(S));
+    TRY(m->in_off.ensure(S + 1));
+    TRY(m->out_off.ensure(S + 1));
+    TRY(m->lens.ensure(S));
+    TRY(m->sizes.ensure(S));
+    TRY(m->trace_off.ensure(S));
+    return BOA_OK;
+}
+
+// Stage the per-stream index arrays on the device and size the CDF trace.
+static boa_status upload_index(boa_model* m, size_t S, const uint64_t* in_off, const uint64_t* out_off,
+                               const uint64_t* lens) {
+    TRY(m->h_u64.ensure(4 * (S + 1)));
+    uint64_t* hb = m->h_u64.p;
+    memcpy(hb, in_off, (S + 1) * 8);
+    memcpy(hb + (S + 1), out_off, (S + 1) * 8);
+    memcpy(hb + 2 * (S + 1), lens, S * 8);
+    uint64_t* toff = hb + 3 * (S + 1);
+    uint64_t acc = 0;
+    for (size_t i = 0; i < S; i++) {
+        toff[i] = acc;
+        acc += lens[i] >= 2 ? lens[i] - 1 : 0;
+    }
+    CU(cudaMemcpyAsync(m->in_off.p, hb, (S + 1) * 8, cudaMemcpyHostToDevice, m->stream));
+    CU(cudaMemcpyAsync(m->out_off.p, hb + (S + 1), (S + 1) * 8, cudaMemcpyHostToDevice, m->stream));
+    CU(cudaMemcpyAsync(m->lens.p, hb + 2 * (S + 1), S * 8, cudaMemcpyHostToDevice, m->stream));
+    CU(cudaMemcpyAsync(m->trace_off.p, toff, S * 8, cudaMemcpyHostToDevice, m->stream));
+    m->trace_n = 0;
+    if (m->trace_on) {
+        TRY(m->trace.ensure(std::max<uint64_t>(acc, 1)));
+        m->trace_n = acc;
+    }
+    return BOA_OK;
+}
+
+static boa_status zero_state(boa_model* m, size_t S) {
+    CU(cudaMemsetAsync(m->h.p, 0, (size_t)m->nl * S * m->N * m->E * 4, m->stream));
+    CU(cudaMemsetAsync(m->conv.p, 0, (size_t)m->nl * S * (m->K - 1) * m->E * 4, m->stream));
+    return BOA_OK;
+}
+
+static boa_status compress_impl(boa_model* m, size_t S, const uint8_t* d_in, const uint64_t* in_off,
+                                uint8_t* d_out, const uint64_t* out_off, uint64_t* out_sizes) {
+    if (S == 0) return BOA_OK;
+    if (S > (1u << 30)) return fail(BOA_ERR_ARG, "too many streams");
+    std::vector<uint64_t> lens(S);
+    uint64_t maxlen = 0;
+    for (size_t i = 0; i < S; i++) {
+        if (in_off[i + 1] < in_off[i] || out_off[i + 1] < out_off[i]) return fail(BOA_ERR_ARG, "offsets must be non-decreasing");
+        lens[i] = in_off[i + 1] - in_off[i];
+        if (out_off[i + 1] - out_off[i] < boa_max_compressed_size(lens[i]))
+            return fail(BOA_ERR_OUTPUT_TOO_SMALL, "stream %zu: output slot %llu < %zu", i,
+                        (unsigned long long)(out_off[i + 1] - out_off[i]), boa_max_compressed_size(lens[i]));
+        maxlen = std::max(maxlen, lens[i]);
+    }
+    m->launches = 0;
+    m->prof_step = true;
+    const int Tc = (int)std::max<uint64_t>(1, std::min<uint64_t>(maxlen > 1 ? maxlen - 1 : 1, kRowsTarget / S));
+    TRY(ensure_workspace(m, S, S * (size_t)Tc));
+    TRY(upload_index(m, S, in_off, out_off, lens.data()));
+    TRY(zero_state(m, S));
+    const int tb = 128;
+    k_enc_init<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(d_in, m->in_off.p, m->lens.p, d_out, m->out_off.p,
+                                                                   m->st.p, (int)S);
+    TRY(check_launch(m, "enc_init"));
+    for (uint64_t t0 = 0; t0 + 1 < maxlen; t0 += Tc) {
+        const int tc = (int)std::min<uint64_t>(Tc, maxlen - 1 - t0);
+        TokenSrc ts{d_in, m->in_off.p, m->lens.p, nullptr, (long long)t0};
+        TRY(forward(m, ts, (int)S, tc));
+        EncArgs a{m->logits.p, d_in, m->in_off.p, m->lens.p, d_out, m->out_off.p, m->st.p,
+                  m->trace_on ? m->trace.p : nullptr, m->trace_off.p, (long long)t0, (int)S, tc};
+        {
+            ProfScope ps(m, BOA_KC_ENCODE, (double)S * tc * 256 * 8, (double)S * tc * (256 * 4 + 2));
+            k_encode<<<(unsigned)((S + 3) / 4), 128, 0, m->stream>>>(a);
+        }
+        TRY(check_launch(m, "encode"));
+    }
+    k_enc_finish<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(m->lens.p, d_out, m->out_off.p, m->st.p,
+                                                                     m->sizes.p, (int)S);
+    TRY(check_launch(m, "enc_finish"));
+    TRY(m->h_u32.ensure(S));
+    CU(cudaMemcpyAsync(out_sizes, m->sizes.p, S * 8, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    prof_collect(m);
+    return BOA_OK;
+}
+
+static boa_status decompress_impl(boa_model* m, size_t S, const uint8_t* d_in, const uint64_t* in_off,
+                                  const uint64_t* in_sizes, const uint64_t* lens, uint8_t* d_out,
+                                  const uint64_t* out_off) {
+    if (S == 0) return BOA_OK;
+    if (S > (1u << 30)) return fail(BOA_ERR_ARG, "too many streams");
+    uint64_t maxlen = 0;
+    std::vector<uint64_t> csz(S);
+    for (size_t i = 0; i < S; i++) {
+        if (in_off[i + 1] < in_off[i] || out_off[i + 1] < out_off[i]) return fail(BOA_ERR_ARG, "offsets must be non-decreasing");
+        csz[i] = in_sizes ? in_sizes[i] : in_off[i + 1] - in_off[i];
+        if (csz[i] > in_off[i + 1] - in_off[i]) return fail(BOA_ERR_ARG, "stream %zu: in_sizes exceeds its slot", i);
+        if (out_off[i + 1] - out_off[i] < lens[i]) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "stream %zu: output slot too small", i);
+        maxlen = std::max(maxlen, lens[i]);
+    }
+    m->launches = 0;
+    TRY(ensure_workspace(m, S, S));
+    TRY(upload_index(m, S, in_off, out_off, lens));
+    TRY(m->h_u64.ensure(S));
+    memcpy(m->h_u64.p, csz.data(), S * 8);
+    CU(cudaMemcpyAsync(m->sizes.p, m->h_u64.p, S * 8, cudaMemcpyHostToDevice, m->stream));
+    TRY(zero_state(m, S));
+    const int tb = 128;
+    k_dec_init<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(d_in, m->in_off.p, m->sizes.p, m->lens.p, d_out,
+                                                                   m->out_off.p, m->tokens.p, m->st.p, (int)S);
+    TRY(check_launch(m, "dec_init"));
+    for (uint64_t t = 0; t + 1 < maxlen; t++) {
+        m->prof_step = (t % (uint64_t)m->prof_stride) == 0;
+        TokenSrc ts{nullptr, m->in_off.p, m->lens.p, m->tokens.p, (long long)t};
+        TRY(forward(m, ts, (int)S, 1));
+        DecArgs a{m->logits.p, d_in, m->in_off.p, m->sizes.p, m->lens.p, d_out, m->out_off.p, m->tokens.p, m->st.p,
+                  m->trace_on ? m->trace.p : nullptr, m->trace_off.p, (long long)t, (int)S};
+        {
+            ProfScope ps(m, BOA_KC_DECODE, (double)S * 256 * 8, (double)S * (256 * 4 + 2));
+            k_decode<<<(unsigned)((S + 3) / 4), 128, 0, m->stream>>>(a);
+        }
+        TRY(check_launch(m, "decode"));
+    }
+    m->prof_step = true;
+    k_dec_finish<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(m->sizes.p, m->lens.p, m->st.p, m->flags.p,
+                                                                     (int)S);
+    TRY(check_launch(m, "dec_finish"));
+    TRY(m->h_u32.ensure(S));
+    CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, S * 4, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    prof_collect(m);
+    for (size_t i = 0; i < S; i++)
+        if (m->h_u32.p[i]) return fail(BOA_ERR_CORRUPT, "stream %zu did not decode cleanly (flags %u)", i, m->h_u32.p[i]);
+    return BOA_OK;
+}
+
+// ------------------------------------------------------------ public API
+
+extern "C" boa_status boa_compress_device(boa_model* m, size_t n, const uint8_t* d_in, const uint64_t* in_off,
+                                          uint8_t* d_out, const uint64_t* out_off, uint64_t* out_sizes) {
+    if (!m || (n && (!d_in || !in_off || !d_out || !out_off || !out_sizes))) return fail(BOA_ERR_ARG, "null argument");
+    CU(cudaSetDevice(m->device));
+    return compress_impl(m, n, d_in, in_off, d_out, out_off, out_sizes);
+}
+
+extern "C" boa_status boa_decompress_device(boa_model* m, size_t n, const uint8_t* d_in, const uint64_t* in_off,
+                                            const uint64_t* in_sizes, const uint64_t* lens, uint8_t* d_out,
+                                            const uint64_t* out_off) {
+    if (!m || (n && (!d_in || !in_off || !lens || !d_out || !out_off))) return fail(BOA_ERR_ARG, "null argument");
+    CU(cudaSetDevice(m->device));
+    return decompress_impl(m, n, d_in, in_off, in_sizes, lens, d_out, out_off);
+}
+
+extern "C" boa_status boa_compress(boa_model* m, size_t n, const uint8_t* const* streams, const size_t* lens,
+                                   uint8_t* const* out, const size_t* out_caps, size_t* out_sizes) {
+    if (!m || (n && (!streams || !lens || !out || !out_caps || !out_sizes))) return fail(BOA_ERR_ARG, "null argument");
+    if (n == 0) return BOA_OK;
+    CU(cudaSetDevice(m->device));
+    std::vector<uint64_t> in_off(n + 1), out_off(n + 1), sizes(n);
+    in_off[0] = out_off[0] = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (lens[i] && !streams[i]) return fail(BOA_ERR_ARG, "stream %zu is null", i);
+        if (out_caps[i] < boa_max_compressed_size(lens[i]))
+            return fail(BOA_ERR_OUTPUT_TOO_SMALL, "stream %zu: capacity %zu < %zu", i, out_caps[i], boa_max_compressed_size(lens[i]));
+        in_off[i + 1] = in_off[i] + lens[i];
+        out_off[i + 1] = out_off[i] + boa_max_compressed_size(lens[i]);
+    }
+    TRY(m->h_in.ensure(in_off[n]));
+    TRY(m->h_out.ensure(out_off[n]));
+    TRY(m->d_in.ensure(in_off[n]));
+    TRY(m->d_out.ensure(out_off[n]));
+    for (size_t i = 0; i < n; i++)
+        if (lens[i]) memcpy(m->h_in.p + in_off[i], streams[i], lens[i]);
+    CU(cudaMemcpyAsync(m->d_in.p, m->h_in.p, in_off[n], cudaMemcpyHostToDevice, m->stream));
+    TRY(compress_impl(m, n, m->d_in.p, in_off.data(), m->d_out.p, out_off.data(), sizes.data()));
+    // Pack the used part of every slot on the device, then one copy back.
+    std::vector<uint64_t> pk(n + 1, 0);
+    for (size_t i = 0; i < n; i++) pk[i + 1] = pk[i] + sizes[i];
+    TRY(m->pack_off.ensure(n + 1));
+    TRY(m->d_pack.ensure(pk[n]));
+    TRY(m->h_u64.ensure(n + 1));
+    memcpy(m->h_u64.p, pk.data(), (n + 1) * 8);
+    CU(cudaMemcpyAsync(m->pack_off.p, m->h_u64.p, (n + 1) * 8, cudaMemcpyHostToDevice, m->stream));
+    k_compact<<<(unsigned)n, 256, 0, m->stream>>>(m->d_out.p, m->out_off.p, m->pack_off.p, m->d_pack.p, (int)n);
+    TRY(check_launch(m, "compact"));
+    CU(cudaMemcpyAsync(m->h_out.p, m->d_pack.p, pk[n], cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    for (size_t i = 0; i < n; i++) {
+        out_sizes[i] = sizes[i];
+        if (sizes[i]) memcpy(out[i], m->h_out.p + pk[i], sizes[i]);
+    }
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_decompress(boa_model* m, size_t n, const uint8_t* const* bitstreams, const size_t* sizes,
+                                     const size_t* lens, uint8_t* const* out) {
+    if (!m || (n && (!bitstreams || !sizes || !lens || !out))) return fail(BOA_ERR_ARG, "null argument");
+    if (n == 0) return BOA_OK;
+    CU(cudaSetDevice(m->device));
+    std::vector<uint64_t> in_off(n + 1), out_off(n + 1), l64(n);
+    in_off[0] = out_off[0] = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (sizes[i] && !bitstreams[i]) return fail(BOA_ERR_ARG, "bitstream %zu is null", i);
+        in_off[i + 1] = in_off[i] + sizes[i];
+        out_off[i + 1] = out_off[i] + lens[i];
+        l64[i] = lens[i];
+    }
+    TRY(m->h_in.ensure(in_off[n]));
+    TRY(m->h_out.ensure(out_off[n]));
+    TRY(m->d_in.ensure(in_off[n]));
+    TRY(m->d_out.ensure(out_off[n]));
+    for (size_t i = 0; i < n; i++)
+        if (sizes[i]) memcpy(m->h_in.p + in_off[i], bitstreams[i], sizes[i]);
+    CU(cudaMemcpyAsync(m->d_in.p, m->h_in.p, in_off[n], cudaMemcpyHostToDevice, m->stream));
+    boa_status st = decompress_impl(m, n, m->d_in.p, in_off.data(), nullptr, l64.data(), m->d_out.p, out_off.data());
+    if (st != BOA_OK && st != BOA_ERR_CORRUPT) return st;
+    std::string msg = g_err;
+    CU(cudaMemcpyAsync(m->h_out.p, m->d_out.p, out_off[n], cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    for (size_t i = 0; i < n; i++)
+        if (lens[i]) memcpy(out[i], m->h_out.p + out_off[i], lens[i]);
+    if (st != BOA_OK) g_err = msg;
+    return st;
+}
+
+extern "C" boa_status boa_profile_enable(boa_model* m, int on, int stride) {
+    if (!m) return fail(BOA_ERR_ARG, "null model");
+    m->prof_on = on != 0;
+    m->prof_stride = stride > 0 ? stride : 1;
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_profile_reset(boa_model* m) {
+    if (!m) return fail(BOA_ERR_ARG, "null model");
+    for (int i = 0; i < BOA_KC_COUNT; i++) {
+        m->prof_launches[i] = 0;
+        m->prof_ms[i] = m->prof_flops[i] = m->prof_bytes[i] = 0.0;
+    }
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_profile_read(const boa_model* m, int cls, uint64_t* launches, double* total_ms,
+                                       double* flops, double* bytes) {
+    if (!m || cls < 0 || cls >= BOA_KC_COUNT) return fail(BOA_ERR_ARG, "bad argument");
+    if (launches) *launches = m->prof_launches[cls];
+    if (total_ms) *total_ms = m->prof_ms[cls];
+    if (flops) *flops = m->prof_flops[cls];
+    if (bytes) *bytes = m->prof_bytes[cls];
+    return BOA_OK;
+}
+
+// ------------------------------------------------------------ test hooks
+
+extern "C" boa_status boa_debug_encode_cdfs(size_t n_seq, const size_t* n_syms, const uint32_t* cdfs,
+                                            const uint8_t* syms, uint8_t* out, size_t out_stride, size_t* sizes) {
+    if (n_seq == 0) return BOA_OK;
+    if (!n_syms || !cdfs || !syms || !out || !sizes) return fail(BOA_ERR_ARG, "null argument");
+    std::vector<uint64_t> off(n_seq + 1, 0);
+    for (size_t i = 0; i < n_seq; i++) {
+        off[i + 1] = off[i] + n_syms[i];
+        if (out_stride < 5 * n_syms[i] + 4) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "out_stride too small");
+    }
+    const size_t rows = off[n_seq];
+    uint64_t *d_off = nullptr, *d_sizes = nullptr;
+    uint32_t *d_cdf = nullptr, *d_flags = nullptr;
+    uint8_t *d_syms = nullptr, *d_out = nullptr;
+    boa_status st = BOA_OK;
+    std::vector<uint64_t> hs(n_seq);
+    std::vector<uint32_t> hf(n_seq);
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&d_off, (n_seq + 1) * 8)) || (e = cudaMalloc(&d_sizes, n_seq * 8)) ||
+        (e = cudaMalloc(&d_cdf, std::max<size_t>(rows, 1) * 257 * 4)) || (e = cudaMalloc(&d_flags, n_seq * 4)) ||
+        (e = cudaMalloc(&d_syms, std::max<size_t>(rows, 1))) || (e = cudaMalloc(&d_out, n_seq * out_stride)) ||
+        (e = cudaMemcpy(d_off, off.data(), (n_seq + 1) * 8, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(d_cdf, cdfs, rows * 257 * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(d_syms, syms, rows, cudaMemcpyHostToDevice))) {
+        st = fail(BOA_ERR_CUDA, "debug encode setup: %s", cudaGetErrorString(e));
+    } else {
+        k_debug_encode_cdfs<<<(unsigned)((n_seq + 63) / 64), 64>>>((int)n_seq, d_off, d_cdf, d_syms, d_out, out_stride,
+                                                                  d_sizes, d_flags);
+        if ((e = cudaGetLastError()) || (e = cudaDeviceSynchronize()) ||
+            (e = cudaMemcpy(out, d_out, n_seq * out_stride, cudaMemcpyDeviceToHost)) ||
+            (e = cudaMemcpy(hs.data(), d_sizes, n_seq * 8, cudaMemcpyDeviceToHost)) ||
+            (e = cudaMemcpy(hf.data(), d_flags, n_seq * 4, cudaMemcpyDeviceToHost))) {
+            st = fail(BOA_ERR_CUDA, "debug encode: %s", cudaGetErrorString(e));
+        } else {
+            for (size_t i = 0; i < n_seq; i++) {
+                sizes[i] = hs[i];
+                if (hf[i]) st = fail(BOA_ERR_OUTPUT_TOO_SMALL, "sequence %zu flags %u", i, hf[i]);
+            }
+        }
+    }
+    cudaFree(d_off); cudaFree(d_sizes); cudaFree(d_cdf); cudaFree(d_flags); cudaFree(d_syms); cudaFree(d_out);
+    return st;
+}
+
+extern "C" boa_status boa_debug_decode_cdfs(size_t n_seq, const size_t* n_syms, const uint32_t* cdfs,
+                                            const uint8_t* in, size_t in_stride, const size_t* in_sizes,
+                                            uint8_t* syms) {
+    if (n_seq == 0) return BOA_OK;
+    if (!n_syms || !cdfs || !in || !in_sizes || !syms) return fail(BOA_ERR_ARG, "null argument");
+    std::vector<uint64_t> off(n_seq + 1, 0), isz(n_seq);
+    for (size_t i = 0; i < n_seq; i++) {
+        off[i + 1] = off[i] + n_syms[i];
+        isz[i] = in_sizes[i];
+        if (in_sizes[i] > in_stride) return fail(BOA_ERR_ARG, "in_sizes[%zu] > in_stride", i);
+    }
+    const size_t rows = off[n_seq];
+    uint64_t *d_off = nullptr, *d_isz = nullptr;
+    uint32_t *d_cdf = nullptr, *d_flags = nullptr;
+    uint8_t *d_syms = nullptr, *d_in = nullptr;
+    boa_status st = BOA_OK;
+    std::vector<uint32_t> hf(n_seq);
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&d_off, (n_seq + 1) * 8)) || (e = cudaMalloc(&d_isz, n_seq * 8)) ||
+        (e = cudaMalloc(&d_cdf, std::max<size_t>(rows, 1) * 257 * 4)) || (e = cudaMalloc(&d_flags, n_seq * 4)) ||
+        (e = cudaMalloc(&d_syms, std::max<size_t>(rows, 1))) || (e = cudaMalloc(&d_in, std::max<size_t>(n_seq * in_stride, 1))) ||
+        (e = cudaMemcpy(d_off, off.data(), (n_seq + 1) * 8, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(d_isz, isz.data(), n_seq * 8, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(d_cdf, cdfs, rows * 257 * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(d_in, in, n_seq * in_stride, cudaMemcpyHostToDevice))) {
+        st = fail(BOA_ERR_CUDA, "debug decode setup: %s", cudaGetErrorString(e));
+    } else {
+        k_debug_decode_cdfs<<<(unsigned)((n_seq + 3) / 4), 128>>>((int)n_seq, d_off, d_cdf, d_in, in_stride, d_isz,
+                                                                  d_syms, d_flags);
+        if ((e = cudaGetLastError()) || (e = cudaDeviceSynchronize()) ||
+            (e = cudaMemcpy(syms, d_syms, rows, cudaMemcpyDeviceToHost)) ||
+            (e = cudaMemcpy(hf.data(), d_flags, n_seq * 4, cudaMemcpyDeviceToHost))) {
+            st = fail(BOA_ERR_CUDA, "debug decode: %s", cudaGetErrorString(e));
+        } else {
+            for (size_t i = 0; i < n_seq; i++)
+                if (hf[i]) st = fail(BOA_ERR_CORRUPT, "sequence %zu flags %u", i, hf[i]);
+        }
+    }
+    cudaFree(d_off); cudaFree(d_isz); cudaFree(d_cdf); cudaFree(d_flags); cudaFree(d_syms); cudaFree(d_in);
+    return st;
+}
+
+extern "C" boa_status boa_debug_quantise(size_t n_rows, const float* p, uint32_t* f) {
+    if (n_rows == 0) return BOA_OK;
+    if (!p || !f) return fail(BOA_ERR_ARG, "null argument");
+    float* d_p = nullptr;
+    uint32_t* d_f = nullptr;
+    boa_status st = BOA_OK;
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&d_p, n_rows * 1024)) || (e = cudaMalloc(&d_f, n_rows * 1024)) ||
+        (e = cudaMemcpy(d_p, p, n_rows * 1024, cudaMemcpyHostToDevice))) {
+        st = fail(BOA_ERR_CUDA, "debug quantise setup: %s", cudaGetErrorString(e));
+    } else {
+        k_debug_quantise<<<(unsigned)((n_rows + 7) / 8), 256>>>(d_p, d_f, (long long)n_rows);
+        if ((e = cudaGetLastError()) || (e = cudaDeviceSynchronize()) ||
+            (e = cudaMemcpy(f, d_f, n_rows * 1024, cudaMemcpyDeviceToHost)))
+            st = fail(BOA_ERR_CUDA, "debug quantise: %s", cudaGetErrorString(e));
+    }
+    cudaFree(d_p); cudaFree(d_f);
+    return st;
+}
+
+extern "C" boa_status boa_debug_logprobs(boa_model* m, const uint8_t* stream, size_t len, float* out) {
+    if (!m || (len && (!stream || !out))) return fail(BOA_ERR_ARG, "null argument");
+    if (len < 2) return BOA_OK;
+    CU(cudaSetDevice(m->device));
+    const size_t T = len - 1;
+    const int Tc = (int)std::min<size_t>(T, kRowsTarget);
+    TRY(ensure_workspace(m, 1, Tc));
+    TRY(m->d_in.ensure(len));
+    DevBuf<float> lp;
+    TRY(lp.ensure(T * 256));
+    uint64_t off[2] = {0, len}, lens1[1] = {len};
+    TRY(upload_index(m, 1, off, off, lens1));
+    TRY(zero_state(m, 1));
+    boa_status st = BOA_OK;
+    cudaError_t e = cudaMemcpyAsync(m->d_in.p, stream, len, cudaMemcpyHostToDevice, m->stream);
+    if (e != cudaSuccess) st = fail(BOA_ERR_CUDA, "%s", cudaGetErrorString(e));
+    for (size_t t0 = 0; st == BOA_OK && t0 < T; t0 += Tc) {
+        const int tc = (int)std::min<size_t>(Tc, T - t0);
+        TokenSrc ts{m->d_in.p, m->in_off.p, m->lens.p, nullptr, (long long)t0};
+        st = forward(m, ts, 1, tc);
+        if (st == BOA_OK) {
+            k_log2_softmax<<<(unsigned)((tc + 7) / 8), 256, 0, m->stream>>>(m->logits.p, lp.p + t0 * 256, tc);
+            st = check_launch(m, "log2_softmax");
+        }
+    }
+    if (st == BOA_OK) {
+        e = cudaMemcpyAsync(out, lp.p, T * 256 * 4, cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) st = fail(BOA_ERR_CUDA, "%s", cudaGetErrorString(e));
+    }
+    cudaStreamSynchronize(m->stream);
+    lp.release();
+    return st;
+}
+
+extern "C" boa_status boa_debug_enable_cdf_trace(boa_model* m, int on) {
+    if (!m) return fail(BOA_ERR_ARG, "null model");
+    m->trace_on = on != 0;
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_debug_read_cdf_trace(boa_model* m, uint64_t* out, size_t n) {
+    if (!m || (n && !out)) return fail(BOA_ERR_ARG, "null argument");
+    if (n > m->trace_n) return fail(BOA_ERR_ARG, "trace holds %zu entries, asked for %zu", m->trace_n, n);
+    if (n == 0) return BOA_OK;
+    CU(cudaSetDevice(m->device));
+    CU(cudaMemcpyAsync(out, m->trace.p, n * 8, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    return BOA_OK;
+}

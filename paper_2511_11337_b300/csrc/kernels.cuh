@@ -1,0 +1,655 @@
+// Per-row and per-stream kernels of the BOA hot path (everything but the GEMMs).
+//
+// Row layout: a batch of rows is S streams x Tc consecutive steps, row index
+// s * Tc + tau.  Compression runs Tc > 1 (teacher forcing over a time
+// chunk); decompression runs Tc = 1 (one step of every stream).  Kernels that
+// carry state along time (conv window, SSM state, coder) loop over tau inside
+// one thread or warp, so results never depend on Tc.
+#pragma once
+#include "common.cuh"
+
+namespace boa {
+
+// ---------------------------------------------------------------- LayerNorm
+
+// (x - mean) / sqrt(var + 1e-5) * g + b over d features, one warp per row,
+// fixed butterfly reductions (identical in every lane and every launch).
+template <int VPT>
+__device__ __forceinline__ void warp_layernorm(const float (&x)[VPT], const float* __restrict__ g,
+                                               const float* __restrict__ b, int lane, float (&y)[VPT]) {
+    constexpr int d = VPT * 32;
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < VPT; i++) s = __fadd_rn(s, x[i]);
+    const float mean = __fdiv_rn(warp_sum(s), (float)d);
+    float v = 0.f;
+#pragma unroll
+    for (int i = 0; i < VPT; i++) {
+        float c = __fsub_rn(x[i], mean);
+        v = __fmaf_rn(c, c, v);
+    }
+    const float var = __fdiv_rn(warp_sum(v), (float)d);
+    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(__fadd_rn(var, 1e-5f)));
+#pragma unroll
+    for (int i = 0; i < VPT; i++) {
+        int k = lane + 32 * i;
+        y[i] = __fadd_rn(__fmul_rn(__fmul_rn(__fsub_rn(x[i], mean), inv), g[k]), b[k]);
+    }
+}
+
+// Token source for a row: compression reads the stream bytes, decompression
+// the token array holding each stream's last decoded byte.
+struct TokenSrc {
+    const uint8_t* data;      // packed stream bytes (compression) or nullptr
+    const uint64_t* offsets;  // [S+1]
+    const uint64_t* lens;     // [S]
+    const uint8_t* tokens;    // [S] (decompression)
+    long long t0;             // first step of the chunk
+};
+
+__device__ __forceinline__ int row_token(const TokenSrc& ts, int s, int tau) {
+    if (ts.tokens) return ts.tokens[s];
+    long long t = ts.t0 + tau;
+    return (t + 1 < (long long)ts.lens[s]) ? ts.data[ts.offsets[s] + t] : 0;
+}
+
+// x = embed[token]; xn = LN_a(x)   (Alg. 1: ByteEmbed, then the first block's norm)
+template <int VPT>
+__global__ void k_embed_ln(TokenSrc ts, int S, int Tc, const float* __restrict__ embed,
+                           const float* __restrict__ g, const float* __restrict__ b,
+                           float* __restrict__ x, float* __restrict__ xn) {
+    constexpr int d = VPT * 32;
+    const int lane = threadIdx.x & 31;
+    const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= (long long)S * Tc) return;
+    const int s = (int)(row / Tc), tau = (int)(row % Tc);
+    const int tok = row_token(ts, s, tau);
+    float v[VPT], y[VPT];
+#pragma unroll
+    for (int i = 0; i < VPT; i++) v[i] = embed[(size_t)tok * d + lane + 32 * i];
+    warp_layernorm<VPT>(v, g, b, lane, y);
+#pragma unroll
+    for (int i = 0; i < VPT; i++) {
+        x[(size_t)row * d + lane + 32 * i] = v[i];
+        xn[(size_t)row * d + lane + 32 * i] = y[i];
+    }
+}
+
+// x = LN_b(x); then, when another block follows, xn = LN_a'(x).
+template <int VPT>
+__global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __restrict__ gb,
+                        const float* __restrict__ bb, const float* __restrict__ ga,
+                        const float* __restrict__ ba, float* __restrict__ xn) {
+    constexpr int d = VPT * 32;
+    const int lane = threadIdx.x & 31;
+    const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= rows) return;
+    float v[VPT], y[VPT];
+#pragma unroll
+    for (int i = 0; i < VPT; i++) v[i] = x[(size_t)row * d + lane + 32 * i];
+    warp_layernorm<VPT>(v, gb, bb, lane, y);
+#pragma unroll
+    for (int i = 0; i < VPT; i++) x[(size_t)row * d + lane + 32 * i] = y[i];
+    if (ga) {
+        float z[VPT];
+        warp_layernorm<VPT>(y, ga, ba, lane, z);
+#pragma unroll
+        for (int i = 0; i < VPT; i++) xn[(size_t)row * d + lane + 32 * i] = z[i];
+    }
+}
+
+// ---------------------------------------------------- causal conv1d + SiLU
+
+// u[s, t, c] = SiLU(b_c + sum_k w[c][k] xi[s, t-K+1+k, c]); the last K-1
+// inputs of every (stream, channel) persist in win[S][K-1][E] across calls.
+template <int K>
+__global__ void k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ w,
+                            const float* __restrict__ bconv, float* __restrict__ win,
+                            float* __restrict__ u, int S, int Tc) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (c >= E) return;
+    float wv[K], h[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) wv[k] = w[(size_t)c * K + k];
+#pragma unroll
+    for (int k = 0; k < K - 1; k++) h[k] = win[((size_t)s * (K - 1) + k) * E + c];
+    const float bc = bconv[c];
+    for (int tau = 0; tau < Tc; tau++) {
+        const size_t row = (size_t)s * Tc + tau;
+        const float xi = xz[row * 2 * E + c];
+        float acc = bc;
+#pragma unroll
+        for (int k = 0; k < K - 1; k++) acc = __fmaf_rn(wv[k], h[k], acc);
+        acc = __fmaf_rn(wv[K - 1], xi, acc);
+#pragma unroll
+        for (int k = 0; k + 1 < K - 1; k++) h[k] = h[k + 1];
+        h[K - 2] = xi;
+        u[row * E + c] = silu_f(acc);
+    }
+#pragma unroll
+    for (int k = 0; k < K - 1; k++) win[((size_t)s * (K - 1) + k) * E + c] = h[k];
+}
+
+// --------------------------------------- dt_proj + softplus + selective scan
+
+// One thread per (stream, channel) walks the chunk's steps (App. A):
+//   Delta = softplus(W_dt . delta + b_dt)
+//   h[n]  = exp(Delta A[n]) h[n] + (Delta u) B[n]
+//   y     = sum_n C[n] h[n] + D u ;   out = y * SiLU(z)
+// h lives in registers for the chunk and in hstate[S][N][E] between chunks.
+// A2 = A * log2(e), so exp(Delta A) = 2^(Delta A2).
+constexpr int kScanThreads = 128;
+constexpr int kScanRowsSmem = 32;
+
+template <int NS, int R>
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* __restrict__ dbc,
+       const float* __restrict__ dt_w, const float* __restrict__ dt_b, const float* __restrict__ A2,
+       const float* __restrict__ Dv, float* __restrict__ hstate, float* __restrict__ yg,
+       int E, int S, int Tc) {
+    constexpr int W = R + 2 * NS;   // dbc row width
+    __shared__ float sm[kScanRowsSmem][W];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    const bool live = c < E;
+    float h[NS], a2[NS], wdt[R];
+    float bdt = 0.f, dv = 0.f;
+    if (live) {
+#pragma unroll
+        for (int n = 0; n < NS; n++) {
+            h[n] = hstate[((size_t)s * NS + n) * E + c];
+            a2[n] = A2[(size_t)c * NS + n];
+        }
+#pragma unroll
+        for (int j = 0; j < R; j++) wdt[j] = dt_w[(size_t)c * R + j];
+        bdt = dt_b[c];
+        dv = Dv[c];
+    }
+    for (int t0 = 0; t0 < Tc; t0 += kScanRowsSmem) {
+        const int nr = min(kScanRowsSmem, Tc - t0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
+            int rr = i / W, j = i % W;
+            sm[rr][j] = dbc[((size_t)s * Tc + t0 + rr) * W + j];
+        }
+        __syncthreads();
+        if (!live) continue;
+        for (int rr = 0; rr < nr; rr++) {
+            const size_t row = (size_t)s * Tc + t0 + rr;
+            float pre = 0.f;
+#pragma unroll
+            for (int j = 0; j < R; j++) pre = __fmaf_rn(wdt[j], sm[rr][j], pre);
+            const float delta = softplus_f(__fadd_rn(pre, bdt));
+            const float uc = u[row * E + c];
+            const float du = __fmul_rn(delta, uc);
+            float y = 0.f;
+#pragma unroll
+            for (int n = 0; n < NS; n++) {
+                const float da = ex2_approx(__fmul_rn(delta, a2[n]));
+                h[n] = __fmaf_rn(da, h[n], __fmul_rn(du, sm[rr][R + n]));
+                y = __fmaf_rn(sm[rr][R + NS + n], h[n], y);
+            }
+            y = __fmaf_rn(dv, uc, y);
+            const float z = xz[row * 2 * E + E + c];
+            yg[row * E + c] = __fmul_rn(y, silu_f(z));
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int n = 0; n < NS; n++) hstate[((size_t)s * NS + n) * E + c] = h[n];
+    }
+}
+
+// ------------------------------------ softmax -> integer histogram -> CDF
+
+// Lane l owns symbols 8l .. 8l+7.  Result: f[8] (the lane's frequencies) and
+// cbase = C(8l), the exclusive prefix of the histogram at the lane's first
+// symbol.  Paper "Probabilities and integer CDF": f_a >= 1, sum f = 2^16.
+__device__ __forceinline__ void warp_quantise_p(float (&p)[8], int lane, uint32_t (&f)[8], uint32_t& cbase) {
+    float best = -1.0f;
+    int best_idx = 0;
+    uint32_t lsum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        float q = p[j];
+        if (!(q >= 0.0f)) q = 0.0f;     // NaN or negative -> 0
+        if (q > 1.0f) q = 1.0f;
+        p[j] = q;
+        if (q > best) { best = q; best_idx = lane * 8 + j; }
+        uint32_t fj = 1u + (uint32_t)floorf(__fmul_rn(q, (float)kQuantScale));
+        f[j] = fj;
+        lsum += fj;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, best_idx, o);
+        if (ob > best || (ob == best && oi < best_idx)) { best = ob; best_idx = oi; }
+    }
+    const uint32_t total = warp_sum_u32(lsum);
+    const int rem = (int)kM - (int)total;            // signed remainder to the argmax
+    uint32_t mine = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        if (best_idx == lane * 8 + j) f[j] = (uint32_t)((int)f[j] + rem);
+        mine += f[j];
+    }
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    cbase = incl - mine;
+}
+
+// Softmax of one 256-logit row (paper, "Probabilities and integer CDF"),
+// then the quantiser above.
+__device__ __forceinline__ void warp_logits_to_hist(const float* __restrict__ lrow, int lane, uint32_t (&f)[8],
+                                                    uint32_t& cbase) {
+    const float4 v0 = reinterpret_cast<const float4*>(lrow)[lane * 2];
+    const float4 v1 = reinterpret_cast<const float4*>(lrow)[lane * 2 + 1];
+    float l[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    float m = l[0];
+#pragma unroll
+    for (int j = 1; j < 8; j++) m = fmaxf(m, l[j]);
+    m = warp_max(m);
+    float e[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) e[j] = expf(__fsub_rn(l[j], m));
+    float s = __fadd_rn(__fadd_rn(__fadd_rn(e[0], e[1]), __fadd_rn(e[2], e[3])),
+                        __fadd_rn(__fadd_rn(e[4], e[5]), __fadd_rn(e[6], e[7])));
+    s = warp_sum(s);
+    float p[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) p[j] = __fdiv_rn(e[j], s);
+    warp_quantise_p(p, lane, f, cbase);
+}
+
+// 64-bit hash of the 256 frequencies (test trace of the CDF each step used).
+__device__ __forceinline__ uint64_t warp_hist_hash(const uint32_t (&f)[8], int lane) {
+    uint64_t h = 1469598103934665603ull;
+#pragma unroll
+    for (int j = 0; j < 8; j++) { h ^= f[j]; h *= 1099511628211ull; }
+    uint64_t w = 0x9E3779B97F4A7C15ull;
+    uint64_t pw = 1;
+    for (int i = 0; i <= lane; i++) pw *= w;
+    return warp_sum_u64(h * pw);
+}
+
+// C(sym) and f(sym) for a symbol owned by lane sym/8, broadcast to all lanes.
+__device__ __forceinline__ void warp_sym_range(const uint32_t (&f)[8], uint32_t cbase, int sym, int lane,
+                                               uint32_t& c_lo, uint32_t& freq) {
+    uint32_t cl = cbase, fr = 0;
+    const int j0 = sym & 7;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        if (j < j0) cl += f[j];
+        if (j == j0) fr = f[j];
+    }
+    c_lo = __shfl_sync(0xffffffffu, cl, sym >> 3);
+    freq = __shfl_sync(0xffffffffu, fr, sym >> 3);
+}
+
+// ------------------------------------------------------------ range coder
+
+// Encoder update and renormalisation (paper, paragraph "Encoder"), with the
+// straddle rule for R < 2^16 and no modulo on R.
+__device__ __forceinline__ void rc_encode(CoderState& st, uint32_t c_lo, uint32_t freq, uint8_t* out,
+                                          uint64_t cap) {
+    uint64_t L = st.L, R = st.R, pos = st.pos;
+    L = L + ((R * c_lo) >> kProbBits);
+    R = (R * freq) >> kProbBits;
+    int it = 0;
+    for (; it < 16; it++) {
+        if ((L >> 24) == ((L + R - 1) >> 24)) {
+            if (pos < cap) out[pos] = (uint8_t)(L >> 24); else st.flags |= kFlagOverflow;
+            pos++;
+            L = (L << 8) & kMask32;
+            R = R << 8;
+        } else if (R < kBot) {
+            R = kBot - (L & (kBot - 1));
+        } else {
+            break;
+        }
+    }
+    if (it == 16) st.flags |= kFlagLoop;
+    st.L = L; st.R = R; st.pos = pos;
+}
+
+__device__ __forceinline__ void rc_flush(CoderState& st, uint8_t* out, uint64_t cap) {
+    for (int i = 3; i >= 0; i--) {
+        if (st.pos < cap) out[st.pos] = (uint8_t)(st.L >> (8 * i)); else st.flags |= kFlagOverflow;
+        st.pos++;
+    }
+}
+
+__device__ __forceinline__ uint8_t rc_read(CoderState& st, const uint8_t* in, uint64_t size) {
+    uint8_t b = 0;
+    if (st.pos < size) b = in[st.pos]; else st.flags |= kFlagCorrupt;
+    st.pos++;
+    return b;
+}
+
+__device__ __forceinline__ void rc_decoder_init(CoderState& st, const uint8_t* in, uint64_t size) {
+    st.L = 0; st.R = 1ull << 32; st.C = 0; st.pos = 0; st.flags = 0;
+    for (int i = 0; i < 4; i++) st.C = (st.C << 8) | rc_read(st, in, size);
+}
+
+// Decoder target x = floor(((C - L + 1) M - 1) / R)  (paragraph "Decoder").
+__device__ __forceinline__ uint32_t rc_target(CoderState& st) {
+    if (st.C < st.L || st.C - st.L >= st.R) {   // impossible on a valid stream
+        st.flags |= kFlagCorrupt;
+        st.C = st.L;
+    }
+    return (uint32_t)((((st.C - st.L + 1) << kProbBits) - 1) / st.R);
+}
+
+__device__ __forceinline__ void rc_decode_update(CoderState& st, uint32_t c_lo, uint32_t freq, const uint8_t* in,
+                                                 uint64_t size) {
+    uint64_t L = st.L, R = st.R;
+    L = L + ((R * c_lo) >> kProbBits);
+    R = (R * freq) >> kProbBits;
+    int it = 0;
+    for (; it < 16; it++) {
+        if ((L >> 24) == ((L + R - 1) >> 24)) {
+            L = (L << 8) & kMask32;
+            R = R << 8;
+            st.C = ((st.C << 8) | rc_read(st, in, size)) & kMask32;
+        } else if (R < kBot) {
+            R = kBot - (L & (kBot - 1));
+        } else {
+            break;
+        }
+    }
+    if (it == 16) st.flags |= kFlagLoop;
+    st.L = L; st.R = R;
+}
+
+// Symbol search: the lane whose range [C(8l), C(8l+8)) holds x is found by a
+// ballot, then a rank search over its 8 cumulative counts.
+__device__ __forceinline__ void warp_find_symbol(const uint32_t (&f)[8], uint32_t cbase, uint32_t x, int lane,
+                                                 int& sym, uint32_t& c_lo, uint32_t& freq) {
+    uint32_t mine = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) mine += f[j];
+    const unsigned hit = __ballot_sync(0xffffffffu, cbase <= x && x < cbase + mine);
+    const int owner = hit ? __ffs(hit) - 1 : 31;
+    uint32_t cum = cbase, cl = cbase, fr = f[0];
+    int j_hit = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        if (cum <= x) { j_hit = j; cl = cum; fr = f[j]; }
+        cum += f[j];
+    }
+    sym = __shfl_sync(0xffffffffu, lane * 8 + j_hit, owner);
+    c_lo = __shfl_sync(0xffffffffu, cl, owner);
+    freq = __shfl_sync(0xffffffffu, fr, owner);
+}
+
+// ------------------------------------------------------- coder kernels
+
+struct EncArgs {
+    const float* logits;        // [S*Tc][256]
+    const uint8_t* data;        // packed input
+    const uint64_t* in_off;     // [S+1]
+    const uint64_t* lens;       // [S]
+    uint8_t* out;               // packed output
+    const uint64_t* out_off;    // [S+1]
+    CoderState* st;             // [S]
+    uint64_t* trace;            // [sum(len-1)] or nullptr
+    const uint64_t* trace_off;  // [S]
+    long long t0;
+    int S, Tc;
+};
+
+// One warp per stream: for every step of the chunk, softmax -> histogram ->
+// encode the true next byte (paper "Encoder"; first byte stored raw).
+__global__ void k_encode(EncArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (s >= a.S) return;
+    const long long len = (long long)a.lens[s];
+    if (len < 2) return;
+    CoderState st;
+    if (lane == 0) st = a.st[s];
+    uint8_t* out = a.out + a.out_off[s] + 1;
+    const uint64_t cap = a.out_off[s + 1] - a.out_off[s] - 1;
+    const uint8_t* in = a.data + a.in_off[s];
+    for (int tau = 0; tau < a.Tc; tau++) {
+        const long long t = a.t0 + tau;
+        if (t + 1 >= len) break;
+        uint32_t f[8], cbase;
+        warp_logits_to_hist(a.logits + ((size_t)s * a.Tc + tau) * 256, lane, f, cbase);
+        if (a.trace) {
+            uint64_t hsh = warp_hist_hash(f, lane);
+            if (lane == 0) a.trace[a.trace_off[s] + t] = hsh;
+        }
+        const int sym = in[t + 1];
+        uint32_t c_lo, freq;
+        warp_sym_range(f, cbase, sym, lane, c_lo, freq);
+        if (lane == 0) rc_encode(st, c_lo, freq, out, cap);
+    }
+    if (lane == 0) a.st[s] = st;
+}
+
+struct DecArgs {
+    const float* logits;        // [S][256]
+    const uint8_t* cin;         // packed coded input
+    const uint64_t* cin_off;    // [S+1] slot offsets
+    const uint64_t* cin_size;   // [S] coded bytes at the start of each slot
+    const uint64_t* lens;       // [S] decoded lengths
+    uint8_t* out;               // packed output
+    const uint64_t* out_off;    // [S+1]
+    uint8_t* tokens;            // [S] next-step input byte
+    CoderState* st;
+    uint64_t* trace;
+    const uint64_t* trace_off;
+    long long t;                // step: this call decodes byte t+1
+    int S;
+};
+
+// One warp per stream, one step: softmax -> histogram -> decode byte t+1,
+// feed it back as the next step's input; finished streams are masked.
+__global__ void k_decode(DecArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (s >= a.S) return;
+    const long long len = (long long)a.lens[s];
+    if (a.t + 1 >= len) return;
+    uint32_t f[8], cbase;
+    warp_logits_to_hist(a.logits + (size_t)s * 256, lane, f, cbase);
+    if (a.trace) {
+        uint64_t hsh = warp_hist_hash(f, lane);
+        if (lane == 0) a.trace[a.trace_off[s] + a.t] = hsh;
+    }
+    const uint8_t* in = a.cin + a.cin_off[s] + 1;
+    const uint64_t size = a.cin_size[s] - 1;
+    CoderState st;
+    uint32_t x = 0;
+    if (lane == 0) {
+        st = a.st[s];
+        x = rc_target(st);
+    }
+    x = __shfl_sync(0xffffffffu, x, 0);
+    int sym;
+    uint32_t c_lo, freq;
+    warp_find_symbol(f, cbase, x, lane, sym, c_lo, freq);
+    if (lane == 0) {
+        rc_decode_update(st, c_lo, freq, in, size);
+        a.st[s] = st;
+        a.out[a.out_off[s] + a.t + 1] = (uint8_t)sym;
+        a.tokens[s] = (uint8_t)sym;
+    }
+}
+
+// Coder set-up: encoder state, raw first byte copied through.
+__global__ void k_enc_init(const uint8_t* data, const uint64_t* in_off, const uint64_t* lens, uint8_t* out,
+                           const uint64_t* out_off, CoderState* st, int S) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    CoderState c;
+    c.L = 0; c.R = 1ull << 32; c.C = 0; c.pos = 0; c.flags = 0; c.pad = 0;
+    if (lens[s] >= 1) {
+        if (out_off[s + 1] > out_off[s]) out[out_off[s]] = data[in_off[s]];
+        else c.flags |= kFlagOverflow;
+    }
+    st[s] = c;
+}
+
+__global__ void k_enc_finish(const uint64_t* lens, uint8_t* out, const uint64_t* out_off, CoderState* st,
+                             uint64_t* sizes, int S) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    CoderState c = st[s];
+    uint64_t size = lens[s] == 0 ? 0 : 1;
+    if (lens[s] >= 2) {
+        uint64_t cap = out_off[s + 1] - out_off[s] - 1;
+        rc_flush(c, out + out_off[s] + 1, cap);
+        size = 1 + c.pos;
+    }
+    st[s] = c;
+    sizes[s] = size;
+}
+
+// Decoder set-up: raw first byte to output and token; code value from the
+// first 4 coded bytes.
+__global__ void k_dec_init(const uint8_t* cin, const uint64_t* cin_off, const uint64_t* cin_size,
+                           const uint64_t* lens, uint8_t* out, const uint64_t* out_off, uint8_t* tokens,
+                           CoderState* st, int S) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    CoderState c;
+    c.L = 0; c.R = 1ull << 32; c.C = 0; c.pos = 0; c.flags = 0; c.pad = 0;
+    const uint64_t size = cin_size[s];
+    tokens[s] = 0;
+    if (lens[s] >= 1) {
+        if (size >= 1) {
+            out[out_off[s]] = cin[cin_off[s]];
+            tokens[s] = cin[cin_off[s]];
+        } else {
+            c.flags |= kFlagCorrupt;
+        }
+    }
+    if (lens[s] >= 2) {
+        rc_decoder_init(c, cin + cin_off[s] + 1, size >= 1 ? size - 1 : 0);
+    } else if (size != (lens[s] == 0 ? 0u : 1u)) {
+        c.flags |= kFlagCorrupt;
+    }
+    st[s] = c;
+}
+
+// Decoder wrap-up: every coded byte must have been consumed exactly.
+__global__ void k_dec_finish(const uint64_t* cin_size, const uint64_t* lens, CoderState* st, uint32_t* flags_out,
+                             int S) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    CoderState c = st[s];
+    uint32_t fl = c.flags;
+    if (lens[s] >= 2) {
+        const uint64_t size = cin_size[s];
+        if (c.pos != size - 1) fl |= kFlagCorrupt;
+    }
+    flags_out[s] = fl;
+}
+
+// Gather each stream's used bytes from its output slot into one packed buffer.
+__global__ void k_compact(const uint8_t* __restrict__ src, const uint64_t* __restrict__ src_off,
+                          const uint64_t* __restrict__ dst_off, uint8_t* __restrict__ dst, int S) {
+    const int s = blockIdx.x;
+    if (s >= S) return;
+    const uint64_t n = dst_off[s + 1] - dst_off[s];
+    const uint8_t* a = src + src_off[s];
+    uint8_t* b = dst + dst_off[s];
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) b[i] = a[i];
+}
+
+// log2 p rows for tests: (l - m - ln Z) / ln 2.
+__global__ void k_log2_softmax(const float* __restrict__ logits, float* __restrict__ out, long long rows) {
+    const int lane = threadIdx.x & 31;
+    const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= rows) return;
+    const float* l = logits + row * 256;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = l[lane * 8 + j];
+    float m = v[0];
+#pragma unroll
+    for (int j = 1; j < 8; j++) m = fmaxf(m, v[j]);
+    m = warp_max(m);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; j++) s = __fadd_rn(s, expf(__fsub_rn(v[j], m)));
+    s = warp_sum(s);
+    const float lz = logf(s);
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        out[row * 256 + lane * 8 + j] = __fmul_rn(__fsub_rn(__fsub_rn(v[j], m), lz), 1.4426950408889634f);
+}
+
+// ------------------------------------------- CDF-driven coder test kernels
+
+// One warp per sequence; the CDF rows come from the caller.
+__global__ void k_debug_encode_cdfs(int n_seq, const uint64_t* sym_off, const uint32_t* cdfs, const uint8_t* syms,
+                                    uint8_t* out, uint64_t out_stride, uint64_t* sizes, uint32_t* flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_seq) return;
+    CoderState st;
+    st.L = 0; st.R = 1ull << 32; st.C = 0; st.pos = 0; st.flags = 0; st.pad = 0;
+    uint8_t* o = out + (size_t)i * out_stride;
+    for (uint64_t t = sym_off[i]; t < sym_off[i + 1]; t++) {
+        const uint32_t* c = cdfs + t * 257;
+        const int s = syms[t];
+        rc_encode(st, c[s], c[s + 1] - c[s], o, out_stride);
+    }
+    rc_flush(st, o, out_stride);
+    sizes[i] = st.pos;
+    flags[i] = st.flags;
+}
+
+__global__ void k_debug_decode_cdfs(int n_seq, const uint64_t* sym_off, const uint32_t* cdfs, const uint8_t* in,
+                                    uint64_t in_stride, const uint64_t* in_sizes, uint8_t* syms, uint32_t* flags) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (i >= n_seq) return;
+    const uint8_t* src = in + (size_t)i * in_stride;
+    CoderState st;
+    if (lane == 0) rc_decoder_init(st, src, in_sizes[i]);
+    for (uint64_t t = sym_off[i]; t < sym_off[i + 1]; t++) {
+        const uint32_t* c = cdfs + t * 257;
+        uint32_t f[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) f[j] = c[lane * 8 + j + 1] - c[lane * 8 + j];
+        const uint32_t cbase = c[lane * 8];
+        uint32_t x = 0;
+        if (lane == 0) x = rc_target(st);
+        x = __shfl_sync(0xffffffffu, x, 0);
+        int sym;
+        uint32_t c_lo, freq;
+        warp_find_symbol(f, cbase, x, lane, sym, c_lo, freq);
+        if (lane == 0) {
+            rc_decode_update(st, c_lo, freq, src, in_sizes[i]);
+            syms[t] = (uint8_t)sym;
+        }
+    }
+    if (lane == 0) {
+        if (st.pos != in_sizes[i]) st.flags |= kFlagCorrupt;
+        flags[i] = st.flags;
+    }
+}
+
+__global__ void k_debug_quantise(const float* __restrict__ p, uint32_t* __restrict__ f_out, long long rows) {
+    const int lane = threadIdx.x & 31;
+    const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= rows) return;
+    float q[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) q[j] = p[row * 256 + lane * 8 + j];
+    uint32_t f[8], cbase;
+    warp_quantise_p(q, lane, f, cbase);
+#pragma unroll
+    for (int j = 0; j < 8; j++) f_out[row * 256 + lane * 8 + j] = f[j];
+}
+
+}  // namespace boa

@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every symbol include/boa.h declares
+(no GPU calls here), and the host-side logic that needs no device behaves."""
+import os
+import re
+
+import pytest
+
+from paper_2511_11337_b300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "boa.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(boa_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_builds_and_loads():
+    build.build()
+    lib = _lib.load()
+    assert lib is not None
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    lib = _lib.load()
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(lib, s), s
+        assert s in _lib.SIGNATURES, s
+    assert set(_lib.SIGNATURES) == set(syms)
+
+
+def test_max_compressed_size():
+    lib = _lib.load()
+    assert lib.boa_max_compressed_size(0) == 0
+    assert lib.boa_max_compressed_size(1) == 1
+    assert lib.boa_max_compressed_size(2) == 1 + 5 + 4
+    assert lib.boa_max_compressed_size(16384) == 1 + 5 * 16383 + 4
+
+
+def test_load_errors_are_reported_not_raised(tmp_path):
+    from paper_2511_11337_b300 import api
+    with pytest.raises(_lib.BoaError) as e:
+        api.Model(str(tmp_path / "missing.boaw"))
+    assert e.value.code == 2
+    bad = tmp_path / "bad.boaw"
+    bad.write_bytes(b"XXXX" + b"\0" * 100)
+    with pytest.raises(_lib.BoaError) as e:
+        api.Model(str(bad))
+    assert e.value.code == 3
+
+
+def test_product_path_does_not_import_oracle():
+    """Nothing in the package imports, links or loads the oracle."""
+    pkg = os.path.join(ROOT, "paper_2511_11337_b300")
+    pat = re.compile(r"^\s*(from\s+oracle|import\s+oracle)|liboracle|boa_oracle", re.M)
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                assert not pat.search(open(os.path.join(dirpath, f)).read()), f
