@@ -129,7 +129,7 @@ struct boa_model {
     DevBuf<uint32_t> flags;
     DevBuf<uint64_t> in_off, out_off, lens, sizes, trace_off, trace, pack_off;
     HostBuf<uint8_t> h_in, h_out;
-    HostBuf<uint64_t> h_u64;
+    HostBuf<uint64_t> h_u64, h_pack;
     HostBuf<uint32_t> h_u32;
 
     bool trace_on = false;
@@ -229,7 +229,7 @@ static void free_workspace(boa_model* m) {
     m->st.release(); m->tokens.release(); m->d_in.release(); m->d_out.release(); m->flags.release();
     m->in_off.release(); m->out_off.release(); m->lens.release(); m->sizes.release();
     m->trace_off.release(); m->trace.release(); m->d_pack.release(); m->pack_off.release();
-    m->h_in.release(); m->h_out.release(); m->h_u64.release(); m->h_u32.release();
+    m->h_in.release(); m->h_out.release(); m->h_u64.release(); m->h_pack.release(); m->h_u32.release();
 }
 
 extern "C" void boa_free_model(boa_model* m) {
@@ -509,9 +509,11 @@ static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
 }
 
 // Stage the per-stream index arrays on the device and size the CDF trace.
+// Each array gets its own region of the pinned staging buffer: the copies are
+// asynchronous and read the host memory only when they execute.
 static boa_status upload_index(boa_model* m, size_t S, const uint64_t* in_off, const uint64_t* out_off,
-                               const uint64_t* lens) {
-    TRY(m->h_u64.ensure(4 * (S + 1)));
+                               const uint64_t* lens, const uint64_t* coded_sizes = nullptr) {
+    TRY(m->h_u64.ensure(5 * (S + 1)));
     uint64_t* hb = m->h_u64.p;
     memcpy(hb, in_off, (S + 1) * 8);
     memcpy(hb + (S + 1), out_off, (S + 1) * 8);
@@ -526,6 +528,11 @@ static boa_status upload_index(boa_model* m, size_t S, const uint64_t* in_off, c
     CU(cudaMemcpyAsync(m->out_off.p, hb + (S + 1), (S + 1) * 8, cudaMemcpyHostToDevice, m->stream));
     CU(cudaMemcpyAsync(m->lens.p, hb + 2 * (S + 1), S * 8, cudaMemcpyHostToDevice, m->stream));
     CU(cudaMemcpyAsync(m->trace_off.p, toff, S * 8, cudaMemcpyHostToDevice, m->stream));
+    if (coded_sizes) {
+        uint64_t* cs = hb + 4 * (S + 1);
+        memcpy(cs, coded_sizes, S * 8);
+        CU(cudaMemcpyAsync(m->sizes.p, cs, S * 8, cudaMemcpyHostToDevice, m->stream));
+    }
     m->trace_n = 0;
     if (m->trace_on) {
         TRY(m->trace.ensure(std::max<uint64_t>(acc, 1)));
@@ -602,10 +609,7 @@ static boa_status decompress_impl(boa_model* m, size_t S, const uint8_t* d_in, c
     }
     m->launches = 0;
     TRY(ensure_workspace(m, S, S));
-    TRY(upload_index(m, S, in_off, out_off, lens));
-    TRY(m->h_u64.ensure(S));
-    memcpy(m->h_u64.p, csz.data(), S * 8);
-    CU(cudaMemcpyAsync(m->sizes.p, m->h_u64.p, S * 8, cudaMemcpyHostToDevice, m->stream));
+    TRY(upload_index(m, S, in_off, out_off, lens, csz.data()));
     TRY(zero_state(m, S));
     const int tb = 128;
     k_dec_init<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(d_in, m->in_off.p, m->sizes.p, m->lens.p, d_out,
@@ -680,9 +684,9 @@ extern "C" boa_status boa_compress(boa_model* m, size_t n, const uint8_t* const*
     for (size_t i = 0; i < n; i++) pk[i + 1] = pk[i] + sizes[i];
     TRY(m->pack_off.ensure(n + 1));
     TRY(m->d_pack.ensure(pk[n]));
-    TRY(m->h_u64.ensure(n + 1));
-    memcpy(m->h_u64.p, pk.data(), (n + 1) * 8);
-    CU(cudaMemcpyAsync(m->pack_off.p, m->h_u64.p, (n + 1) * 8, cudaMemcpyHostToDevice, m->stream));
+    TRY(m->h_pack.ensure(n + 1));
+    memcpy(m->h_pack.p, pk.data(), (n + 1) * 8);
+    CU(cudaMemcpyAsync(m->pack_off.p, m->h_pack.p, (n + 1) * 8, cudaMemcpyHostToDevice, m->stream));
     k_compact<<<(unsigned)n, 256, 0, m->stream>>>(m->d_out.p, m->out_off.p, m->pack_off.p, m->d_pack.p, (int)n);
     TRY(check_launch(m, "compact"));
     CU(cudaMemcpyAsync(m->h_out.p, m->d_pack.p, pk[n], cudaMemcpyDeviceToHost, m->stream));
