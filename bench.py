@@ -177,12 +177,12 @@ def run_boa(args):
 
     tmpd = tempfile.mkdtemp()
     path = synth.make_model_file(os.path.join(tmpd, "paper.boaw"), synth.PAPER_SCALE, seed=2)
-    buf = synth.atlas_workload(N_STREAMS, STREAM_LEN, seed=2000 + rank)
-    streams = synth.split_equal(buf, N_STREAMS)
+    buf = synth.atlas_workload(args.streams, args.stream_len, seed=2000 + rank)
+    streams = synth.split_equal(buf, args.streams)
     total = len(buf)
 
     stream = torch.cuda.Stream()
-    model = api.Model(path, device=local, cuda_stream=stream.cuda_stream)
+    model = api.Model(path, device=local, cuda_stream=stream.cuda_stream, max_rows=args.max_rows)
     flat, in_off = api.pack(streams)
     lens = np.diff(in_off)
     out_off = api.compressed_slot_offsets(lens)
@@ -201,10 +201,12 @@ def run_boa(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    assert torch.equal(d_dec, d_in), "round trip failed in warm-up"
+    if args.warmup:
+        assert torch.equal(d_dec, d_in), "round trip failed in warm-up"
 
     # timed region
-    model.profile(True, decode_step_stride=8)
+    stride = 8
+    model.profile(True, decode_step_stride=stride)
     model.profile_reset()
     evs = []
     launches = 0
@@ -238,17 +240,19 @@ def run_boa(args):
     comp_total = int(np.sum(sizes))
 
     # end to end through the host API (pinned staging, H2D, compute, D2H)
-    host_streams = streams
-    e2e_times = []
-    for _ in range(max(args.e2e_steps, 1)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        comp = model.compress(host_streams)
-        dec = model.decompress(comp, [len(s) for s in host_streams])
-        e2e_times.append(time.perf_counter() - t0)
-    assert dec == host_streams
-    e2e_comp = sum(map(len, comp))
-    e2e_s = statistics.mean(e2e_times)
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e_times = []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            comp = model.compress(streams)
+            dec = model.decompress(comp, [len(s) for s in streams])
+            e2e_times.append(time.perf_counter() - t0)
+        assert dec == streams
+        e2e_comp = sum(map(len, comp))
+        e2e = {"value": world * total / 1e6 / statistics.mean(e2e_times), "unit": UNIT,
+               "h2d_bytes_per_step": total + e2e_comp, "d2h_bytes_per_step": e2e_comp + total}
 
     if rank != 0:
         if dist:
@@ -257,27 +261,37 @@ def run_boa(args):
 
     value = world * total / 1e6 / (ms / 1e3)
     peaks, peak_src = measured_peaks()
-    # dominant kernel class over the step
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"] / kv[1]["launches"] * (kv[1]["launches"]))[0] if prof else None
+    # Per-(phase, class) device time per step: compression launches are all
+    # timed; decompression launches every `stride`-th step, so scale by it.
+    est = {}
+    for phase, d in prof.items():
+        for k, v in d.items():
+            scale = (stride if phase == "decompress" else 1) / args.steps
+            est[(phase, k)] = dict(v, ms_step=v["ms"] * scale)
+    step_est = sum(v["ms_step"] for v in est.values())
+    dom = max(est, key=lambda k: est[k]["ms_step"]) if est else None
     roof = None
     if dom:
-        p = prof[dom]
-        if dom.startswith("gemm"):
+        p = est[dom]
+        name = f"{dom[1]} ({dom[0]})"
+        if dom[1].startswith("gemm"):
             achieved = p["flops"] / (p["ms"] / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_PEAK_TFLOPS, "kernel": dom,
-                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz (FP32 FFMA, no tensor cores)"}
+                    "frac": achieved / FP32_PEAK_TFLOPS, "kernel": name,
+                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz (FP32 FFMA pipe)"}
         else:
             achieved = p["bytes"] / (p["ms"] / 1e3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "kernel": dom, "peak_source": f"hbm_gbs ({peak_src})"}
-        tr = traffic_for(dom)
+                    "frac": achieved / peaks["hbm_gbs"], "kernel": name, "peak_source": f"hbm_gbs ({peak_src})"}
+        tr = traffic_for(f"{dom[0]}:{dom[1]}")
         roof["traffic"] = tr["bytes_per_launch"] if tr else None
         roof["avg_launch_ms"] = p["ms"] / p["launches"]
-        roof["algorithmic_per_launch"] = (p["flops"] if dom.startswith("gemm") else p["bytes"]) / p["launches"]
-    step_ms = sum(v["ms"] for v in prof.values())
-    breakdown = {k: {"launches_timed": v["launches"], "ms": round(v["ms"], 3),
-                     "share_of_timed": round(v["ms"] / step_ms, 4) if step_ms else None} for k, v in prof.items()}
+        roof["algorithmic_per_launch"] = (p["flops"] if dom[1].startswith("gemm") else p["bytes"]) / p["launches"]
+    breakdown = {f"{ph}:{k}": {"launches_timed": v["launches"], "ms_per_step": round(v["ms_step"], 2),
+                               "share": round(v["ms_step"] / step_est, 4) if step_est else None}
+                 for (ph, k), v in sorted(est.items(), key=lambda kv: -kv[1]["ms_step"])}
+    phase_ms = {ph: round(sum(v["ms_step"] for (p2, _), v in est.items() if p2 == ph), 1)
+                for ph in ("compress", "decompress")}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -291,15 +305,19 @@ def run_boa(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "streams": N_STREAMS, "stream_len": STREAM_LEN, "bytes_per_gpu": total,
+        "config": {"workload": WORKLOAD if (args.streams, args.stream_len) == (N_STREAMS, STREAM_LEN) else
+                   f"reduced: {args.streams} x {args.stream_len} B of the jet table, same model",
+                   "streams": args.streams, "stream_len": args.stream_len, "bytes_per_gpu": total,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed (256 MiB write) before every timed step"},
         "compression_ratio": total / comp_total,
         "compressed_bytes": comp_total,
         "wall_s_timed": t_wall,
-        "e2e": {"value": world * total / 1e6 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": total + e2e_comp,
-                "d2h_bytes_per_step": e2e_comp + total},
+        "e2e": e2e,
         "gpu_launches": launches,
+        "phase_ms_per_step": phase_ms,
+        "compress_MBps": total / 1e6 / (phase_ms["compress"] / 1e3) if phase_ms["compress"] else None,
+        "decompress_MBps": total / 1e6 / (phase_ms["decompress"] / 1e3) if phase_ms["decompress"] else None,
         "roofline": roof,
         "kernel_breakdown": breakdown,
         "cpu_baseline": cpu,
@@ -317,6 +335,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="boa", choices=["boa", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--streams", type=int, default=N_STREAMS)
+    ap.add_argument("--stream-len", type=int, default=STREAM_LEN)
+    ap.add_argument("--max-rows", type=int, default=0)
     ap.add_argument("--cpu-prefix", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

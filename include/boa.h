@@ -54,6 +54,8 @@ typedef struct {
     int device;                     /* CUDA device ordinal */
     int precision;                  /* boa_precision */
     void* cuda_stream;              /* cudaStream_t to run on; NULL = library-owned stream */
+    size_t max_rows;                /* compression workspace: rows (stream x step) per
+                                       chunk; 0 = 262144 (about 3 GB at d_model 256) */
 } boa_opts;
 
 typedef struct boa_model boa_model; /* opaque; owned by the library */
@@ -148,13 +150,14 @@ typedef enum {
 
 /* Benchmark hook: when on, every kernel launch of compress / decompress is
  * bracketed by a pair of CUDA events on the model's stream (decompression:
- * only every decode_step_stride-th step), and per-class totals accumulate:
- * launches timed, summed device milliseconds, and the algorithmic FLOPs and
- * DRAM bytes those launches must at least perform.  Reset clears totals. */
+ * only every decode_step_stride-th step), and per-(phase, class) totals
+ * accumulate: launches timed, summed device milliseconds, and the
+ * algorithmic FLOPs and DRAM bytes those launches must at least perform.
+ * phase: 0 = compression, 1 = decompression.  Reset clears totals. */
 boa_status boa_profile_enable(boa_model* model, int on, int decode_step_stride);
 boa_status boa_profile_reset(boa_model* model);
-boa_status boa_profile_read(const boa_model* model, int kernel_class, uint64_t* launches, double* total_ms,
-                            double* flops, double* bytes);
+boa_status boa_profile_read(const boa_model* model, int phase, int kernel_class, uint64_t* launches,
+                            double* total_ms, double* flops, double* bytes);
 
 /* Thread-local message describing the last error on this thread. */
 const char* boa_last_error(void);

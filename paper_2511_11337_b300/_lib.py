@@ -26,7 +26,7 @@ SIGNATURES = {
     "boa_last_error": (C.c_char_p, []),
     "boa_profile_enable": (i32, [vp, i32, i32]),
     "boa_profile_reset": (i32, [vp]),
-    "boa_profile_read": (i32, [vp, i32, vp, vp, vp, vp]),
+    "boa_profile_read": (i32, [vp, i32, i32, vp, vp, vp, vp]),
     "boa_debug_encode_cdfs": (i32, [sz, vp, vp, vp, vp, sz, vp]),
     "boa_debug_decode_cdfs": (i32, [sz, vp, vp, vp, sz, vp, vp]),
     "boa_debug_quantise": (i32, [sz, vp, vp]),

@@ -20,15 +20,16 @@ def max_compressed_size(n: int) -> int:
 
 
 class _Opts(C.Structure):
-    _fields_ = [("device", C.c_int), ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
+    _fields_ = [("device", C.c_int), ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("max_rows", C.c_size_t)]
 
 
 class Model:
     """A predictor loaded on the GPU (boa_load_model)."""
 
-    def __init__(self, path: str, device: int = 0, precision: int = PREC_FP32, cuda_stream: int | None = None):
+    def __init__(self, path: str, device: int = 0, precision: int = PREC_FP32, cuda_stream: int | None = None,
+                 max_rows: int = 0):
         self._h = C.c_void_p()
-        opts = _Opts(device, precision, cuda_stream)
+        opts = _Opts(device, precision, cuda_stream, max_rows)
         check(load().boa_load_model(os.fsencode(path), C.byref(opts), C.byref(self._h)))
 
     def close(self):
@@ -115,12 +116,16 @@ class Model:
         check(load().boa_profile_reset(self._h))
 
     def profile_read(self) -> dict:
+        """{phase: {class: {launches, ms, flops, bytes}}} for the timed launches."""
         out = {}
-        for i, name in enumerate(self.KERNEL_CLASSES):
-            n, ms, fl, by = C.c_uint64(), C.c_double(), C.c_double(), C.c_double()
-            check(load().boa_profile_read(self._h, i, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
-            if n.value:
-                out[name] = {"launches": int(n.value), "ms": ms.value, "flops": fl.value, "bytes": by.value}
+        for ph, pname in enumerate(("compress", "decompress")):
+            d = {}
+            for i, name in enumerate(self.KERNEL_CLASSES):
+                n, ms, fl, by = C.c_uint64(), C.c_double(), C.c_double(), C.c_double()
+                check(load().boa_profile_read(self._h, ph, i, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
+                if n.value:
+                    d[name] = {"launches": int(n.value), "ms": ms.value, "flops": fl.value, "bytes": by.value}
+            out[pname] = d
         return out
 
     # ----------------------------------------------------------- test hooks

@@ -140,12 +140,14 @@ struct boa_model {
     bool prof_on = false;
     int prof_stride = 1;            // time every prof_stride-th step of the decode loop
     bool prof_step = true;          // is the current step timed?
-    struct ProfRec { int cls; cudaEvent_t a, b; double flops, bytes; };
+    int prof_phase = 0;             // 0 compression, 1 decompression
+    struct ProfRec { int phase, cls; cudaEvent_t a, b; double flops, bytes; };
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<ProfRec> prof_pending;
-    uint64_t prof_launches[BOA_KC_COUNT] = {};
-    double prof_ms[BOA_KC_COUNT] = {}, prof_flops[BOA_KC_COUNT] = {}, prof_bytes[BOA_KC_COUNT] = {};
+    uint64_t prof_launches[2][BOA_KC_COUNT] = {};
+    double prof_ms[2][BOA_KC_COUNT] = {}, prof_flops[2][BOA_KC_COUNT] = {}, prof_bytes[2][BOA_KC_COUNT] = {};
+    size_t max_rows = 1u << 18;
 };
 
 static uint64_t fnv1a64(const uint8_t* p, size_t n) {
@@ -186,7 +188,7 @@ struct ProfScope {
         cudaEvent_t b = prof_event(m);
         if (!b) return;
         cudaEventRecord(b, m->stream);
-        m->prof_pending.push_back({cls, a, b, flops, bytes});
+        m->prof_pending.push_back({m->prof_phase, cls, a, b, flops, bytes});
     }
 };
 
@@ -195,10 +197,10 @@ static void prof_collect(boa_model* m) {
     for (auto& r : m->prof_pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
-            m->prof_launches[r.cls]++;
-            m->prof_ms[r.cls] += ms;
-            m->prof_flops[r.cls] += r.flops;
-            m->prof_bytes[r.cls] += r.bytes;
+            m->prof_launches[r.phase][r.cls]++;
+            m->prof_ms[r.phase][r.cls] += ms;
+            m->prof_flops[r.phase][r.cls] += r.flops;
+            m->prof_bytes[r.phase][r.cls] += r.bytes;
         }
     }
     m->prof_pending.clear();
@@ -282,7 +284,7 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
     const size_t total = 256 * (size_t)d + nl * per_layer + 256 * (size_t)d + 256;
     if (buf.size() != 40 + total * 4) return fail(BOA_ERR_FORMAT, "weight file size %zu, expected %zu", buf.size(), 40 + total * 4);
 
-    boa_opts o = {0, BOA_PREC_FP32, nullptr};
+    boa_opts o = {0, BOA_PREC_FP32, nullptr, 0};
     if (opts) o = *opts;
     if (o.precision != BOA_PREC_FP32) return fail(BOA_ERR_ARG, "precision %d not supported", o.precision);
     int ndev = 0;
@@ -321,6 +323,7 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
 
     boa_model* m = new boa_model();
     m->device = o.device;
+    if (o.max_rows) m->max_rows = std::max<size_t>(o.max_rows, 1);
     m->d = d; m->nl = nl; m->N = N; m->K = K; m->E = E; m->r = r; m->ffn_mult = ffn; m->F = F; m->R2 = R2;
     m->fingerprint = fnv1a64(buf.data(), buf.size());
     cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, o.device);
@@ -483,7 +486,6 @@ static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc) {
     return gemm<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_wt, m->head_b, m->logits.p, rows, 256, d);
 }
 
-static const size_t kRowsTarget = 1u << 18;
 
 static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
     const size_t d = m->d, E = m->E;
@@ -563,7 +565,8 @@ static boa_status compress_impl(boa_model* m, size_t S, const uint8_t* d_in, con
     }
     m->launches = 0;
     m->prof_step = true;
-    const int Tc = (int)std::max<uint64_t>(1, std::min<uint64_t>(maxlen > 1 ? maxlen - 1 : 1, kRowsTarget / S));
+    m->prof_phase = 0;
+    const int Tc = (int)std::max<uint64_t>(1, std::min<uint64_t>(maxlen > 1 ? maxlen - 1 : 1, m->max_rows / S));
     TRY(ensure_workspace(m, S, S * (size_t)Tc));
     TRY(upload_index(m, S, in_off, out_off, lens.data()));
     TRY(zero_state(m, S));
@@ -608,6 +611,7 @@ static boa_status decompress_impl(boa_model* m, size_t S, const uint8_t* d_in, c
         maxlen = std::max(maxlen, lens[i]);
     }
     m->launches = 0;
+    m->prof_phase = 1;
     TRY(ensure_workspace(m, S, S));
     TRY(upload_index(m, S, in_off, out_off, lens, csz.data()));
     TRY(zero_state(m, S));
@@ -738,20 +742,21 @@ extern "C" boa_status boa_profile_enable(boa_model* m, int on, int stride) {
 
 extern "C" boa_status boa_profile_reset(boa_model* m) {
     if (!m) return fail(BOA_ERR_ARG, "null model");
-    for (int i = 0; i < BOA_KC_COUNT; i++) {
-        m->prof_launches[i] = 0;
-        m->prof_ms[i] = m->prof_flops[i] = m->prof_bytes[i] = 0.0;
-    }
+    for (int ph = 0; ph < 2; ph++)
+        for (int i = 0; i < BOA_KC_COUNT; i++) {
+            m->prof_launches[ph][i] = 0;
+            m->prof_ms[ph][i] = m->prof_flops[ph][i] = m->prof_bytes[ph][i] = 0.0;
+        }
     return BOA_OK;
 }
 
-extern "C" boa_status boa_profile_read(const boa_model* m, int cls, uint64_t* launches, double* total_ms,
-                                       double* flops, double* bytes) {
-    if (!m || cls < 0 || cls >= BOA_KC_COUNT) return fail(BOA_ERR_ARG, "bad argument");
-    if (launches) *launches = m->prof_launches[cls];
-    if (total_ms) *total_ms = m->prof_ms[cls];
-    if (flops) *flops = m->prof_flops[cls];
-    if (bytes) *bytes = m->prof_bytes[cls];
+extern "C" boa_status boa_profile_read(const boa_model* m, int phase, int cls, uint64_t* launches,
+                                       double* total_ms, double* flops, double* bytes) {
+    if (!m || cls < 0 || cls >= BOA_KC_COUNT || phase < 0 || phase > 1) return fail(BOA_ERR_ARG, "bad argument");
+    if (launches) *launches = m->prof_launches[phase][cls];
+    if (total_ms) *total_ms = m->prof_ms[phase][cls];
+    if (flops) *flops = m->prof_flops[phase][cls];
+    if (bytes) *bytes = m->prof_bytes[phase][cls];
     return BOA_OK;
 }
 
@@ -867,7 +872,7 @@ extern "C" boa_status boa_debug_logprobs(boa_model* m, const uint8_t* stream, si
     if (len < 2) return BOA_OK;
     CU(cudaSetDevice(m->device));
     const size_t T = len - 1;
-    const int Tc = (int)std::min<size_t>(T, kRowsTarget);
+    const int Tc = (int)std::min<size_t>(T, m->max_rows);
     TRY(ensure_workspace(m, 1, Tc));
     TRY(m->d_in.ensure(len));
     DevBuf<float> lp;
@@ -912,3 +917,4 @@ extern "C" boa_status boa_debug_read_cdf_trace(boa_model* m, uint64_t* out, size
     CU(cudaStreamSynchronize(m->stream));
     return BOA_OK;
 }
+
