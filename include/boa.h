@@ -197,6 +197,30 @@ boa_status boa_debug_logprobs(boa_model* model, const uint8_t* stream, size_t le
 boa_status boa_debug_enable_cdf_trace(boa_model* model, int on);
 boa_status boa_debug_read_cdf_trace(boa_model* model, uint64_t* out, size_t n);
 
+/* Allocation-free range decoder.  The paper has no counterpart: this entry
+ * exists for callers that must not allocate device memory while running --
+ * e.g. a data-acquisition process whose GPU memory budget is fixed at
+ * start-up, or a host framework whose own pool owns all device memory.
+ * It decodes like boa_debug_decode_cdfs, but every pointer except n_syms and
+ * in_sizes is DEVICE memory the caller owns: d_cdfs ([sum n_syms][257] u32,
+ * sequence i's rows first), d_in (sequence i's coded bytes at d_in + i *
+ * in_stride, in_sizes[i] of them), d_syms (sum n_syms symbols out).  n_syms
+ * and in_sizes are host arrays.  cuda_stream: cudaStream_t or NULL (legacy
+ * default stream); the call returns after that stream is synchronised.
+ * Scratch (per-sequence offsets, sizes and status words) lives in one
+ * statically sized device array of about 1.8 MB that every GPU loading this
+ * library holds until the process exits; the call allocates nothing.
+ * Limit: at most 65536 sequences per call (BOA_ERR_ARG beyond it).  The first
+ * call on each device looks up the array's device address (once, under a
+ * lock); make that first call before any stream capture.  All calls share the
+ * one array, so calls whose work overlaps on the GPU (different streams or
+ * host threads) race and must be serialised by the caller.  Errors:
+ * BOA_ERR_ARG, BOA_ERR_CORRUPT (some sequence did not decode cleanly),
+ * BOA_ERR_CUDA. */
+boa_status boa_decode_cdfs_static(size_t n_seq, const size_t* n_syms, const uint32_t* d_cdfs,
+                                  const uint8_t* d_in, size_t in_stride, const size_t* in_sizes,
+                                  uint8_t* d_syms, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

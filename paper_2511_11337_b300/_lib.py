@@ -33,6 +33,7 @@ SIGNATURES = {
     "boa_debug_logprobs": (i32, [vp, vp, sz, vp]),
     "boa_debug_enable_cdf_trace": (i32, [vp, i32]),
     "boa_debug_read_cdf_trace": (i32, [vp, vp, sz]),
+    "boa_decode_cdfs_static": (i32, [sz, vp, vp, vp, sz, vp, vp, vp]),
 }
 
 STATUS = {0: "BOA_OK", 1: "BOA_ERR_ARG", 2: "BOA_ERR_IO", 3: "BOA_ERR_FORMAT", 4: "BOA_ERR_CUDA",

@@ -176,6 +176,16 @@ def decode_cdfs(cdf_list: list[np.ndarray], coded: list[bytes]) -> list[np.ndarr
     return out
 
 
+def decode_cdfs_static(n_syms, d_cdfs_ptr: int, d_in_ptr: int, in_stride: int, in_sizes, d_syms_ptr: int,
+                       cuda_stream: int | None = None) -> None:
+    """Allocation-free decoder (boa_decode_cdfs_static): device inputs and
+    outputs, scratch in the library's static device array."""
+    n = np.ascontiguousarray(n_syms, np.uintp)
+    sz = np.ascontiguousarray(in_sizes, np.uintp)
+    check(load().boa_decode_cdfs_static(len(n), _p(n), C.c_void_p(d_cdfs_ptr), C.c_void_p(d_in_ptr), in_stride,
+                                        _p(sz), C.c_void_p(d_syms_ptr), C.c_void_p(cuda_stream)))
+
+
 def quantise(p: np.ndarray) -> np.ndarray:
     p = np.ascontiguousarray(p, np.float32).reshape(-1, 256)
     f = np.zeros_like(p, dtype=np.uint32)
@@ -202,4 +212,4 @@ def compressed_slot_offsets(lens) -> np.ndarray:
     return slot_offsets([max_compressed_size(int(n)) for n in lens])
 
 
-__all__ = ["pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32"]
+__all__ = ["decode_cdfs_static", "pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32"]

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -918,3 +919,104 @@ extern "C" boa_status boa_debug_read_cdf_trace(boa_model* m, uint64_t* out, size
     return BOA_OK;
 }
 
+// ------------------------------------------------- allocation-free decoder
+//
+// boa_decode_cdfs_static: the CDF-driven range decoder for callers that may
+// not allocate device memory once they are running -- for example a
+// data-acquisition process whose device memory budget is fixed at start-up,
+// or a host framework whose own memory pool owns the GPU and forbids other
+// allocations.  The caller passes device inputs and outputs; the decoder's
+// scratch (per-sequence symbol offsets, coded sizes, status words) lives in
+// the file-scope array below, which every GPU that loads this library holds
+// until the process exits.
+
+static constexpr size_t kStaticMaxSeq = 65536;
+static constexpr size_t kStaticCountsOff = 0;                                  // u64[kStaticMaxSeq]
+static constexpr size_t kStaticSymOffOff = kStaticCountsOff + 8 * kStaticMaxSeq;   // u64[kStaticMaxSeq + 1]
+static constexpr size_t kStaticSizesOff = kStaticSymOffOff + 8 * (kStaticMaxSeq + 256);  // u64[kStaticMaxSeq]
+static constexpr size_t kStaticFlagsOff = kStaticSizesOff + 8 * kStaticMaxSeq;     // u32[kStaticMaxSeq]
+static constexpr size_t kStaticOrOff = kStaticFlagsOff + 4 * kStaticMaxSeq;        // u32 (OR of all flags)
+static constexpr size_t kStaticScratchBytes = kStaticOrOff + 256;
+static_assert(sizeof(size_t) == sizeof(uint64_t), "size_t arrays are copied as u64");
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Exclusive prefix sum of n counts in one block of 1024 threads.
+__global__ void k_static_prefix(const uint64_t* __restrict__ counts, uint64_t* __restrict__ off, int n) {
+    __shared__ uint64_t part[1024];
+    const int tid = threadIdx.x;
+    const int per = (n + 1023) / 1024;
+    const int b = tid * per, e = min(n, b + per);
+    uint64_t s = 0;
+    for (int i = b; i < e; i++) s += counts[i];
+    part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t acc = 0;
+        for (int i = 0; i < 1024; i++) { uint64_t v = part[i]; part[i] = acc; acc += v; }
+    }
+    __syncthreads();
+    uint64_t acc = part[tid];
+    for (int i = b; i < e; i++) { off[i] = acc; acc += counts[i]; }
+    if (e == n && b < e) off[n] = acc;
+    if (n == 0 && tid == 0) off[0] = 0;
+}
+
+__global__ void k_static_flags_or(const uint32_t* __restrict__ flags, int n, uint32_t* __restrict__ out) {
+    uint32_t v = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v |= flags[i];
+    if (v) atomicOr(out, v);
+}
+
+static std::mutex g_static_mu;
+static unsigned char* g_static_ptr[256];   // per device ordinal, set once
+
+// Once per device, with that device current: the device address of the
+// scratch array (host code cannot use the symbol itself as an address).
+static boa_status static_scratch(unsigned char** out) {
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(BOA_ERR_CUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) return fail(BOA_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_static_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_static_ptr[dev];
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_decode_cdfs_static(size_t n_seq, const size_t* n_syms, const uint32_t* d_cdfs,
+                                             const uint8_t* d_in, size_t in_stride, const size_t* in_sizes,
+                                             uint8_t* d_syms, void* cuda_stream) {
+    if (n_seq == 0) return BOA_OK;
+    if (n_seq > kStaticMaxSeq)
+        return fail(BOA_ERR_ARG, "boa_decode_cdfs_static: %zu sequences exceed the static scratch limit of %zu",
+                    n_seq, kStaticMaxSeq);
+    if (!n_syms || !d_cdfs || !d_in || !in_sizes || !d_syms) return fail(BOA_ERR_ARG, "null argument");
+    for (size_t i = 0; i < n_seq; i++)
+        if (in_sizes[i] > in_stride) return fail(BOA_ERR_ARG, "in_sizes[%zu] > in_stride", i);
+    unsigned char* base = nullptr;
+    TRY(static_scratch(&base));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint64_t* counts = reinterpret_cast<uint64_t*>(base + kStaticCountsOff);
+    uint64_t* sym_off = reinterpret_cast<uint64_t*>(base + kStaticSymOffOff);
+    uint64_t* sizes = reinterpret_cast<uint64_t*>(base + kStaticSizesOff);
+    uint32_t* flags = reinterpret_cast<uint32_t*>(base + kStaticFlagsOff);
+    uint32_t* flag_or = reinterpret_cast<uint32_t*>(base + kStaticOrOff);
+    CU(cudaMemcpyAsync(counts, n_syms, n_seq * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(sizes, in_sizes, n_seq * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(flag_or, 0, 4, st));   // the array keeps the previous call's contents
+    k_static_prefix<<<1, 1024, 0, st>>>(counts, sym_off, (int)n_seq);
+    k_debug_decode_cdfs<<<(unsigned)((n_seq + 3) / 4), 128, 0, st>>>((int)n_seq, sym_off, d_cdfs, d_in, in_stride,
+                                                                    sizes, d_syms, flags);
+    k_static_flags_or<<<(unsigned)std::min<size_t>((n_seq + 255) / 256, 64), 256, 0, st>>>(flags, (int)n_seq, flag_or);
+    CU(cudaGetLastError());
+    uint32_t h_or = 0;
+    CU(cudaMemcpyAsync(&h_or, flag_or, 4, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (h_or) return fail(BOA_ERR_CORRUPT, "a sequence did not decode cleanly (flags %u)", h_or);
+    return BOA_OK;
+}
