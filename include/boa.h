@@ -47,7 +47,9 @@ typedef enum {
 } boa_status;
 
 typedef enum {
-    BOA_PREC_FP32 = 0               /* all projections in FP32 on the CUDA cores */
+    BOA_PREC_FP32 = 0,              /* all projections in FP32 on the CUDA cores */
+    BOA_PREC_BF16 = 1               /* projections in BF16 on the tensor cores (tcgen05), FP32
+                                       accumulation; norms, conv, scan, softmax and CDF stay FP32 */
 } boa_precision;
 
 typedef struct {
@@ -190,6 +192,15 @@ boa_status boa_debug_quantise(size_t n_rows, const float* p, uint32_t* f);
 /* Teacher-forced log2 next-byte probabilities of one stream from the
  * compression path: out (host) [(len-1)][256], row t predicting byte t+1. */
 boa_status boa_debug_logprobs(boa_model* model, const uint8_t* stream, size_t len, float* out);
+
+/* One projection GEMM on the GPU, for kernel tests:
+ * C_out[M][N] = epi(A[M][K] . W[N][K]^T) with the library's FP32 CUDA-core
+ * kernel (precision BOA_PREC_FP32) or its tcgen05 tensor-core kernel with
+ * A and W rounded to BF16 (BOA_PREC_BF16).  epilogue: 0 store, 1 + bias[n],
+ * 2 C_in + acc, 3 GELU(acc + bias[n]), 4 C_in + (acc + bias[n]).  All pointers
+ * host memory; N % 4 == 0; K % 8 == 0 (FP32) or K % 64 == 0 (BF16).  Device 0. */
+boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K, const float* A, const float* W,
+                          const float* bias, int epilogue, const float* C_in, float* C_out);
 
 /* When on, the next compress / decompress calls record a 64-bit hash of the
  * integer CDF used at every coded step; boa_debug_read_cdf_trace copies the

@@ -30,6 +30,7 @@ SIGNATURES = {
     "boa_debug_encode_cdfs": (i32, [sz, vp, vp, vp, vp, sz, vp]),
     "boa_debug_decode_cdfs": (i32, [sz, vp, vp, vp, sz, vp, vp]),
     "boa_debug_quantise": (i32, [sz, vp, vp]),
+    "boa_debug_gemm": (i32, [i32, sz, sz, sz, vp, vp, vp, i32, vp, vp]),
     "boa_debug_logprobs": (i32, [vp, vp, sz, vp]),
     "boa_debug_enable_cdf_trace": (i32, [vp, i32]),
     "boa_debug_read_cdf_trace": (i32, [vp, vp, sz]),

@@ -9,6 +9,7 @@ import numpy as np
 from ._lib import BoaError, check, load
 
 PREC_FP32 = 0
+PREC_BF16 = 1
 
 
 def _p(a: np.ndarray):
@@ -186,6 +187,19 @@ def decode_cdfs_static(n_syms, d_cdfs_ptr: int, d_in_ptr: int, in_stride: int, i
                                         _p(sz), C.c_void_p(d_syms_ptr), C.c_void_p(cuda_stream)))
 
 
+def gemm(A: np.ndarray, W: np.ndarray, bias=None, epilogue: int = 0, C_in=None, precision: int = PREC_FP32):
+    """One projection GEMM on the GPU (boa_debug_gemm): epi(A . W^T)."""
+    A = np.ascontiguousarray(A, np.float32); W = np.ascontiguousarray(W, np.float32)
+    M, K = A.shape
+    N = W.shape[0]
+    out = np.zeros((M, N), np.float32)
+    b = np.ascontiguousarray(bias, np.float32) if bias is not None else None
+    ci = np.ascontiguousarray(C_in, np.float32) if C_in is not None else None
+    check(load().boa_debug_gemm(precision, M, N, K, _p(A), _p(W), _p(b) if b is not None else None, epilogue,
+                                _p(ci) if ci is not None else None, _p(out)))
+    return out
+
+
 def quantise(p: np.ndarray) -> np.ndarray:
     p = np.ascontiguousarray(p, np.float32).reshape(-1, 256)
     f = np.zeros_like(p, dtype=np.uint32)
@@ -212,4 +226,4 @@ def compressed_slot_offsets(lens) -> np.ndarray:
     return slot_offsets([max_compressed_size(int(n)) for n in lens])
 
 
-__all__ = ["decode_cdfs_static", "pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32"]
+__all__ = ["decode_cdfs_static", "pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32", "PREC_BF16", "gemm"]

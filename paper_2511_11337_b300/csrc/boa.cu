@@ -20,9 +20,12 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "boa.h"
 #include "common.cuh"
 #include "gemm_fp32.cuh"
+#include "gemm_tc.cuh"
 #include "kernels.cuh"
 
 using namespace boa;
@@ -123,8 +126,18 @@ struct boa_model {
     float *embed = nullptr, *head_wt = nullptr, *head_b = nullptr;
     std::vector<DevLayer> layers;
 
+    // BF16 tensor-core path: weight copies in nn.Linear layout [out][in]
+    __nv_bfloat16* wb = nullptr;
+    struct BLayer { __nv_bfloat16 *in_w, *x_w, *out_w, *w1, *w2; };
+    std::vector<BLayer> blayers;
+    __nv_bfloat16* head_wb = nullptr;
+    struct MapEnt { const void* p; uint64_t rows, cols; uint32_t box; CUtensorMap map; };
+    std::vector<MapEnt> maps;
+
     // workspace
     DevBuf<float> x, xn, xz, u, dbc, yg, logits, hid, h, conv;
+    DevBuf<__nv_bfloat16> xn_b, u_b, yg_b, x_b, hid_b;
+    DevBuf<int> err;
     DevBuf<CoderState> st;
     DevBuf<uint8_t> tokens, d_in, d_out, d_pack;
     DevBuf<uint32_t> flags;
@@ -232,6 +245,7 @@ static void free_workspace(boa_model* m) {
     m->st.release(); m->tokens.release(); m->d_in.release(); m->d_out.release(); m->flags.release();
     m->in_off.release(); m->out_off.release(); m->lens.release(); m->sizes.release();
     m->trace_off.release(); m->trace.release(); m->d_pack.release(); m->pack_off.release();
+    m->xn_b.release(); m->u_b.release(); m->yg_b.release(); m->x_b.release(); m->hid_b.release(); m->err.release();
     m->h_in.release(); m->h_out.release(); m->h_u64.release(); m->h_pack.release(); m->h_u32.release();
 }
 
@@ -242,6 +256,7 @@ extern "C" void boa_free_model(boa_model* m) {
     free_workspace(m);
     for (auto e : m->ev_pool) cudaEventDestroy(e);
     if (m->weights) cudaFree(m->weights);
+    if (m->wb) cudaFree(m->wb);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -287,7 +302,8 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
 
     boa_opts o = {0, BOA_PREC_FP32, nullptr, 0};
     if (opts) o = *opts;
-    if (o.precision != BOA_PREC_FP32) return fail(BOA_ERR_ARG, "precision %d not supported", o.precision);
+    if (o.precision != BOA_PREC_FP32 && o.precision != BOA_PREC_BF16)
+        return fail(BOA_ERR_ARG, "precision %d not supported", o.precision);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(BOA_ERR_CUDA, "no CUDA device available");
     if (o.device < 0 || o.device >= ndev) return fail(BOA_ERR_ARG, "bad device %d", o.device);
@@ -301,12 +317,17 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
     auto copy_t = [&](int rows, int cols) { size_t at = dof; transpose(src + so, rows, cols, &dev[dof]); so += (size_t)rows * cols; dof += (size_t)rows * cols; return at; };
     struct Off { size_t ln_a_w, ln_a_b, in_wt, conv_w, conv_b, x_wt, dt_w, dt_b, A2, D, out_wt, w1t, b1, w2t, b2, ln_b_w, ln_b_b; };
     std::vector<Off> lo(nl);
+    struct SrcOff { size_t in_w, x_w, out_w, w1, w2; };   // file offsets of the GEMM weights
+    std::vector<SrcOff> sro(nl);
+    size_t head_src = 0;
     size_t embed_o = copy(256 * (size_t)d);
     for (int l = 0; l < nl; l++) {
         Off& q = lo[l];
         q.ln_a_w = copy(d); q.ln_a_b = copy(d);
+        sro[l].in_w = so;
         q.in_wt = copy_t(2 * E, d);
         q.conv_w = copy((size_t)E * K); q.conv_b = copy(E);
+        sro[l].x_w = so;
         q.x_wt = copy_t(R2, E);
         q.dt_w = copy((size_t)E * r); q.dt_b = copy(E);
         q.A2 = dof;
@@ -314,16 +335,27 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
             dev[dof + i] = (float)(-std::exp((double)src[so + i]) * 1.4426950408889634);
         so += (size_t)E * N; dof += (size_t)E * N;
         q.D = copy(E);
+        sro[l].out_w = so;
         q.out_wt = copy_t(d, E);
         q.w1t = q.b1 = q.w2t = q.b2 = 0;
-        if (F) { q.w1t = copy_t(F, d); q.b1 = copy(F); q.w2t = copy_t(d, F); q.b2 = copy(d); }
+        sro[l].w1 = sro[l].w2 = 0;
+        if (F) {
+            sro[l].w1 = so;
+            q.w1t = copy_t(F, d);
+            q.b1 = copy(F);
+            sro[l].w2 = so;
+            q.w2t = copy_t(d, F);
+            q.b2 = copy(d);
+        }
         q.ln_b_w = copy(d); q.ln_b_b = copy(d);
     }
+    head_src = so;
     size_t head_o = copy_t(256, d);
     size_t head_b_o = copy(256);
 
     boa_model* m = new boa_model();
     m->device = o.device;
+    m->precision = o.precision;
     if (o.max_rows) m->max_rows = std::max<size_t>(o.max_rows, 1);
     m->d = d; m->nl = nl; m->N = N; m->K = K; m->E = E; m->r = r; m->ffn_mult = ffn; m->F = F; m->R2 = R2;
     m->fingerprint = fnv1a64(buf.data(), buf.size());
@@ -356,6 +388,40 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
         L.w1t = F ? w + q.w1t : nullptr; L.b1 = F ? w + q.b1 : nullptr;
         L.w2t = F ? w + q.w2t : nullptr; L.b2 = F ? w + q.b2 : nullptr;
         L.ln_b_w = w + q.ln_b_w; L.ln_b_b = w + q.ln_b_b;
+    }
+    if (m->precision == BOA_PREC_BF16) {
+        // BF16 copies of the projection weights, kept in the file's [out][in]
+        // layout (K-major, as the tensor-core B operand wants it).
+        std::vector<std::pair<size_t, size_t>> mats;   // (source offset, elements)
+        for (int l = 0; l < nl; l++) {
+            mats.push_back({sro[l].in_w, (size_t)2 * E * d});
+            mats.push_back({sro[l].x_w, (size_t)R2 * E});
+            mats.push_back({sro[l].out_w, (size_t)d * E});
+            if (F) { mats.push_back({sro[l].w1, (size_t)F * d}); mats.push_back({sro[l].w2, (size_t)d * F}); }
+        }
+        mats.push_back({head_src, (size_t)256 * d});
+        size_t tot = 0;
+        std::vector<size_t> at;
+        for (auto& mt : mats) { at.push_back(tot); tot += (mt.second + 63) / 64 * 64; }
+        std::vector<__nv_bfloat16> hb(tot, __float2bfloat16_rn(0.f));
+        for (size_t i = 0; i < mats.size(); i++)
+            for (size_t j = 0; j < mats[i].second; j++) hb[at[i] + j] = __float2bfloat16_rn(src[mats[i].first + j]);
+        if (cudaMalloc(&m->wb, tot * 2) != cudaSuccess ||
+            cudaMemcpy(m->wb, hb.data(), tot * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
+            boa_free_model(m);
+            return fail(BOA_ERR_OOM, "bf16 weight upload failed");
+        }
+        size_t k = 0;
+        m->blayers.resize(nl);
+        for (int l = 0; l < nl; l++) {
+            auto& B = m->blayers[l];
+            B.in_w = m->wb + at[k++];
+            B.x_w = m->wb + at[k++];
+            B.out_w = m->wb + at[k++];
+            B.w1 = F ? m->wb + at[k++] : nullptr;
+            B.w2 = F ? m->wb + at[k++] : nullptr;
+        }
+        m->head_wb = m->wb + at[k++];
     }
     *out = m;
     return BOA_OK;
@@ -393,17 +459,97 @@ static boa_status gemm(boa_model* m, int cls, const float* A, const float* Wt, c
     return check_launch(m, "gemm");
 }
 
+// ---- tensor-core GEMM (BF16 operands, FP32 accumulation)
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
+static std::mutex g_encode_mu;
+
+// 2-D BF16 tensor map over a row-major [rows][cols] matrix, boxes of
+// 64 columns (128 bytes, 128-byte swizzle) by box_rows rows.
+static boa_status tmap_bf16(boa_model* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows,
+                            CUtensorMap* out) {
+    for (auto& e : m->maps)
+        if (e.p == ptr && e.rows == rows && e.cols == cols && e.box == box_rows) { *out = e.map; return BOA_OK; }
+    {
+        std::lock_guard<std::mutex> lock(g_encode_mu);
+        if (!g_encode_tiled) {
+            cudaDriverEntryPointQueryResult q;
+            void* fn = nullptr;
+            cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+                return fail(BOA_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+            g_encode_tiled = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        }
+    }
+    if (((uintptr_t)ptr & 15) || (cols * 2) % 16) return fail(BOA_ERR_ARG, "tensor map needs 16-byte aligned rows");
+    boa_model::MapEnt e;
+    e.p = ptr; e.rows = rows; e.cols = cols; e.box = box_rows;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcBK, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode_tiled(&e.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(BOA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    if (m->maps.size() >= 256) m->maps.clear();
+    m->maps.push_back(e);
+    *out = e.map;
+    return BOA_OK;
+}
+
+// Tile width by output width only, so a given projection always runs the
+// same MMA shape in compression and decompression.
+static int tc_bn(int N) { return N >= 512 ? 128 : N > 48 ? 64 : 48; }
+
+template <int BN, int EPI>
+static void launch_tc(boa_model* m, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, float* C,
+                      __nv_bfloat16* outb, long long M, int N, int K) {
+    using L = TcSmem<BN>;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_gemm_tc_bf16<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
+    });
+    dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
+    k_gemm_tc_bf16<BN, EPI><<<grid, kTcThreads, L::kBytes, m->stream>>>(ta, tb, bias, C, outb, (int)M, N, K, m->err.p);
+}
+
+template <int EPI>
+static boa_status gemm_tc(boa_model* m, int cls, const __nv_bfloat16* A, const __nv_bfloat16* W, const float* bias,
+                          float* C, __nv_bfloat16* outb, long long M, int N, int K) {
+    if (M <= 0) return BOA_OK;
+    if (N % 4 != 0 || K % kTcBK != 0) return fail(BOA_ERR_FORMAT, "tensor-core gemm shape N=%d K=%d unsupported", N, K);
+    const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
+    ProfScope ps(m, cls, 2.0 * M * N * K,
+                 2.0 * ((double)M * K + (double)K * N) + 4.0 * (double)M * N * (resid ? 2 : 1) + (outb ? 2.0 * M * N : 0));
+    const int BN = tc_bn(N);
+    CUtensorMap ta, tb;
+    TRY(tmap_bf16(m, A, (uint64_t)M, (uint64_t)K, kTcBM, &ta));
+    TRY(tmap_bf16(m, W, (uint64_t)N, (uint64_t)K, (uint32_t)BN, &tb));
+    switch (BN) {
+        case 48: launch_tc<48, EPI>(m, ta, tb, bias, C, outb, M, N, K); break;
+        case 64: launch_tc<64, EPI>(m, ta, tb, bias, C, outb, M, N, K); break;
+        default: launch_tc<128, EPI>(m, ta, tb, bias, C, outb, M, N, K); break;
+    }
+    return check_launch(m, "gemm_tc");
+}
+
 template <int VPT>
 static void launch_embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc, const DevLayer& L0) {
     const long long rows = (long long)S * Tc;
+    const bool tc = m->precision == BOA_PREC_BF16;
     k_embed_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->stream>>>(ts, S, Tc, m->embed, L0.ln_a_w, L0.ln_a_b,
-                                                                      m->x.p, m->xn.p);
+                                                                      m->x.p, m->xn.p, tc ? m->xn_b.p : nullptr);
 }
 
 template <int VPT>
 static void launch_ln_ln(boa_model* m, long long rows, const DevLayer& L, const DevLayer* next) {
+    const bool tc = m->precision == BOA_PREC_BF16;
+    // the BF16 copy of x feeds the head (last block) or the next block's FFN
+    __nv_bfloat16* xb = (tc && (!next || m->F)) ? m->x_b.p : nullptr;
     k_ln_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->stream>>>(
-        rows, m->x.p, L.ln_b_w, L.ln_b_b, next ? next->ln_a_w : nullptr, next ? next->ln_a_b : nullptr, m->xn.p);
+        rows, m->x.p, L.ln_b_w, L.ln_b_b, next ? next->ln_a_w : nullptr, next ? next->ln_a_b : nullptr, m->xn.p, xb,
+        tc ? m->xn_b.p : nullptr);
 }
 
 static boa_status embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc) {
@@ -435,10 +581,11 @@ static boa_status conv(boa_model* m, int l, int S, int Tc) {
     float* win = m->conv.p + (size_t)l * S * (m->K - 1) * m->E;
     const double rows = (double)S * Tc;
     ProfScope ps(m, BOA_KC_CONV, rows * m->E * (2.0 * m->K + 4), 4.0 * (2 * rows * m->E + 2.0 * S * (m->K - 1) * m->E));
+    __nv_bfloat16* ub = m->precision == BOA_PREC_BF16 ? m->u_b.p : nullptr;
     switch (m->K) {
-        case 2: k_conv_silu<2><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, S, Tc); break;
-        case 3: k_conv_silu<3><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, S, Tc); break;
-        case 4: k_conv_silu<4><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, S, Tc); break;
+        case 2: k_conv_silu<2><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, ub, S, Tc); break;
+        case 3: k_conv_silu<3><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, ub, S, Tc); break;
+        case 4: k_conv_silu<4><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, ub, S, Tc); break;
     }
     return check_launch(m, "conv");
 }
@@ -450,10 +597,11 @@ static boa_status scan(boa_model* m, int l, int S, int Tc) {
     const double rows = (double)S * Tc;
     ProfScope ps(m, BOA_KC_SCAN, rows * m->E * (2.0 * m->r + 5.0 * m->N + 12),
                  4.0 * (rows * (3.0 * m->E + m->R2) + 2.0 * S * m->N * m->E));
+    __nv_bfloat16* ygb = m->precision == BOA_PREC_BF16 ? m->yg_b.p : nullptr;
 #define SCAN_CASE(RR)                                                                                           \
     case RR:                                                                                                    \
         k_scan<16, RR><<<grid, kScanThreads, 0, m->stream>>>(m->u.p, m->xz.p, m->dbc.p, L.dt_w, L.dt_b, L.A2, L.D, \
-                                                             hs, m->yg.p, m->E, S, Tc);                         \
+                                                             hs, m->yg.p, ygb, m->E, S, Tc);                    \
         break;
     switch (m->r) {
         SCAN_CASE(1)
@@ -470,23 +618,51 @@ static boa_status scan(boa_model* m, int l, int S, int Tc) {
 static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc) {
     const long long rows = (long long)S * Tc;
     const int d = m->d, E = m->E;
+    const bool tc = m->precision == BOA_PREC_BF16;
     TRY(embed_ln(m, ts, S, Tc));
     for (int l = 0; l < m->nl; l++) {
         const DevLayer& L = m->layers[l];
-        TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn.p, L.in_wt, nullptr, m->xz.p, rows, 2 * E, d));
-        TRY(conv(m, l, S, Tc));
-        TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_X, m->u.p, L.x_wt, nullptr, m->dbc.p, rows, m->R2, E));
-        TRY(scan(m, l, S, Tc));
-        TRY(gemm<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg.p, L.out_wt, nullptr, m->x.p, rows, d, E));
-        if (m->F) {
-            TRY(gemm<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x.p, L.w1t, L.b1, m->hid.p, rows, m->F, d));
-            TRY(gemm<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid.p, L.w2t, L.b2, m->x.p, rows, d, m->F));
+        if (tc) {
+            const auto& B = m->blayers[l];
+            TRY(gemm_tc<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn_b.p, B.in_w, nullptr, m->xz.p, nullptr, rows, 2 * E, d));
+            TRY(conv(m, l, S, Tc));
+            TRY(gemm_tc<kEpiStore>(m, BOA_KC_GEMM_X, m->u_b.p, B.x_w, nullptr, m->dbc.p, nullptr, rows, m->R2, E));
+            TRY(scan(m, l, S, Tc));
+            TRY(gemm_tc<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg_b.p, B.out_w, nullptr, m->x.p, m->F ? m->x_b.p : nullptr,
+                                   rows, d, E));
+            if (m->F) {
+                TRY(gemm_tc<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x_b.p, B.w1, L.b1, m->hid.p, m->hid_b.p, rows, m->F, d));
+                TRY(gemm_tc<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid_b.p, B.w2, L.b2, m->x.p, nullptr, rows, d, m->F));
+            }
+        } else {
+            TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn.p, L.in_wt, nullptr, m->xz.p, rows, 2 * E, d));
+            TRY(conv(m, l, S, Tc));
+            TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_X, m->u.p, L.x_wt, nullptr, m->dbc.p, rows, m->R2, E));
+            TRY(scan(m, l, S, Tc));
+            TRY(gemm<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg.p, L.out_wt, nullptr, m->x.p, rows, d, E));
+            if (m->F) {
+                TRY(gemm<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x.p, L.w1t, L.b1, m->hid.p, rows, m->F, d));
+                TRY(gemm<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid.p, L.w2t, L.b2, m->x.p, rows, d, m->F));
+            }
         }
         TRY(ln_ln(m, rows, l));
     }
+    if (tc) return gemm_tc<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x_b.p, m->head_wb, m->head_b, m->logits.p, nullptr, rows, 256, d);
     return gemm<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_wt, m->head_b, m->logits.p, rows, 256, d);
 }
 
+// Tensor-core waits that timed out leave a nonzero code in m->err.
+static boa_status check_tc_error(boa_model* m) {
+    if (m->precision != BOA_PREC_BF16) return BOA_OK;
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, m->err.p, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    if (h) {
+        cudaMemsetAsync(m->err.p, 0, sizeof(int), m->stream);
+        return fail(BOA_ERR_CUDA, "tensor-core GEMM pipeline wait timed out (code %d)", h);
+    }
+    return BOA_OK;
+}
 
 static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
     const size_t d = m->d, E = m->E;
@@ -498,6 +674,17 @@ static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
     TRY(m->yg.ensure(rows * E));
     TRY(m->logits.ensure(rows * 256));
     if (m->F) TRY(m->hid.ensure(rows * m->F));
+    if (m->precision == BOA_PREC_BF16) {
+        TRY(m->xn_b.ensure(rows * d));
+        TRY(m->u_b.ensure(rows * E));
+        TRY(m->yg_b.ensure(rows * E));
+        TRY(m->x_b.ensure(rows * d));
+        if (m->F) TRY(m->hid_b.ensure(rows * m->F));
+        if (!m->err.p) {
+            TRY(m->err.ensure(1));
+            CU(cudaMemset(m->err.p, 0, sizeof(int)));
+        }
+    }
     TRY(m->h.ensure((size_t)m->nl * S * m->N * E));
     TRY(m->conv.ensure((size_t)m->nl * S * (m->K - 1) * E));
     TRY(m->st.ensure(S));
@@ -594,7 +781,7 @@ static boa_status compress_impl(boa_model* m, size_t S, const uint8_t* d_in, con
     CU(cudaMemcpyAsync(out_sizes, m->sizes.p, S * 8, cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     prof_collect(m);
-    return BOA_OK;
+    return check_tc_error(m);
 }
 
 static boa_status decompress_impl(boa_model* m, size_t S, const uint8_t* d_in, const uint64_t* in_off,
@@ -640,6 +827,7 @@ static boa_status decompress_impl(boa_model* m, size_t S, const uint8_t* d_in, c
     CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, S * 4, cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     prof_collect(m);
+    TRY(check_tc_error(m));
     for (size_t i = 0; i < S; i++)
         if (m->h_u32.p[i]) return fail(BOA_ERR_CORRUPT, "stream %zu did not decode cleanly (flags %u)", i, m->h_u32.p[i]);
     return BOA_OK;
@@ -900,6 +1088,68 @@ extern "C" boa_status boa_debug_logprobs(boa_model* m, const uint8_t* stream, si
     }
     cudaStreamSynchronize(m->stream);
     lp.release();
+    if (st == BOA_OK) st = check_tc_error(m);
+    return st;
+}
+
+extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K, const float* A, const float* W,
+                                     const float* bias, int epilogue, const float* C_in, float* C_out) {
+    if (!A || !W || !C_out || M == 0 || N == 0 || K == 0) return fail(BOA_ERR_ARG, "bad argument");
+    if (epilogue < 0 || epilogue > kEpiBiasResid) return fail(BOA_ERR_ARG, "bad epilogue %d", epilogue);
+    if ((epilogue == kEpiBias || epilogue == kEpiBiasGelu || epilogue == kEpiBiasResid) && !bias)
+        return fail(BOA_ERR_ARG, "epilogue needs a bias");
+    if ((epilogue == kEpiResid || epilogue == kEpiBiasResid) && !C_in) return fail(BOA_ERR_ARG, "epilogue needs C_in");
+    if (precision != BOA_PREC_FP32 && precision != BOA_PREC_BF16) return fail(BOA_ERR_ARG, "bad precision");
+    boa_model t;
+    t.precision = precision;
+    cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, 0);
+    DevBuf<float> dA, dW, dB, dC;
+    DevBuf<__nv_bfloat16> bA, bW;
+    boa_status st = BOA_OK;
+    auto body = [&]() -> boa_status {
+        TRY(dA.ensure(M * K)); TRY(dC.ensure(M * N)); TRY(dB.ensure(N)); TRY(dW.ensure(N * K));
+        CU(cudaMemcpy(dA.p, A, M * K * 4, cudaMemcpyHostToDevice));
+        CU(cudaMemset(dB.p, 0, N * 4));
+        if (bias) CU(cudaMemcpy(dB.p, bias, N * 4, cudaMemcpyHostToDevice));
+        CU(cudaMemset(dC.p, 0, M * N * 4));
+        if (C_in) CU(cudaMemcpy(dC.p, C_in, M * N * 4, cudaMemcpyHostToDevice));
+        if (precision == BOA_PREC_BF16) {
+            TRY(t.err.ensure(1));
+            CU(cudaMemset(t.err.p, 0, 4));
+            TRY(bA.ensure(M * K)); TRY(bW.ensure(N * K));
+            CU(cudaMemcpy(dW.p, W, N * K * 4, cudaMemcpyHostToDevice));
+            k_to_bf16<<<256, 256>>>(dA.p, bA.p, M * K);
+            k_to_bf16<<<256, 256>>>(dW.p, bW.p, N * K);
+            switch (epilogue) {
+                case kEpiStore: TRY(gemm_tc<kEpiStore>(&t, BOA_KC_OTHER, bA.p, bW.p, dB.p, dC.p, nullptr, M, N, K)); break;
+                case kEpiBias: TRY(gemm_tc<kEpiBias>(&t, BOA_KC_OTHER, bA.p, bW.p, dB.p, dC.p, nullptr, M, N, K)); break;
+                case kEpiResid: TRY(gemm_tc<kEpiResid>(&t, BOA_KC_OTHER, bA.p, bW.p, dB.p, dC.p, nullptr, M, N, K)); break;
+                case kEpiBiasGelu: TRY(gemm_tc<kEpiBiasGelu>(&t, BOA_KC_OTHER, bA.p, bW.p, dB.p, dC.p, nullptr, M, N, K)); break;
+                default: TRY(gemm_tc<kEpiBiasResid>(&t, BOA_KC_OTHER, bA.p, bW.p, dB.p, dC.p, nullptr, M, N, K)); break;
+            }
+        } else {
+            std::vector<float> wt(N * K);
+            transpose(W, (int)N, (int)K, wt.data());
+            CU(cudaMemcpy(dW.p, wt.data(), N * K * 4, cudaMemcpyHostToDevice));
+            switch (epilogue) {
+                case kEpiStore: TRY(gemm<kEpiStore>(&t, BOA_KC_OTHER, dA.p, dW.p, dB.p, dC.p, M, N, K)); break;
+                case kEpiBias: TRY(gemm<kEpiBias>(&t, BOA_KC_OTHER, dA.p, dW.p, dB.p, dC.p, M, N, K)); break;
+                case kEpiResid: TRY(gemm<kEpiResid>(&t, BOA_KC_OTHER, dA.p, dW.p, dB.p, dC.p, M, N, K)); break;
+                case kEpiBiasGelu: TRY(gemm<kEpiBiasGelu>(&t, BOA_KC_OTHER, dA.p, dW.p, dB.p, dC.p, M, N, K)); break;
+                default: TRY(gemm<kEpiBiasResid>(&t, BOA_KC_OTHER, dA.p, dW.p, dB.p, dC.p, M, N, K)); break;
+            }
+        }
+        CU(cudaDeviceSynchronize());
+        if (precision == BOA_PREC_BF16) {
+            int h = 0;
+            CU(cudaMemcpy(&h, t.err.p, 4, cudaMemcpyDeviceToHost));
+            if (h) return fail(BOA_ERR_CUDA, "tensor-core GEMM wait timed out");
+        }
+        CU(cudaMemcpy(C_out, dC.p, M * N * 4, cudaMemcpyDeviceToHost));
+        return BOA_OK;
+    };
+    st = body();
+    dA.release(); dW.release(); dB.release(); dC.release(); bA.release(); bW.release(); t.err.release();
     return st;
 }
 

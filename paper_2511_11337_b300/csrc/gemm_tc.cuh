@@ -1,0 +1,264 @@
+// Tensor-core GEMM for the predictor's projections on sm_103a:
+//     C[M][N] = epi(A[M][K] . W[N][K]^T),  A and W in BF16, FP32 accumulation.
+//
+// One CTA of 128 threads owns one 128 x BN output tile:
+//   - thread 0 streams K-blocks of A and W into a ring of shared-memory
+//     stages with TMA (cp.async.bulk.tensor, 128-byte swizzle), signalling
+//     "full" mbarriers;
+//   - thread 32 issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction)
+//     into a TMEM accumulator and frees each stage with tcgen05.commit;
+//   - all four warps then read their 32 TMEM lanes (rows) with tcgen05.ld and
+//     apply the epilogue.
+// Every output element sees the same instruction sequence (same K order,
+// same MMA shape, same epilogue) wherever its row sits in the batch, so the
+// compression and decompression passes stay bit-identical.
+//
+// Waits on mbarriers are bounded (about 2 s of globaltimer); on expiry the
+// kernel records an error code in *err, skips the remaining work, releases
+// its TMEM and returns.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "gemm_fp32.cuh"
+
+namespace boa {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcBM = 128;
+constexpr int kTcBK = 64;                  // 64 bf16 = 128 bytes = one swizzle atom row
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true once the phase with the given parity has completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try(bar, parity))
+        if (globaltimer() - t0 > kWaitNs) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile written by TMA with the
+// 128-byte swizzle; rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);         // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                          // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                          // swizzle mode: 128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4)                      // D format F32
+         | (1u << 7)                      // A format BF16
+         | (1u << 10)                     // B format BF16
+         | ((uint32_t)(N >> 3) << 17)     // N / 8
+         | ((uint32_t)(M >> 4) << 24);    // M / 16
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+struct TcSmem {
+    static constexpr int kA = kTcBM * kTcBK * 2;     // 16 KB
+    static constexpr int kB = BN * kTcBK * 2;
+    static constexpr int kStage = kA + kB;
+    // about 110 KB of stages so that two CTAs share an SM (one's epilogue
+    // overlaps the other's loads and MMAs); TMEM: 2 x kTmemCols <= 512
+    static constexpr int kStagesRaw = (110 * 1024) / kStage;
+    static constexpr int kStages = kStagesRaw < 2 ? 2 : (kStagesRaw > 6 ? 6 : kStagesRaw);
+    static constexpr int kTmemCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    // stages, then barriers (full, empty, done) and the TMEM address slot
+    static constexpr int kBars = 2 * kStages + 1;
+    static constexpr size_t kBytes = 1024 /*alignment slack*/ + (size_t)kStages * kStage + 8 * kBars + 16;
+};
+
+// out_bf16 (optional): a BF16 copy of the stored result (feeds the next GEMM).
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kTcThreads)
+k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const float* __restrict__ bias, float* __restrict__ Cm, __nv_bfloat16* __restrict__ out_bf16,
+               int M, int N, int K, int* __restrict__ err) {
+    using L = TcSmem<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)L::kStages * L::kStage);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + L::kStages;
+    uint64_t* done = bars + 2 * L::kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::kBars);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
+    const int nk = K / kTcBK;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int i = 0; i < L::kBars; i++) mbar_init(&bars[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(L::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    int armed_last = -1;   // producer: last K-block whose loads were issued
+    if (threadIdx.x == 0) {
+        // TMA producer
+        for (int kb = 0; kb < nk; kb++) {
+            const int s = kb % L::kStages;
+            if (kb >= L::kStages && !mbar_wait(&empty[s], ((kb / L::kStages) - 1) & 1)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            uint8_t* sa = smem + (size_t)s * L::kStage;
+            mbar_expect_tx(&full[s], L::kStage);
+            tma_load_2d(&tmA, &full[s], sa, kb * kTcBK, m0);
+            tma_load_2d(&tmB, &full[s], sa + L::kA, kb * kTcBK, n0);
+            armed_last = kb;
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        constexpr uint32_t idesc = umma_idesc_bf16(kTcBM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk && ok; kb++) {
+            const int s = kb % L::kStages;
+            if (!mbar_wait(&full[s], (kb / L::kStages) & 1)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(smem + (size_t)s * L::kStage);
+            const uint32_t sb = sa + L::kA;
+#pragma unroll
+            for (int k = 0; k < kTcBK / 16; k++)
+                umma_bf16(tmem, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
+                          (kb | k) != 0 ? 1u : 0u);
+            umma_commit(&empty[s]);
+        }
+        if (!ok) atomicExch(&abort_flag, 1);
+        umma_commit(&done[0]);
+    }
+
+    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31
+    const bool finished = mbar_wait(&done[0], 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!finished || abort_flag) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            // let copies and MMAs still in flight land before TMEM and shared
+            // memory are released (each wait again bounded)
+            for (int kb = armed_last; kb >= 0 && kb > armed_last - L::kStages; kb--)
+                mbar_wait(&full[kb % L::kStages], (kb / L::kStages) & 1);
+            if (!finished) mbar_wait(&done[0], 0);
+        }
+    } else {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            const int n = n0 + c0;
+            if (row >= M || n >= N) continue;
+            float* cp = Cm + (size_t)row * N + n;
+#pragma unroll
+            for (int q = 0; q < 16; q += 4) {
+                if (n + q >= N) break;   // N % 4 == 0
+                float o[4];
+                float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (EPI == kEpiResid || EPI == kEpiBiasResid) old = *reinterpret_cast<const float4*>(cp + q);
+                const float* ov = reinterpret_cast<const float*>(&old);
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    float x = v[q + j];
+                    if (EPI == kEpiBias || EPI == kEpiBiasGelu || EPI == kEpiBiasResid) x = __fadd_rn(x, bias[n + q + j]);
+                    if (EPI == kEpiBiasGelu) x = gelu_f(x);
+                    if (EPI == kEpiResid || EPI == kEpiBiasResid) x = __fadd_rn(ov[j], x);
+                    o[j] = x;
+                }
+                *reinterpret_cast<float4*>(cp + q) = make_float4(o[0], o[1], o[2], o[3]);
+                if (out_bf16) {
+                    __nv_bfloat162* bp = reinterpret_cast<__nv_bfloat162*>(out_bf16 + (size_t)row * N + n + q);
+                    bp[0] = __floats2bfloat162_rn(o[0], o[1]);
+                    bp[1] = __floats2bfloat162_rn(o[2], o[3]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kTmemCols));
+}
+
+}  // namespace boa

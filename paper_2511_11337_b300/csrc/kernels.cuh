@@ -6,6 +6,8 @@
 // carry state along time (conv window, SSM state, coder) loop over tau inside
 // one thread or warp, so results never depend on Tc.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace boa {
@@ -57,7 +59,7 @@ __device__ __forceinline__ int row_token(const TokenSrc& ts, int s, int tau) {
 template <int VPT>
 __global__ void k_embed_ln(TokenSrc ts, int S, int Tc, const float* __restrict__ embed,
                            const float* __restrict__ g, const float* __restrict__ b,
-                           float* __restrict__ x, float* __restrict__ xn) {
+                           float* __restrict__ x, float* __restrict__ xn, __nv_bfloat16* __restrict__ xn_b) {
     constexpr int d = VPT * 32;
     const int lane = threadIdx.x & 31;
     const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -71,15 +73,19 @@ __global__ void k_embed_ln(TokenSrc ts, int S, int Tc, const float* __restrict__
 #pragma unroll
     for (int i = 0; i < VPT; i++) {
         x[(size_t)row * d + lane + 32 * i] = v[i];
-        xn[(size_t)row * d + lane + 32 * i] = y[i];
+        if (xn_b) xn_b[(size_t)row * d + lane + 32 * i] = __float2bfloat16_rn(y[i]);
+        else xn[(size_t)row * d + lane + 32 * i] = y[i];
     }
 }
 
 // x = LN_b(x); then, when another block follows, xn = LN_a'(x).
+// Optional BF16 copies for the tensor-core path: x_b (input of the head or the
+// FFN) and xn_b (input of the next in_proj, replacing xn).
 template <int VPT>
 __global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __restrict__ gb,
                         const float* __restrict__ bb, const float* __restrict__ ga,
-                        const float* __restrict__ ba, float* __restrict__ xn) {
+                        const float* __restrict__ ba, float* __restrict__ xn,
+                        __nv_bfloat16* __restrict__ x_b, __nv_bfloat16* __restrict__ xn_b) {
     constexpr int d = VPT * 32;
     const int lane = threadIdx.x & 31;
     const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -89,12 +95,18 @@ __global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __re
     for (int i = 0; i < VPT; i++) v[i] = x[(size_t)row * d + lane + 32 * i];
     warp_layernorm<VPT>(v, gb, bb, lane, y);
 #pragma unroll
-    for (int i = 0; i < VPT; i++) x[(size_t)row * d + lane + 32 * i] = y[i];
+    for (int i = 0; i < VPT; i++) {
+        x[(size_t)row * d + lane + 32 * i] = y[i];
+        if (x_b) x_b[(size_t)row * d + lane + 32 * i] = __float2bfloat16_rn(y[i]);
+    }
     if (ga) {
         float z[VPT];
         warp_layernorm<VPT>(y, ga, ba, lane, z);
 #pragma unroll
-        for (int i = 0; i < VPT; i++) xn[(size_t)row * d + lane + 32 * i] = z[i];
+        for (int i = 0; i < VPT; i++) {
+            if (xn_b) xn_b[(size_t)row * d + lane + 32 * i] = __float2bfloat16_rn(z[i]);
+            else xn[(size_t)row * d + lane + 32 * i] = z[i];
+        }
     }
 }
 
@@ -105,7 +117,7 @@ __global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __re
 template <int K>
 __global__ void k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ w,
                             const float* __restrict__ bconv, float* __restrict__ win,
-                            float* __restrict__ u, int S, int Tc) {
+                            float* __restrict__ u, __nv_bfloat16* __restrict__ u_b, int S, int Tc) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = blockIdx.y;
     if (c >= E) return;
@@ -125,7 +137,9 @@ __global__ void k_conv_silu(const float* __restrict__ xz, int E, const float* __
 #pragma unroll
         for (int k = 0; k + 1 < K - 1; k++) h[k] = h[k + 1];
         h[K - 2] = xi;
-        u[row * E + c] = silu_f(acc);
+        const float uo = silu_f(acc);
+        u[row * E + c] = uo;
+        if (u_b) u_b[row * E + c] = __float2bfloat16_rn(uo);
     }
 #pragma unroll
     for (int k = 0; k < K - 1; k++) win[((size_t)s * (K - 1) + k) * E + c] = h[k];
@@ -147,7 +161,7 @@ __global__ void __launch_bounds__(kScanThreads)
 k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* __restrict__ dbc,
        const float* __restrict__ dt_w, const float* __restrict__ dt_b, const float* __restrict__ A2,
        const float* __restrict__ Dv, float* __restrict__ hstate, float* __restrict__ yg,
-       int E, int S, int Tc) {
+       __nv_bfloat16* __restrict__ yg_b, int E, int S, int Tc) {
     constexpr int W = R + 2 * NS;   // dbc row width
     __shared__ float sm[kScanRowsSmem][W];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -192,7 +206,9 @@ k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* _
             }
             y = __fmaf_rn(dv, uc, y);
             const float z = xz[row * 2 * E + E + c];
-            yg[row * E + c] = __fmul_rn(y, silu_f(z));
+            const float o = __fmul_rn(y, silu_f(z));
+            if (yg_b) yg_b[row * E + c] = __float2bfloat16_rn(o);
+            else yg[row * E + c] = o;
         }
     }
     if (live) {
@@ -552,6 +568,11 @@ __global__ void k_dec_finish(const uint64_t* cin_size, const uint64_t* lens, Cod
         if (c.pos != size - 1) fl |= kFlagCorrupt;
     }
     flags_out[s] = fl;
+}
+
+__global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(in[i]);
 }
 
 // Gather each stream's used bytes from its output slot into one packed buffer.

@@ -1,0 +1,131 @@
+"""Tensor-core (tcgen05) projection GEMM and the BF16 predictor path.
+
+* The GEMM kernels against float64 products of the same (BF16-rounded or
+  FP32) operands, for every epilogue and for shapes with ragged M and N.
+* Row-position invariance: a row's result does not depend on the batch it
+  sits in (what keeps the encoder and decoder in lockstep).
+* The BF16 model: lossless round trip, identical CDFs in encoder and decoder,
+  batch invariance, code length within 0.5 % of the FP64 oracle; the log2 p
+  error against the oracle is reported against a stated bound.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2511_11337_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+BF16_LOG2P_TOL = 0.03    # BF16 operands: relative rounding 2^-9 per input, summed over d <= 512 terms
+
+
+def bf16_round(x):
+    x = np.ascontiguousarray(x, np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def ref_gemm(A, W, bias, epi, C_in):
+    acc = A.astype(np.float64) @ W.astype(np.float64).T
+    if epi in (1, 3, 4):
+        acc = acc + bias.astype(np.float64)
+    if epi == 3:
+        from scipy.special import erf
+        acc = 0.5 * acc * (1 + erf(acc / np.sqrt(2)))
+    if epi in (2, 4):
+        acc = C_in.astype(np.float64) + acc
+    return acc
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2511_11337_b300 import api as A, build
+    build.build()
+    return A
+
+
+SHAPES = [(128, 128, 64), (300, 1024, 256), (4096, 48, 512), (1000, 256, 512), (77, 64, 64), (129, 36, 64),
+          (513, 256, 1024)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gemm_kernels(api, shape, precision):
+    M, N, K = shape
+    g = np.random.default_rng(M * 7 + N + K)
+    A = g.normal(0, 1, (M, K)).astype(np.float32)
+    W = g.normal(0, 0.05, (N, K)).astype(np.float32)
+    bias = g.normal(0, 0.1, N).astype(np.float32)
+    C_in = g.normal(0, 1, (M, N)).astype(np.float32)
+    Ar, Wr = (bf16_round(A), bf16_round(W)) if precision == 1 else (A, W)
+    mag = np.abs(Ar.astype(np.float64)) @ np.abs(Wr.astype(np.float64)).T
+    for epi in range(5):
+        got = api.gemm(A, W, bias, epi, C_in, precision=precision)
+        ref = ref_gemm(Ar, Wr, bias, epi, C_in)
+        bound = 4 * 2.0 ** -24 * (K + 2) * (mag + np.abs(bias) + np.abs(C_in) + 1e-30) + 1e-6
+        err = np.abs(got - ref)
+        assert (err <= bound).all(), (epi, float(err.max()), float((err / bound).max()))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gemm_rows_independent_of_batch(api, precision):
+    g = np.random.default_rng(5)
+    A = g.normal(0, 1, (1000, 256)).astype(np.float32)
+    W = g.normal(0, 0.05, (1024, 256)).astype(np.float32)
+    full = api.gemm(A, W, precision=precision)
+    for lo, hi in ((0, 1), (5, 133), (999, 1000), (300, 428)):
+        part = api.gemm(A[lo:hi], W, precision=precision)
+        assert np.array_equal(part, full[lo:hi])
+
+
+@pytest.fixture(scope="module")
+def tiny_bf16(api, tiny_model_path):
+    return api.Model(tiny_model_path, precision=api.PREC_BF16)
+
+
+def test_bf16_round_trip_gap_and_logprobs(tiny_bf16, tiny_model_path):
+    streams = synth.records_workload()
+    comp = tiny_bf16.compress(streams)
+    assert tiny_bf16.decompress(comp, [len(s) for s in streams]) == streams
+    om = O.Model(tiny_model_path)
+    ref = om.compress_batch(streams)
+    gap = (sum(map(len, comp)) - sum(map(len, ref))) / sum(map(len, ref))
+    assert abs(gap) <= 0.005, gap
+    err = np.abs(tiny_bf16.logprobs(streams[0][:2000]) - om.logprobs(streams[0][:2000])).max()
+    print(f"BF16 max |dlog2p| = {err:.3e}, code-length gap = {gap:+.3e}")
+    assert err <= BF16_LOG2P_TOL
+
+
+def test_bf16_encoder_decoder_lockstep_and_batch_invariance(tiny_bf16):
+    streams = [synth.records_stream(60 + i, n) for i, n in enumerate([3000, 1, 0, 2, 777, 4096, 130])]
+    n_steps = sum(max(len(s) - 1, 0) for s in streams)
+    tiny_bf16.enable_cdf_trace(True)
+    try:
+        comp = tiny_bf16.compress(streams)
+        enc = tiny_bf16.read_cdf_trace(n_steps)
+        out = tiny_bf16.decompress(comp, [len(s) for s in streams])
+        dec = tiny_bf16.read_cdf_trace(n_steps)
+    finally:
+        tiny_bf16.enable_cdf_trace(False)
+    assert out == streams and np.array_equal(enc, dec)
+    alone = tiny_bf16.compress([streams[0]])[0]
+    assert alone == comp[0] and tiny_bf16.compress([streams[0]] * 40)[17] == alone
+
+
+def test_bf16_paper_scale_batch(api, model_dir):
+    path = synth.make_model_file(os.path.join(model_dir, "paper_bf16.boaw"), synth.PAPER_SCALE, seed=2)
+    m = api.Model(path, precision=api.PREC_BF16)
+    buf = synth.atlas_workload(300, 2048, seed=77)
+    streams = synth.split_equal(buf, 300)
+    comp = m.compress(streams)
+    assert m.decompress(comp, [len(s) for s in streams]) == streams
+    om = O.Model(path)
+    ref = om.compress(streams[7])
+    assert abs(len(comp[7]) - len(ref)) / len(ref) <= 0.005
+    ffn = synth.make_model_file(os.path.join(model_dir, "ffn_bf16.boaw"), synth.PAPER_SHAPE_FFN, seed=5)
+    mf = api.Model(ffn, precision=api.PREC_BF16)
+    comp = mf.compress(streams[:50])
+    assert mf.decompress(comp, [len(s) for s in streams[:50]]) == streams[:50]
