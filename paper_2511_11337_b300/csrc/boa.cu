@@ -221,9 +221,7 @@ static void prof_collect(boa_model* m) {
     m->ev_used = 0;
 }
 
-static bool supported_scan(int N, int r) {
-    return N == 16 && (r == 1 || r == 2 || r == 4 || r == 8 || r == 16);
-}
+static bool supported_scan(int N, int r) { return N == 16 && (r == 4 || r == 8 || r == 16); }
 
 static bool supported_d(int d) { return d == 64 || d == 128 || d == 256; }
 
@@ -326,13 +324,14 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
         q.ln_a_w = copy(d); q.ln_a_b = copy(d);
         sro[l].in_w = so;
         q.in_wt = copy_t(2 * E, d);
-        q.conv_w = copy((size_t)E * K); q.conv_b = copy(E);
+        q.conv_w = copy_t(E, K); q.conv_b = copy(E);                   // taps stored [K][E]
         sro[l].x_w = so;
         q.x_wt = copy_t(R2, E);
-        q.dt_w = copy((size_t)E * r); q.dt_b = copy(E);
-        q.A2 = dof;
-        for (size_t i = 0; i < (size_t)E * N; i++)
-            dev[dof + i] = (float)(-std::exp((double)src[so + i]) * 1.4426950408889634);
+        q.dt_w = copy_t(E, r); q.dt_b = copy(E);                       // W_dt stored [r][E]
+        q.A2 = dof;                                                     // A log2(e) stored [N][E]
+        for (size_t c = 0; c < (size_t)E; c++)
+            for (size_t n = 0; n < (size_t)N; n++)
+                dev[dof + n * E + c] = (float)(-std::exp((double)src[so + c * N + n]) * 1.4426950408889634);
         so += (size_t)E * N; dof += (size_t)E * N;
         q.D = copy(E);
         sro[l].out_w = so;
@@ -575,40 +574,45 @@ static boa_status ln_ln(boa_model* m, long long rows, int l) {
     return check_launch(m, "ln_ln");
 }
 
+// Streams per CTA for the per-channel kernels: one step over many streams
+// (decompression) groups 8 streams so the per-channel weights load once.
+static int stream_group(int S, int Tc) { return (Tc == 1 && S >= 1024) ? 8 : 1; }
+
 static boa_status conv(boa_model* m, int l, int S, int Tc) {
     const DevLayer& L = m->layers[l];
-    dim3 grid((m->E + 127) / 128, S);
+    const int G = stream_group(S, Tc);
+    dim3 grid((m->E + 127) / 128, (S + G - 1) / G);
     float* win = m->conv.p + (size_t)l * S * (m->K - 1) * m->E;
     const double rows = (double)S * Tc;
     ProfScope ps(m, BOA_KC_CONV, rows * m->E * (2.0 * m->K + 4), 4.0 * (2 * rows * m->E + 2.0 * S * (m->K - 1) * m->E));
     __nv_bfloat16* ub = m->precision == BOA_PREC_BF16 ? m->u_b.p : nullptr;
-    switch (m->K) {
-        case 2: k_conv_silu<2><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, ub, S, Tc); break;
-        case 3: k_conv_silu<3><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, ub, S, Tc); break;
-        case 4: k_conv_silu<4><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, ub, S, Tc); break;
+#define CONV_CASE(KK, GG) \
+    k_conv_silu<KK, GG><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, ub, S, Tc)
+    if (G == 8) {
+        switch (m->K) { case 2: CONV_CASE(2, 8); break; case 3: CONV_CASE(3, 8); break; default: CONV_CASE(4, 8); break; }
+    } else {
+        switch (m->K) { case 2: CONV_CASE(2, 1); break; case 3: CONV_CASE(3, 1); break; default: CONV_CASE(4, 1); break; }
     }
+#undef CONV_CASE
     return check_launch(m, "conv");
 }
 
 static boa_status scan(boa_model* m, int l, int S, int Tc) {
     const DevLayer& L = m->layers[l];
-    dim3 grid((m->E + kScanThreads - 1) / kScanThreads, S);
+    const int G = stream_group(S, Tc);
+    dim3 grid((m->E + kScanThreads - 1) / kScanThreads, (S + G - 1) / G);
     float* hs = m->h.p + (size_t)l * S * m->N * m->E;
     const double rows = (double)S * Tc;
     ProfScope ps(m, BOA_KC_SCAN, rows * m->E * (2.0 * m->r + 5.0 * m->N + 12),
                  4.0 * (rows * (3.0 * m->E + m->R2) + 2.0 * S * m->N * m->E));
     __nv_bfloat16* ygb = m->precision == BOA_PREC_BF16 ? m->yg_b.p : nullptr;
-#define SCAN_CASE(RR)                                                                                           \
-    case RR:                                                                                                    \
-        k_scan<16, RR><<<grid, kScanThreads, 0, m->stream>>>(m->u.p, m->xz.p, m->dbc.p, L.dt_w, L.dt_b, L.A2, L.D, \
-                                                             hs, m->yg.p, ygb, m->E, S, Tc);                    \
-        break;
-    switch (m->r) {
-        SCAN_CASE(1)
-        SCAN_CASE(2)
-        SCAN_CASE(4)
-        SCAN_CASE(8)
-        SCAN_CASE(16)
+#define SCAN_CASE(RR, GG)                                                                                         \
+    k_scan<16, RR, GG><<<grid, kScanThreads, 0, m->stream>>>(m->u.p, m->xz.p, m->dbc.p, L.dt_w, L.dt_b, L.A2, L.D, \
+                                                             hs, m->yg.p, ygb, m->E, S, Tc)
+    if (G == 8) {
+        switch (m->r) { case 4: SCAN_CASE(4, 8); break; case 8: SCAN_CASE(8, 8); break; default: SCAN_CASE(16, 8); break; }
+    } else {
+        switch (m->r) { case 4: SCAN_CASE(4, 1); break; case 8: SCAN_CASE(8, 1); break; default: SCAN_CASE(16, 1); break; }
     }
 #undef SCAN_CASE
     return check_launch(m, "scan");

@@ -54,12 +54,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// SiLU and softplus on the MUFU unit (ex2 / lg2 / rcp approximations): a
+// fixed instruction sequence, so every kernel that calls them produces the
+// same bits for the same input.
 __device__ __forceinline__ float silu_f(float v) {
-    return __fdiv_rn(v, __fadd_rn(1.0f, __expf(-v)));
+    return __fdividef(v, __fadd_rn(1.0f, __expf(-v)));
 }
 
 __device__ __forceinline__ float softplus_f(float v) {
-    return v > 20.0f ? v : log1pf(expf(v));
+    return v > 20.0f ? v : __logf(__fadd_rn(1.0f, __expf(v)));
 }
 
 __device__ __forceinline__ float gelu_f(float v) {
