@@ -10,6 +10,7 @@ from ._lib import BoaError, check, load
 
 PREC_FP32 = 0
 PREC_BF16 = 1
+PREC_TF32X3 = 2
 
 
 def _p(a: np.ndarray):
@@ -226,4 +227,4 @@ def compressed_slot_offsets(lens) -> np.ndarray:
     return slot_offsets([max_compressed_size(int(n)) for n in lens])
 
 
-__all__ = ["decode_cdfs_static", "pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32", "PREC_BF16", "gemm"]
+__all__ = ["decode_cdfs_static", "pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32", "PREC_BF16", "PREC_TF32X3", "gemm"]

@@ -131,7 +131,12 @@ struct boa_model {
     struct BLayer { __nv_bfloat16 *in_w, *x_w, *out_w, *w1, *w2; };
     std::vector<BLayer> blayers;
     __nv_bfloat16* head_wb = nullptr;
-    struct MapEnt { const void* p; uint64_t rows, cols; uint32_t box; CUtensorMap map; };
+    // 3xTF32 path: pre-split weights (hi, lo), [out][in]
+    float* w3 = nullptr;
+    struct TLayer { float *in_hi, *in_lo, *x_hi, *x_lo, *out_hi, *out_lo, *w1_hi, *w1_lo, *w2_hi, *w2_lo; };
+    std::vector<TLayer> tlayers;
+    float *head_hi = nullptr, *head_lo = nullptr;
+    struct MapEnt { const void* p; uint64_t rows, cols; uint32_t box; int f32; CUtensorMap map; };
     std::vector<MapEnt> maps;
 
     // workspace
@@ -255,6 +260,7 @@ extern "C" void boa_free_model(boa_model* m) {
     for (auto e : m->ev_pool) cudaEventDestroy(e);
     if (m->weights) cudaFree(m->weights);
     if (m->wb) cudaFree(m->wb);
+    if (m->w3) cudaFree(m->w3);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -300,7 +306,7 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
 
     boa_opts o = {0, BOA_PREC_FP32, nullptr, 0};
     if (opts) o = *opts;
-    if (o.precision != BOA_PREC_FP32 && o.precision != BOA_PREC_BF16)
+    if (o.precision != BOA_PREC_FP32 && o.precision != BOA_PREC_BF16 && o.precision != BOA_PREC_TF32X3)
         return fail(BOA_ERR_ARG, "precision %d not supported", o.precision);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(BOA_ERR_CUDA, "no CUDA device available");
@@ -422,6 +428,56 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
         }
         m->head_wb = m->wb + at[k++];
     }
+    if (m->precision == BOA_PREC_TF32X3) {
+        // x = hi + lo with hi = x rounded to TF32 (nearest, ties away), lo = x - hi
+        std::vector<std::pair<size_t, size_t>> mats;
+        for (int l = 0; l < nl; l++) {
+            mats.push_back({sro[l].in_w, (size_t)2 * E * d});
+            mats.push_back({sro[l].x_w, (size_t)R2 * E});
+            mats.push_back({sro[l].out_w, (size_t)d * E});
+            if (F) { mats.push_back({sro[l].w1, (size_t)F * d}); mats.push_back({sro[l].w2, (size_t)d * F}); }
+        }
+        mats.push_back({head_src, (size_t)256 * d});
+        size_t tot = 0;
+        std::vector<size_t> at;
+        for (auto& mt : mats) { at.push_back(tot); tot += 2 * ((mt.second + 31) / 32 * 32); }
+        std::vector<float> hb(tot, 0.f);
+        for (size_t i = 0; i < mats.size(); i++) {
+            const size_t n = mats[i].second, half = (n + 31) / 32 * 32;
+            for (size_t j = 0; j < n; j++) {
+                const float x = src[mats[i].first + j];
+                uint32_t u;
+                memcpy(&u, &x, 4);
+                u = (u + 0x1000u) & ~0x1FFFu;
+                float hi;
+                memcpy(&hi, &u, 4);
+                hb[at[i] + j] = hi;
+                hb[at[i] + half + j] = x - hi;
+            }
+        }
+        if (cudaMalloc(&m->w3, tot * 4) != cudaSuccess ||
+            cudaMemcpy(m->w3, hb.data(), tot * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            boa_free_model(m);
+            return fail(BOA_ERR_OOM, "tf32 weight upload failed");
+        }
+        size_t k = 0;
+        auto pair = [&](float*& hi, float*& lo) {
+            const size_t half = (mats[k].second + 31) / 32 * 32;
+            hi = m->w3 + at[k];
+            lo = m->w3 + at[k] + half;
+            k++;
+        };
+        m->tlayers.resize(nl);
+        for (int l = 0; l < nl; l++) {
+            auto& T = m->tlayers[l];
+            pair(T.in_hi, T.in_lo);
+            pair(T.x_hi, T.x_lo);
+            pair(T.out_hi, T.out_lo);
+            T.w1_hi = T.w1_lo = T.w2_hi = T.w2_lo = nullptr;
+            if (F) { pair(T.w1_hi, T.w1_lo); pair(T.w2_hi, T.w2_lo); }
+        }
+        pair(m->head_hi, m->head_lo);
+    }
     *out = m;
     return BOA_OK;
 }
@@ -465,10 +521,13 @@ static std::mutex g_encode_mu;
 
 // 2-D BF16 tensor map over a row-major [rows][cols] matrix, boxes of
 // 64 columns (128 bytes, 128-byte swizzle) by box_rows rows.
-static boa_status tmap_bf16(boa_model* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows,
-                            CUtensorMap* out) {
+static boa_status tmap_2d(boa_model* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows, bool f32,
+                          CUtensorMap* out) {
     for (auto& e : m->maps)
-        if (e.p == ptr && e.rows == rows && e.cols == cols && e.box == box_rows) { *out = e.map; return BOA_OK; }
+        if (e.p == ptr && e.rows == rows && e.cols == cols && e.box == box_rows && e.f32 == (int)f32) {
+            *out = e.map;
+            return BOA_OK;
+        }
     {
         std::lock_guard<std::mutex> lock(g_encode_mu);
         if (!g_encode_tiled) {
@@ -480,14 +539,16 @@ static boa_status tmap_bf16(boa_model* m, const void* ptr, uint64_t rows, uint64
             g_encode_tiled = (PFN_cuTensorMapEncodeTiled_v12000)fn;
         }
     }
-    if (((uintptr_t)ptr & 15) || (cols * 2) % 16) return fail(BOA_ERR_ARG, "tensor map needs 16-byte aligned rows");
+    const uint64_t esz = f32 ? 4 : 2;
+    if (((uintptr_t)ptr & 15) || (cols * esz) % 16) return fail(BOA_ERR_ARG, "tensor map needs 16-byte aligned rows");
     boa_model::MapEnt e;
-    e.p = ptr; e.rows = rows; e.cols = cols; e.box = box_rows;
+    e.p = ptr; e.rows = rows; e.cols = cols; e.box = box_rows; e.f32 = (int)f32;
     cuuint64_t dims[2] = {cols, rows};
-    cuuint64_t strides[1] = {cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kTcBK, box_rows};
+    cuuint64_t strides[1] = {cols * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), box_rows};   // 128-byte rows: one swizzle atom
     cuuint32_t es[2] = {1, 1};
-    CUresult r = g_encode_tiled(&e.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+    CUresult r = g_encode_tiled(&e.map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                const_cast<void*>(ptr), dims, strides, box, es,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(BOA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -523,14 +584,45 @@ static boa_status gemm_tc(boa_model* m, int cls, const __nv_bfloat16* A, const _
                  2.0 * ((double)M * K + (double)K * N) + 4.0 * (double)M * N * (resid ? 2 : 1) + (outb ? 2.0 * M * N : 0));
     const int BN = tc_bn(N);
     CUtensorMap ta, tb;
-    TRY(tmap_bf16(m, A, (uint64_t)M, (uint64_t)K, kTcBM, &ta));
-    TRY(tmap_bf16(m, W, (uint64_t)N, (uint64_t)K, (uint32_t)BN, &tb));
+    TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, false, &ta));
+    TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)K, (uint32_t)BN, false, &tb));
     switch (BN) {
         case 48: launch_tc<48, EPI>(m, ta, tb, bias, C, outb, M, N, K); break;
         case 64: launch_tc<64, EPI>(m, ta, tb, bias, C, outb, M, N, K); break;
         default: launch_tc<128, EPI>(m, ta, tb, bias, C, outb, M, N, K); break;
     }
     return check_launch(m, "gemm_tc");
+}
+
+template <int BN, int EPI>
+static void launch_t3(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th, const CUtensorMap& tl,
+                      const float* bias, float* C, long long M, int N, int K) {
+    using L = T3Smem<BN>;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_gemm_tc_tf32x3<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
+    });
+    dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
+    k_gemm_tc_tf32x3<BN, EPI><<<grid, kT3Threads, L::kBytes, m->stream>>>(ta, th, tl, bias, C, (int)M, N, K, m->err.p);
+}
+
+// FP32-accurate tensor-core GEMM (3xTF32); A is FP32, W pre-split.
+template <int EPI>
+static boa_status gemm_t3(boa_model* m, int cls, const float* A, const float* Whi, const float* Wlo, const float* bias,
+                          float* C, long long M, int N, int K) {
+    if (M <= 0) return BOA_OK;
+    if (N % 4 != 0 || K % kT3BK != 0) return fail(BOA_ERR_FORMAT, "3xTF32 gemm shape N=%d K=%d unsupported", N, K);
+    const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
+    ProfScope ps(m, cls, 2.0 * M * N * K,
+                 4.0 * ((double)M * K + 2.0 * K * N) + 4.0 * (double)M * N * (resid ? 2 : 1));
+    const int BN = N > 48 ? 64 : 48;
+    CUtensorMap ta, th, tl;
+    TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, true, &ta));
+    TRY(tmap_2d(m, Whi, (uint64_t)N, (uint64_t)K, (uint32_t)BN, true, &th));
+    TRY(tmap_2d(m, Wlo, (uint64_t)N, (uint64_t)K, (uint32_t)BN, true, &tl));
+    if (BN == 48) launch_t3<48, EPI>(m, ta, th, tl, bias, C, M, N, K);
+    else launch_t3<64, EPI>(m, ta, th, tl, bias, C, M, N, K);
+    return check_launch(m, "gemm_t3");
 }
 
 template <int VPT>
@@ -638,6 +730,17 @@ static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc) {
                 TRY(gemm_tc<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x_b.p, B.w1, L.b1, m->hid.p, m->hid_b.p, rows, m->F, d));
                 TRY(gemm_tc<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid_b.p, B.w2, L.b2, m->x.p, nullptr, rows, d, m->F));
             }
+        } else if (m->precision == BOA_PREC_TF32X3) {
+            const auto& T = m->tlayers[l];
+            TRY(gemm_t3<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn.p, T.in_hi, T.in_lo, nullptr, m->xz.p, rows, 2 * E, d));
+            TRY(conv(m, l, S, Tc));
+            TRY(gemm_t3<kEpiStore>(m, BOA_KC_GEMM_X, m->u.p, T.x_hi, T.x_lo, nullptr, m->dbc.p, rows, m->R2, E));
+            TRY(scan(m, l, S, Tc));
+            TRY(gemm_t3<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg.p, T.out_hi, T.out_lo, nullptr, m->x.p, rows, d, E));
+            if (m->F) {
+                TRY(gemm_t3<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x.p, T.w1_hi, T.w1_lo, L.b1, m->hid.p, rows, m->F, d));
+                TRY(gemm_t3<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid.p, T.w2_hi, T.w2_lo, L.b2, m->x.p, rows, d, m->F));
+            }
         } else {
             TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn.p, L.in_wt, nullptr, m->xz.p, rows, 2 * E, d));
             TRY(conv(m, l, S, Tc));
@@ -652,12 +755,14 @@ static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc) {
         TRY(ln_ln(m, rows, l));
     }
     if (tc) return gemm_tc<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x_b.p, m->head_wb, m->head_b, m->logits.p, nullptr, rows, 256, d);
+    if (m->precision == BOA_PREC_TF32X3)
+        return gemm_t3<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_hi, m->head_lo, m->head_b, m->logits.p, rows, 256, d);
     return gemm<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_wt, m->head_b, m->logits.p, rows, 256, d);
 }
 
 // Tensor-core waits that timed out leave a nonzero code in m->err.
 static boa_status check_tc_error(boa_model* m) {
-    if (m->precision != BOA_PREC_BF16) return BOA_OK;
+    if (m->precision == BOA_PREC_FP32) return BOA_OK;
     int h = 0;
     CU(cudaMemcpyAsync(&h, m->err.p, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
@@ -678,6 +783,10 @@ static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
     TRY(m->yg.ensure(rows * E));
     TRY(m->logits.ensure(rows * 256));
     if (m->F) TRY(m->hid.ensure(rows * m->F));
+    if (m->precision != BOA_PREC_FP32 && !m->err.p) {
+        TRY(m->err.ensure(1));
+        CU(cudaMemset(m->err.p, 0, sizeof(int)));
+    }
     if (m->precision == BOA_PREC_BF16) {
         TRY(m->xn_b.ensure(rows * d));
         TRY(m->u_b.ensure(rows * E));
@@ -1103,7 +1212,8 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
     if ((epilogue == kEpiBias || epilogue == kEpiBiasGelu || epilogue == kEpiBiasResid) && !bias)
         return fail(BOA_ERR_ARG, "epilogue needs a bias");
     if ((epilogue == kEpiResid || epilogue == kEpiBiasResid) && !C_in) return fail(BOA_ERR_ARG, "epilogue needs C_in");
-    if (precision != BOA_PREC_FP32 && precision != BOA_PREC_BF16) return fail(BOA_ERR_ARG, "bad precision");
+    if (precision != BOA_PREC_FP32 && precision != BOA_PREC_BF16 && precision != BOA_PREC_TF32X3)
+        return fail(BOA_ERR_ARG, "bad precision");
     boa_model t;
     t.precision = precision;
     cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, 0);
@@ -1131,6 +1241,35 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
                 case kEpiBiasGelu: TRY(gemm_tc<kEpiBiasGelu>(&t, BOA_KC_OTHER, bA.p, bW.p, dB.p, dC.p, nullptr, M, N, K)); break;
                 default: TRY(gemm_tc<kEpiBiasResid>(&t, BOA_KC_OTHER, bA.p, bW.p, dB.p, dC.p, nullptr, M, N, K)); break;
             }
+        } else if (precision == BOA_PREC_TF32X3) {
+            TRY(t.err.ensure(1));
+            CU(cudaMemset(t.err.p, 0, 4));
+            std::vector<float> hl(2 * N * K);
+            for (size_t i = 0; i < N * K; i++) {
+                uint32_t u;
+                memcpy(&u, &W[i], 4);
+                u = (u + 0x1000u) & ~0x1FFFu;
+                float hi;
+                memcpy(&hi, &u, 4);
+                hl[i] = hi;
+                hl[N * K + i] = W[i] - hi;
+            }
+            DevBuf<float> dW2;
+            TRY(dW2.ensure(2 * N * K));
+            CU(cudaMemcpy(dW2.p, hl.data(), 2 * N * K * 4, cudaMemcpyHostToDevice));
+            const float* hi = dW2.p;
+            const float* lo = dW2.p + N * K;
+            boa_status r = BOA_OK;
+            switch (epilogue) {
+                case kEpiStore: r = gemm_t3<kEpiStore>(&t, BOA_KC_OTHER, dA.p, hi, lo, dB.p, dC.p, M, N, K); break;
+                case kEpiBias: r = gemm_t3<kEpiBias>(&t, BOA_KC_OTHER, dA.p, hi, lo, dB.p, dC.p, M, N, K); break;
+                case kEpiResid: r = gemm_t3<kEpiResid>(&t, BOA_KC_OTHER, dA.p, hi, lo, dB.p, dC.p, M, N, K); break;
+                case kEpiBiasGelu: r = gemm_t3<kEpiBiasGelu>(&t, BOA_KC_OTHER, dA.p, hi, lo, dB.p, dC.p, M, N, K); break;
+                default: r = gemm_t3<kEpiBiasResid>(&t, BOA_KC_OTHER, dA.p, hi, lo, dB.p, dC.p, M, N, K); break;
+            }
+            cudaDeviceSynchronize();
+            dW2.release();
+            TRY(r);
         } else {
             std::vector<float> wt(N * K);
             transpose(W, (int)N, (int)K, wt.data());
@@ -1144,7 +1283,7 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
             }
         }
         CU(cudaDeviceSynchronize());
-        if (precision == BOA_PREC_BF16) {
+        if (precision != BOA_PREC_FP32) {
             int h = 0;
             CU(cudaMemcpy(&h, t.err.p, 4, cudaMemcpyDeviceToHost));
             if (h) return fail(BOA_ERR_CUDA, "tensor-core GEMM wait timed out");

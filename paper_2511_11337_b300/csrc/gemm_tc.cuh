@@ -123,6 +123,83 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Residual epilogues read the old C row; threads fetch it into registers
+// while the MMAs run (tiles up to 64 columns).
+template <int BN, int EPI>
+struct TcResidPrefetch {
+    static constexpr bool kOn = (EPI == kEpiResid || EPI == kEpiBiasResid) && BN <= 64;
+    static constexpr int kN = kOn ? BN / 4 : 1;
+    float4 v[kN];
+    __device__ __forceinline__ void load(const float* __restrict__ Cm, int row, int n0, int M, int N) {
+        if (!kOn || row >= M) return;
+#pragma unroll
+        for (int i = 0; i < kN; i++)
+            if (n0 + 4 * i < N) v[i] = *reinterpret_cast<const float4*>(Cm + (size_t)row * N + n0 + 4 * i);
+    }
+};
+
+// Epilogue shared by the tensor-core kernels: the warp reading TMEM lanes
+// 32q .. 32q+31 (rows) pulls the tile's columns 64 at a time (four x16 loads,
+// one wait), applies the epilogue and stores.
+template <int BN, int EPI>
+__device__ __forceinline__ void tc_epilogue(uint32_t tmem, int q, int lane, int m0, int n0, int M, int N,
+                                            const float* __restrict__ bias, float* __restrict__ Cm,
+                                            __nv_bfloat16* __restrict__ out_bf16,
+                                            const TcResidPrefetch<BN, EPI>& pre) {
+    constexpr int kChunks = BN / 16;
+    const int row = m0 + q * 32 + lane;
+#pragma unroll
+    for (int g0 = 0; g0 < kChunks; g0 += 4) {
+        uint32_t r[4][16];
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            if (g0 + c < kChunks) tmem_ld16_nowait(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * (g0 + c)), r[c]);
+        tmem_wait_ld();
+        if (row >= M) continue;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            if (g0 + c >= kChunks) break;
+#pragma unroll
+            for (int qq = 0; qq < 16; qq += 4) {
+                const int col = 16 * (g0 + c) + qq;       // column within the tile
+                const int n = n0 + col;
+                if (n >= N) break;                         // N % 4 == 0
+                float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (EPI == kEpiResid || EPI == kEpiBiasResid) {
+                    if constexpr (TcResidPrefetch<BN, EPI>::kOn) old = pre.v[col / 4];
+                    else old = *reinterpret_cast<const float4*>(Cm + (size_t)row * N + n);
+                }
+                const float* ov = reinterpret_cast<const float*>(&old);
+                float o[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    float x = __uint_as_float(r[c][qq + j]);
+                    if (EPI == kEpiBias || EPI == kEpiBiasGelu || EPI == kEpiBiasResid) x = __fadd_rn(x, bias[n + j]);
+                    if (EPI == kEpiBiasGelu) x = gelu_f(x);
+                    if (EPI == kEpiResid || EPI == kEpiBiasResid) x = __fadd_rn(ov[j], x);
+                    o[j] = x;
+                }
+                *reinterpret_cast<float4*>(Cm + (size_t)row * N + n) = make_float4(o[0], o[1], o[2], o[3]);
+                if (out_bf16) {
+                    __nv_bfloat162* bp = reinterpret_cast<__nv_bfloat162*>(out_bf16 + (size_t)row * N + n);
+                    bp[0] = __floats2bfloat162_rn(o[0], o[1]);
+                    bp[1] = __floats2bfloat162_rn(o[2], o[3]);
+                }
+            }
+        }
+    }
+}
+
 template <int BN>
 struct TcSmem {
     static constexpr int kA = kTcBM * kTcBK * 2;     // 16 KB
@@ -210,6 +287,8 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
 
     // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31
+    TcResidPrefetch<BN, EPI> pre;
+    pre.load(Cm, m0 + warp * 32 + lane, n0, M, N);
     const bool finished = mbar_wait(&done[0], 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
@@ -223,37 +302,179 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if (!finished) mbar_wait(&done[0], 0);
         }
     } else {
-        const int row = m0 + warp * 32 + lane;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            const int n = n0 + c0;
-            if (row >= M || n >= N) continue;
-            float* cp = Cm + (size_t)row * N + n;
-#pragma unroll
-            for (int q = 0; q < 16; q += 4) {
-                if (n + q >= N) break;   // N % 4 == 0
-                float o[4];
-                float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (EPI == kEpiResid || EPI == kEpiBiasResid) old = *reinterpret_cast<const float4*>(cp + q);
-                const float* ov = reinterpret_cast<const float*>(&old);
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    float x = v[q + j];
-                    if (EPI == kEpiBias || EPI == kEpiBiasGelu || EPI == kEpiBiasResid) x = __fadd_rn(x, bias[n + q + j]);
-                    if (EPI == kEpiBiasGelu) x = gelu_f(x);
-                    if (EPI == kEpiResid || EPI == kEpiBiasResid) x = __fadd_rn(ov[j], x);
-                    o[j] = x;
-                }
-                *reinterpret_cast<float4*>(cp + q) = make_float4(o[0], o[1], o[2], o[3]);
-                if (out_bf16) {
-                    __nv_bfloat162* bp = reinterpret_cast<__nv_bfloat162*>(out_bf16 + (size_t)row * N + n + q);
-                    bp[0] = __floats2bfloat162_rn(o[0], o[1]);
-                    bp[1] = __floats2bfloat162_rn(o[2], o[3]);
-                }
-            }
+        tc_epilogue<BN, EPI>(tmem, warp, lane, m0, n0, M, N, bias, Cm, out_bf16, pre);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kTmemCols));
+}
+
+// ------------------------------------------------------------ 3xTF32 form
+//
+// FP32-accurate projections on the tensor cores: every operand x is split
+// into x_hi = tf32(x) (round to nearest) and x_lo = x - x_hi, and
+//     A . W^T ~= A_hi W_hi^T + A_hi W_lo^T + A_lo W_hi^T
+// is accumulated in FP32 in TMEM (kind::tf32, K = 8 per instruction), the
+// three products of each K step always in that order.  The weights arrive
+// pre-split; A arrives as FP32 by TMA and four converter warps split each
+// stage in shared memory (in place for hi, a second buffer for lo) before the
+// MMA thread consumes it.  Warps: 0 TMA, 1 MMA, 2-5 converters then epilogue.
+
+constexpr int kT3Threads = 192;
+constexpr int kT3BK = 32;                  // 32 fp32 = 128 bytes = one swizzle atom row
+
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
+    return (1u << 4)                      // D format F32
+         | (2u << 7)                      // A format TF32
+         | (2u << 10)                     // B format TF32
+         | ((uint32_t)(N >> 3) << 17)
+         | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int BN>
+struct T3Smem {
+    static constexpr int kA = kTcBM * kT3BK * 4;     // 16 KB (fp32 -> hi in place)
+    static constexpr int kB = BN * kT3BK * 4;
+    static constexpr int kStage = 2 * kA + 2 * kB;   // A_hi, A_lo, B_hi, B_lo
+    static constexpr int kStages = 2;
+    static constexpr int kTmemCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static constexpr int kBars = 3 * kStages + 1;    // full, converted, empty, done
+    static constexpr size_t kBytes = 1024 + (size_t)kStages * kStage + 8 * kBars + 16;
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kT3Threads)
+k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+                 const __grid_constant__ CUtensorMap tmBlo, const float* __restrict__ bias, float* __restrict__ Cm,
+                 int M, int N, int K, int* __restrict__ err) {
+    using L = T3Smem<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)L::kStages * L::kStage);
+    uint64_t* full = bars;
+    uint64_t* conv = bars + L::kStages;
+    uint64_t* empty = bars + 2 * L::kStages;
+    uint64_t* done = bars + 3 * L::kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::kBars);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
+    const int nk = K / kT3BK;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int i = 0; i < L::kStages; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&conv[i], 128);
+            mbar_init(&empty[i], 1);
         }
+        mbar_init(&done[0], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(L::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    int armed_last = -1;
+    if (threadIdx.x == 0) {
+        for (int kb = 0; kb < nk; kb++) {
+            const int s = kb % L::kStages;
+            if (kb >= L::kStages && !mbar_wait(&empty[s], ((kb / L::kStages) - 1) & 1)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            uint8_t* st = smem + (size_t)s * L::kStage;
+            mbar_expect_tx(&full[s], L::kA + 2 * L::kB);
+            tma_load_2d(&tmA, &full[s], st, kb * kT3BK, m0);
+            tma_load_2d(&tmBhi, &full[s], st + 2 * L::kA, kb * kT3BK, n0);
+            tma_load_2d(&tmBlo, &full[s], st + 2 * L::kA + L::kB, kb * kT3BK, n0);
+            armed_last = kb;
+        }
+    } else if (threadIdx.x == 32) {
+        constexpr uint32_t idesc = umma_idesc_tf32(kTcBM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk && ok; kb++) {
+            const int s = kb % L::kStages;
+            if (!mbar_wait(&conv[s], (kb / L::kStages) & 1)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ahi = smem_u32(smem + (size_t)s * L::kStage);
+            const uint32_t alo = ahi + L::kA;
+            const uint32_t bhi = ahi + 2 * L::kA;
+            const uint32_t blo = bhi + L::kB;
+#pragma unroll
+            for (int k = 0; k < kT3BK / 8; k++) {
+                const uint32_t o = 32 * k;
+                umma_tf32(tmem, umma_desc_sw128(ahi + o), umma_desc_sw128(bhi + o), idesc, (kb | k) != 0 ? 1u : 0u);
+                umma_tf32(tmem, umma_desc_sw128(ahi + o), umma_desc_sw128(blo + o), idesc, 1u);
+                umma_tf32(tmem, umma_desc_sw128(alo + o), umma_desc_sw128(bhi + o), idesc, 1u);
+            }
+            umma_commit(&empty[s]);
+        }
+        if (!ok) atomicExch(&abort_flag, 1);
+        umma_commit(&done[0]);
+    } else if (warp >= 2) {
+        // converters: split each A stage into hi (in place) and lo
+        const int ct = threadIdx.x - 64;
+        for (int kb = 0; kb < nk; kb++) {
+            const int s = kb % L::kStages;
+            if (!mbar_wait(&full[s], (kb / L::kStages) & 1)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            float4* a = reinterpret_cast<float4*>(smem + (size_t)s * L::kStage);
+            float4* lo = reinterpret_cast<float4*>(smem + (size_t)s * L::kStage + L::kA);
+#pragma unroll 4
+            for (int i = ct; i < L::kA / 16; i += 128) {
+                const float4 v = a[i];
+                float4 h, l;
+                h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
+                l.x = __fsub_rn(v.x, h.x); l.y = __fsub_rn(v.y, h.y); l.z = __fsub_rn(v.z, h.z); l.w = __fsub_rn(v.w, h.w);
+                a[i] = h;
+                lo[i] = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
+        }
+    }
+
+    TcResidPrefetch<BN, EPI> pre;
+    if (warp >= 2) pre.load(Cm, m0 + (warp % 4) * 32 + lane, n0, M, N);
+    const bool finished = mbar_wait(&done[0], 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!finished || abort_flag) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            for (int kb = armed_last; kb >= 0 && kb > armed_last - L::kStages; kb--)
+                mbar_wait(&full[kb % L::kStages], (kb / L::kStages) & 1);
+            if (!finished) mbar_wait(&done[0], 0);
+        }
+    } else if (warp >= 2) {
+        tc_epilogue<BN, EPI>(tmem, warp % 4, lane, m0, n0, M, N, bias, Cm, nullptr, pre);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -52,7 +52,7 @@ SHAPES = [(128, 128, 64), (300, 1024, 256), (4096, 48, 512), (1000, 256, 512), (
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_gemm_kernels(api, shape, precision):
     M, N, K = shape
     g = np.random.default_rng(M * 7 + N + K)
@@ -66,11 +66,13 @@ def test_gemm_kernels(api, shape, precision):
         got = api.gemm(A, W, bias, epi, C_in, precision=precision)
         ref = ref_gemm(Ar, Wr, bias, epi, C_in)
         bound = 4 * 2.0 ** -24 * (K + 2) * (mag + np.abs(bias) + np.abs(C_in) + 1e-30) + 1e-6
+        if precision == 2:      # 3xTF32: each product carries ~3 x 2^-21 relative error
+            bound = bound + 8 * 2.0 ** -21 * mag
         err = np.abs(got - ref)
         assert (err <= bound).all(), (epi, float(err.max()), float((err / bound).max()))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_gemm_rows_independent_of_batch(api, precision):
     g = np.random.default_rng(5)
     A = g.normal(0, 1, (1000, 256)).astype(np.float32)
@@ -129,3 +131,50 @@ def test_bf16_paper_scale_batch(api, model_dir):
     mf = api.Model(ffn, precision=api.PREC_BF16)
     comp = mf.compress(streams[:50])
     assert mf.decompress(comp, [len(s) for s in streams[:50]]) == streams[:50]
+
+
+@pytest.fixture(scope="module")
+def tiny_t3(api, tiny_model_path):
+    return api.Model(tiny_model_path, precision=api.PREC_TF32X3)
+
+
+def test_tf32x3_meets_the_fp32_bounds(tiny_t3, tiny_model_path):
+    """The 3xTF32 tensor-core form is held to the FP32 path's bounds."""
+    streams = synth.records_workload()
+    comp = tiny_t3.compress(streams)
+    assert tiny_t3.decompress(comp, [len(s) for s in streams]) == streams
+    om = O.Model(tiny_model_path)
+    ref = om.compress_batch(streams)
+    gap = (sum(map(len, comp)) - sum(map(len, ref))) / sum(map(len, ref))
+    assert abs(gap) <= 0.005, gap
+    worst = 0.0
+    for data in streams:
+        worst = max(worst, float(np.abs(tiny_t3.logprobs(data) - om.logprobs(data)).max()))
+    print(f"TF32x3 max |dlog2p| = {worst:.3e}")
+    assert worst <= 1e-3
+
+
+def test_tf32x3_lockstep_and_batch_invariance(tiny_t3):
+    streams = [synth.records_stream(90 + i, n) for i, n in enumerate([2500, 0, 1, 2, 640, 4097])]
+    n_steps = sum(max(len(s) - 1, 0) for s in streams)
+    tiny_t3.enable_cdf_trace(True)
+    try:
+        comp = tiny_t3.compress(streams)
+        enc = tiny_t3.read_cdf_trace(n_steps)
+        out = tiny_t3.decompress(comp, [len(s) for s in streams])
+        dec = tiny_t3.read_cdf_trace(n_steps)
+    finally:
+        tiny_t3.enable_cdf_trace(False)
+    assert out == streams and np.array_equal(enc, dec)
+    assert tiny_t3.compress([streams[0]] * 33)[20] == comp[0]
+
+
+def test_tf32x3_paper_scale(api, model_dir):
+    path = synth.make_model_file(os.path.join(model_dir, "paper_t3.boaw"), synth.PAPER_SCALE, seed=2)
+    m = api.Model(path, precision=api.PREC_TF32X3)
+    buf = synth.atlas_workload(200, 2048, seed=78)
+    streams = synth.split_equal(buf, 200)
+    comp = m.compress(streams)
+    assert m.decompress(comp, [len(s) for s in streams]) == streams
+    om = O.Model(path)
+    assert np.abs(m.logprobs(streams[3][:400]) - om.logprobs(streams[3][:400])).max() <= 1e-3
