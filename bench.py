@@ -182,7 +182,7 @@ def run_boa(args):
     total = len(buf)
 
     stream = torch.cuda.Stream()
-    prec = {"fp32": api.PREC_FP32, "bf16": api.PREC_BF16, "tf32x3": api.PREC_TF32X3}[args.precision]
+    prec = {"fp32": api.PREC_FP32, "bf16": api.PREC_BF16, "tf32x3": api.PREC_TF32X3, "fp8": api.PREC_FP8}[args.precision]
     model = api.Model(path, device=local, cuda_stream=stream.cuda_stream, max_rows=args.max_rows, precision=prec)
     flat, in_off = api.pack(streams)
     lens = np.diff(in_off)
@@ -275,7 +275,7 @@ def run_boa(args):
     if dom:
         p = est[dom]
         name = f"{dom[1]} ({dom[0]})"
-        if dom[1].startswith("gemm") and args.precision in ("bf16", "tf32x3"):
+        if dom[1].startswith("gemm") and args.precision in ("bf16", "tf32x3", "fp8"):
             achieved = p["flops"] / (p["ms"] / 1e3) / 1e12
             pk = peaks["bf16_tflops_sustained"]
             roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
@@ -344,7 +344,7 @@ def main():
     ap.add_argument("--streams", type=int, default=N_STREAMS)
     ap.add_argument("--stream-len", type=int, default=STREAM_LEN)
     ap.add_argument("--max-rows", type=int, default=0)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32x3"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32x3", "fp8"])
     ap.add_argument("--cpu-prefix", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -50,8 +50,10 @@ typedef enum {
     BOA_PREC_FP32 = 0,              /* all projections in FP32 on the CUDA cores */
     BOA_PREC_BF16 = 1,              /* projections in BF16 on the tensor cores (tcgen05), FP32
                                        accumulation; norms, conv, scan, softmax and CDF stay FP32 */
-    BOA_PREC_TF32X3 = 2             /* FP32-accurate projections on the tensor cores: operands split
+    BOA_PREC_TF32X3 = 2,            /* FP32-accurate projections on the tensor cores: operands split
                                        into TF32 hi + lo parts, three products accumulated in FP32 */
+    BOA_PREC_FP8 = 3                /* projections in FP8 E4M3 on the tensor cores, FP32 accumulation;
+                                       weights scaled per output channel, activations per row */
 } boa_precision;
 
 typedef struct {
@@ -199,10 +201,11 @@ boa_status boa_debug_logprobs(boa_model* model, const uint8_t* stream, size_t le
  * C_out[M][N] = epi(A[M][K] . W[N][K]^T) with the library's FP32 CUDA-core
  * kernel (precision BOA_PREC_FP32), its tcgen05 tensor-core kernel with
  * A and W rounded to BF16 (BOA_PREC_BF16), or its 3xTF32 tensor-core kernel
- * (BOA_PREC_TF32X3).  epilogue: 0 store, 1 + bias[n],
+ * (BOA_PREC_TF32X3), or its E4M3 kernel with W scaled per row of W and
+ * A per row of A (BOA_PREC_FP8).  epilogue: 0 store, 1 + bias[n],
  * 2 C_in + acc, 3 GELU(acc + bias[n]), 4 C_in + (acc + bias[n]).  All pointers
- * host memory; N % 4 == 0; K % 8 == 0 (FP32), K % 64 == 0 (BF16) or
- * K % 32 == 0 (TF32X3).  Device 0. */
+ * host memory; N % 4 == 0; K % 8 == 0 (FP32), K % 64 == 0 (BF16),
+ * K % 32 == 0 (TF32X3) or K % 16 == 0 (FP8).  Device 0. */
 boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K, const float* A, const float* W,
                           const float* bias, int epilogue, const float* C_in, float* C_out);
 

@@ -11,6 +11,7 @@ from ._lib import BoaError, check, load
 PREC_FP32 = 0
 PREC_BF16 = 1
 PREC_TF32X3 = 2
+PREC_FP8 = 3
 
 
 def _p(a: np.ndarray):
@@ -227,4 +228,4 @@ def compressed_slot_offsets(lens) -> np.ndarray:
     return slot_offsets([max_compressed_size(int(n)) for n in lens])
 
 
-__all__ = ["decode_cdfs_static", "pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32", "PREC_BF16", "PREC_TF32X3", "gemm"]
+__all__ = ["decode_cdfs_static", "pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32", "PREC_BF16", "PREC_TF32X3", "PREC_FP8", "gemm"]

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include "boa.h"
 #include "common.cuh"
@@ -136,12 +137,21 @@ struct boa_model {
     struct TLayer { float *in_hi, *in_lo, *x_hi, *x_lo, *out_hi, *out_lo, *w1_hi, *w1_lo, *w2_hi, *w2_lo; };
     std::vector<TLayer> tlayers;
     float *head_hi = nullptr, *head_lo = nullptr;
-    struct MapEnt { const void* p; uint64_t rows, cols; uint32_t box; int f32; CUtensorMap map; };
+    // FP8 path: E4M3 weights [out][in] and per-output-channel scales
+    uint8_t* w8 = nullptr;
+    float* w8s = nullptr;
+    struct QLayer { const __nv_fp8_e4m3 *in_w, *x_w, *out_w, *w1, *w2; const float *in_s, *x_s, *out_s, *w1_s, *w2_s; };
+    std::vector<QLayer> qlayers;
+    const __nv_fp8_e4m3* head_w8 = nullptr;
+    const float* head_s = nullptr;
+    struct MapEnt { const void* p; uint64_t rows, cols; uint32_t box; int esz; CUtensorMap map; };
     std::vector<MapEnt> maps;
 
     // workspace
     DevBuf<float> x, xn, xz, u, dbc, yg, logits, hid, h, conv;
     DevBuf<__nv_bfloat16> xn_b, u_b, yg_b, x_b, hid_b;
+    DevBuf<uint8_t> a8;          // FP8 activations of the current GEMM
+    DevBuf<float> a8s;           // their per-row scales
     DevBuf<int> err;
     DevBuf<CoderState> st;
     DevBuf<uint8_t> tokens, d_in, d_out, d_pack;
@@ -249,6 +259,7 @@ static void free_workspace(boa_model* m) {
     m->in_off.release(); m->out_off.release(); m->lens.release(); m->sizes.release();
     m->trace_off.release(); m->trace.release(); m->d_pack.release(); m->pack_off.release();
     m->xn_b.release(); m->u_b.release(); m->yg_b.release(); m->x_b.release(); m->hid_b.release(); m->err.release();
+    m->a8.release(); m->a8s.release();
     m->h_in.release(); m->h_out.release(); m->h_u64.release(); m->h_pack.release(); m->h_u32.release();
 }
 
@@ -261,6 +272,8 @@ extern "C" void boa_free_model(boa_model* m) {
     if (m->weights) cudaFree(m->weights);
     if (m->wb) cudaFree(m->wb);
     if (m->w3) cudaFree(m->w3);
+    if (m->w8) cudaFree(m->w8);
+    if (m->w8s) cudaFree(m->w8s);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -306,7 +319,7 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
 
     boa_opts o = {0, BOA_PREC_FP32, nullptr, 0};
     if (opts) o = *opts;
-    if (o.precision != BOA_PREC_FP32 && o.precision != BOA_PREC_BF16 && o.precision != BOA_PREC_TF32X3)
+    if (o.precision < BOA_PREC_FP32 || o.precision > BOA_PREC_FP8)
         return fail(BOA_ERR_ARG, "precision %d not supported", o.precision);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(BOA_ERR_CUDA, "no CUDA device available");
@@ -358,6 +371,8 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
     size_t head_o = copy_t(256, d);
     size_t head_b_o = copy(256);
 
+    if (o.precision == BOA_PREC_FP8 && d < 128)
+        return fail(BOA_ERR_FORMAT, "FP8 projections need d_model >= 128 (K-blocks of 128 E4M3 values)");
     boa_model* m = new boa_model();
     m->device = o.device;
     m->precision = o.precision;
@@ -478,6 +493,62 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
         }
         pair(m->head_hi, m->head_lo);
     }
+    if (m->precision == BOA_PREC_FP8) {
+        // w8[n][k] = e4m3(W[n][k] * 448 / max_k |W[n][k]|), scale[n] = max / 448
+        struct Mat { size_t src, rows, cols; };
+        std::vector<Mat> mats;
+        for (int l = 0; l < nl; l++) {
+            mats.push_back({sro[l].in_w, (size_t)2 * E, (size_t)d});
+            mats.push_back({sro[l].x_w, (size_t)R2, (size_t)E});
+            mats.push_back({sro[l].out_w, (size_t)d, (size_t)E});
+            if (F) { mats.push_back({sro[l].w1, (size_t)F, (size_t)d}); mats.push_back({sro[l].w2, (size_t)d, (size_t)F}); }
+        }
+        mats.push_back({head_src, (size_t)256, (size_t)d});
+        size_t tb = 0, ts = 0;
+        std::vector<size_t> atb, ats;
+        for (auto& mt : mats) {
+            atb.push_back(tb); ats.push_back(ts);
+            tb += (mt.rows * mt.cols + 255) / 256 * 256;
+            ts += (mt.rows + 63) / 64 * 64;
+        }
+        std::vector<uint8_t> hq(tb, 0);
+        std::vector<float> hs(ts, 1.f);
+        for (size_t i = 0; i < mats.size(); i++) {
+            const size_t R = mats[i].rows, Cc = mats[i].cols;
+            for (size_t rr = 0; rr < R; rr++) {
+                const float* w = src + mats[i].src + rr * Cc;
+                float amax = 0.f;
+                for (size_t k = 0; k < Cc; k++) amax = std::max(amax, std::fabs(w[k]));
+                const float inv = amax > 0.f ? 448.0f / amax : 1.0f;
+                hs[ats[i] + rr] = amax > 0.f ? amax / 448.0f : 1.0f;
+                for (size_t k = 0; k < Cc; k++)
+                    hq[atb[i] + rr * Cc + k] = (uint8_t)__nv_cvt_float_to_fp8(w[k] * inv, __NV_SATFINITE, __NV_E4M3);
+            }
+        }
+        if (cudaMalloc(&m->w8, tb) != cudaSuccess || cudaMalloc(&m->w8s, ts * 4) != cudaSuccess ||
+            cudaMemcpy(m->w8, hq.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(m->w8s, hs.data(), ts * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            boa_free_model(m);
+            return fail(BOA_ERR_OOM, "fp8 weight upload failed");
+        }
+        size_t k = 0;
+        auto q = [&](const __nv_fp8_e4m3*& w, const float*& sc) {
+            w = reinterpret_cast<const __nv_fp8_e4m3*>(m->w8 + atb[k]);
+            sc = m->w8s + ats[k];
+            k++;
+        };
+        m->qlayers.resize(nl);
+        for (int l = 0; l < nl; l++) {
+            auto& Q = m->qlayers[l];
+            q(Q.in_w, Q.in_s);
+            q(Q.x_w, Q.x_s);
+            q(Q.out_w, Q.out_s);
+            Q.w1 = Q.w2 = nullptr;
+            Q.w1_s = Q.w2_s = nullptr;
+            if (F) { q(Q.w1, Q.w1_s); q(Q.w2, Q.w2_s); }
+        }
+        q(m->head_w8, m->head_s);
+    }
     *out = m;
     return BOA_OK;
 }
@@ -521,10 +592,11 @@ static std::mutex g_encode_mu;
 
 // 2-D BF16 tensor map over a row-major [rows][cols] matrix, boxes of
 // 64 columns (128 bytes, 128-byte swizzle) by box_rows rows.
-static boa_status tmap_2d(boa_model* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows, bool f32,
+// esz: element size in bytes (1 E4M3, 2 BF16, 4 FP32).
+static boa_status tmap_2d(boa_model* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows, int esz,
                           CUtensorMap* out) {
     for (auto& e : m->maps)
-        if (e.p == ptr && e.rows == rows && e.cols == cols && e.box == box_rows && e.f32 == (int)f32) {
+        if (e.p == ptr && e.rows == rows && e.cols == cols && e.box == box_rows && e.esz == esz) {
             *out = e.map;
             return BOA_OK;
         }
@@ -539,15 +611,16 @@ static boa_status tmap_2d(boa_model* m, const void* ptr, uint64_t rows, uint64_t
             g_encode_tiled = (PFN_cuTensorMapEncodeTiled_v12000)fn;
         }
     }
-    const uint64_t esz = f32 ? 4 : 2;
     if (((uintptr_t)ptr & 15) || (cols * esz) % 16) return fail(BOA_ERR_ARG, "tensor map needs 16-byte aligned rows");
     boa_model::MapEnt e;
-    e.p = ptr; e.rows = rows; e.cols = cols; e.box = box_rows; e.f32 = (int)f32;
+    e.p = ptr; e.rows = rows; e.cols = cols; e.box = box_rows; e.esz = esz;
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {cols * esz};
     cuuint32_t box[2] = {(cuuint32_t)(128 / esz), box_rows};   // 128-byte rows: one swizzle atom
     cuuint32_t es[2] = {1, 1};
-    CUresult r = g_encode_tiled(&e.map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    const CUtensorMapDataType dt = esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    CUresult r = g_encode_tiled(&e.map, dt, 2,
                                 const_cast<void*>(ptr), dims, strides, box, es,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -562,16 +635,17 @@ static boa_status tmap_2d(boa_model* m, const void* ptr, uint64_t rows, uint64_t
 // same MMA shape in compression and decompression.
 static int tc_bn(int N) { return N >= 512 ? 128 : N > 48 ? 64 : 48; }
 
-template <int BN, int EPI>
+template <int BN, int EPI, int KIND>
 static void launch_tc(boa_model* m, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, float* C,
-                      __nv_bfloat16* outb, long long M, int N, int K) {
+                      __nv_bfloat16* outb, long long M, int N, int K, const float* rs, const float* cs) {
     using L = TcSmem<BN>;
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_gemm_tc_bf16<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
+        cudaFuncSetAttribute(k_gemm_tc_bf16<BN, EPI, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
     });
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
-    k_gemm_tc_bf16<BN, EPI><<<grid, kTcThreads, L::kBytes, m->stream>>>(ta, tb, bias, C, outb, (int)M, N, K, m->err.p);
+    k_gemm_tc_bf16<BN, EPI, KIND><<<grid, kTcThreads, L::kBytes, m->stream>>>(ta, tb, bias, C, outb, (int)M, N, K,
+                                                                              m->err.p, rs, cs);
 }
 
 template <int EPI>
@@ -584,14 +658,43 @@ static boa_status gemm_tc(boa_model* m, int cls, const __nv_bfloat16* A, const _
                  2.0 * ((double)M * K + (double)K * N) + 4.0 * (double)M * N * (resid ? 2 : 1) + (outb ? 2.0 * M * N : 0));
     const int BN = tc_bn(N);
     CUtensorMap ta, tb;
-    TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, false, &ta));
-    TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)K, (uint32_t)BN, false, &tb));
+    TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, 2, &ta));
+    TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 2, &tb));
     switch (BN) {
-        case 48: launch_tc<48, EPI>(m, ta, tb, bias, C, outb, M, N, K); break;
-        case 64: launch_tc<64, EPI>(m, ta, tb, bias, C, outb, M, N, K); break;
-        default: launch_tc<128, EPI>(m, ta, tb, bias, C, outb, M, N, K); break;
+        case 48: launch_tc<48, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
+        case 64: launch_tc<64, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
+        default: launch_tc<128, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
     }
     return check_launch(m, "gemm_tc");
+}
+
+// FP8 projection: quantise the FP32 activation rows (one warp per row), then
+// the E4M3 tensor-core kernel with the row and weight scales in its epilogue.
+template <int EPI>
+static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_e4m3* W, const float* wscale,
+                          const float* bias, float* C, long long M, int N, int K) {
+    if (M <= 0) return BOA_OK;
+    if (N % 4 != 0 || K % 128 != 0 || K > 1024) return fail(BOA_ERR_FORMAT, "fp8 gemm shape N=%d K=%d unsupported", N, K);
+    TRY(m->a8.ensure((size_t)M * K));
+    TRY(m->a8s.ensure((size_t)M));
+    {
+        ProfScope pq(m, BOA_KC_OTHER, 3.0 * M * K, 5.0 * M * K + 4.0 * M);
+        k_quant_rows_e4m3<<<(unsigned)((M + 7) / 8), 256, 0, m->stream>>>(
+            A, reinterpret_cast<__nv_fp8_e4m3*>(m->a8.p), m->a8s.p, M, K);
+    }
+    TRY(check_launch(m, "quant_rows"));
+    const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
+    ProfScope ps(m, cls, 2.0 * M * N * K, ((double)M * K + (double)K * N) + 4.0 * (double)M * N * (resid ? 2 : 1));
+    const int BN = tc_bn(N);
+    CUtensorMap ta, tb;
+    TRY(tmap_2d(m, m->a8.p, (uint64_t)M, (uint64_t)K, kTcBM, 1, &ta));
+    TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 1, &tb));
+    switch (BN) {
+        case 48: launch_tc<48, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, K, m->a8s.p, wscale); break;
+        case 64: launch_tc<64, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, K, m->a8s.p, wscale); break;
+        default: launch_tc<128, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, K, m->a8s.p, wscale); break;
+    }
+    return check_launch(m, "gemm_f8");
 }
 
 template <int BN, int EPI>
@@ -617,9 +720,9 @@ static boa_status gemm_t3(boa_model* m, int cls, const float* A, const float* Wh
                  4.0 * ((double)M * K + 2.0 * K * N) + 4.0 * (double)M * N * (resid ? 2 : 1));
     const int BN = N > 48 ? 64 : 48;
     CUtensorMap ta, th, tl;
-    TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, true, &ta));
-    TRY(tmap_2d(m, Whi, (uint64_t)N, (uint64_t)K, (uint32_t)BN, true, &th));
-    TRY(tmap_2d(m, Wlo, (uint64_t)N, (uint64_t)K, (uint32_t)BN, true, &tl));
+    TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, 4, &ta));
+    TRY(tmap_2d(m, Whi, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 4, &th));
+    TRY(tmap_2d(m, Wlo, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 4, &tl));
     if (BN == 48) launch_t3<48, EPI>(m, ta, th, tl, bias, C, M, N, K);
     else launch_t3<64, EPI>(m, ta, th, tl, bias, C, M, N, K);
     return check_launch(m, "gemm_t3");
@@ -672,8 +775,8 @@ static int stream_group(int S, int Tc) { return (Tc == 1 && S >= 1024) ? 8 : 1; 
 
 static boa_status conv(boa_model* m, int l, int S, int Tc) {
     const DevLayer& L = m->layers[l];
-    const int G = stream_group(S, Tc);
-    dim3 grid((m->E + 127) / 128, (S + G - 1) / G);
+    const int G = 1;                                  // one stream per thread: more loads in flight
+    dim3 grid((m->E + 511) / 512, (S + G - 1) / G);   // 4 channels per thread
     float* win = m->conv.p + (size_t)l * S * (m->K - 1) * m->E;
     const double rows = (double)S * Tc;
     ProfScope ps(m, BOA_KC_CONV, rows * m->E * (2.0 * m->K + 4), 4.0 * (2 * rows * m->E + 2.0 * S * (m->K - 1) * m->E));
@@ -711,11 +814,13 @@ static boa_status scan(boa_model* m, int l, int S, int Tc) {
 }
 
 // The predictor over S x Tc rows: embedding, n_l blocks, head (Alg. 1).
-static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc) {
+// embedded: the input rows x / xn were already written (decode steps after
+// the first, by the previous step's decode kernel).
+static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc, bool embedded = false) {
     const long long rows = (long long)S * Tc;
     const int d = m->d, E = m->E;
     const bool tc = m->precision == BOA_PREC_BF16;
-    TRY(embed_ln(m, ts, S, Tc));
+    if (!embedded) TRY(embed_ln(m, ts, S, Tc));
     for (int l = 0; l < m->nl; l++) {
         const DevLayer& L = m->layers[l];
         if (tc) {
@@ -729,6 +834,17 @@ static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc) {
             if (m->F) {
                 TRY(gemm_tc<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x_b.p, B.w1, L.b1, m->hid.p, m->hid_b.p, rows, m->F, d));
                 TRY(gemm_tc<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid_b.p, B.w2, L.b2, m->x.p, nullptr, rows, d, m->F));
+            }
+        } else if (m->precision == BOA_PREC_FP8) {
+            const auto& Q = m->qlayers[l];
+            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn.p, Q.in_w, Q.in_s, nullptr, m->xz.p, rows, 2 * E, d));
+            TRY(conv(m, l, S, Tc));
+            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_X, m->u.p, Q.x_w, Q.x_s, nullptr, m->dbc.p, rows, m->R2, E));
+            TRY(scan(m, l, S, Tc));
+            TRY(gemm_f8<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg.p, Q.out_w, Q.out_s, nullptr, m->x.p, rows, d, E));
+            if (m->F) {
+                TRY(gemm_f8<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x.p, Q.w1, Q.w1_s, L.b1, m->hid.p, rows, m->F, d));
+                TRY(gemm_f8<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid.p, Q.w2, Q.w2_s, L.b2, m->x.p, rows, d, m->F));
             }
         } else if (m->precision == BOA_PREC_TF32X3) {
             const auto& T = m->tlayers[l];
@@ -757,6 +873,8 @@ static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc) {
     if (tc) return gemm_tc<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x_b.p, m->head_wb, m->head_b, m->logits.p, nullptr, rows, 256, d);
     if (m->precision == BOA_PREC_TF32X3)
         return gemm_t3<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_hi, m->head_lo, m->head_b, m->logits.p, rows, 256, d);
+    if (m->precision == BOA_PREC_FP8)
+        return gemm_f8<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_w8, m->head_s, m->head_b, m->logits.p, rows, 256, d);
     return gemm<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_wt, m->head_b, m->logits.p, rows, 256, d);
 }
 
@@ -920,15 +1038,25 @@ static boa_status decompress_impl(boa_model* m, size_t S, const uint8_t* d_in, c
     k_dec_init<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(d_in, m->in_off.p, m->sizes.p, m->lens.p, d_out,
                                                                    m->out_off.p, m->tokens.p, m->st.p, (int)S);
     TRY(check_launch(m, "dec_init"));
+    const DevLayer& L0 = m->layers[0];
+    NextEmbed ne{m->embed, L0.ln_a_w, L0.ln_a_b, m->x.p, m->xn.p,
+                 m->precision == BOA_PREC_BF16 ? m->xn_b.p : nullptr};
     for (uint64_t t = 0; t + 1 < maxlen; t++) {
         m->prof_step = (t % (uint64_t)m->prof_stride) == 0;
+        // step 0 embeds the raw first bytes; later steps were embedded by the
+        // previous step's decode kernel
         TokenSrc ts{nullptr, m->in_off.p, m->lens.p, m->tokens.p, (long long)t};
-        TRY(forward(m, ts, (int)S, 1));
+        TRY(forward(m, ts, (int)S, 1, /*embedded=*/t > 0));
         DecArgs a{m->logits.p, d_in, m->in_off.p, m->sizes.p, m->lens.p, d_out, m->out_off.p, m->tokens.p, m->st.p,
                   m->trace_on ? m->trace.p : nullptr, m->trace_off.p, (long long)t, (int)S};
         {
-            ProfScope ps(m, BOA_KC_DECODE, (double)S * 256 * 8, (double)S * (256 * 4 + 2));
-            k_decode<<<(unsigned)((S + 3) / 4), 128, 0, m->stream>>>(a);
+            ProfScope ps(m, BOA_KC_DECODE, (double)S * 256 * 8, (double)S * (256 * 4 + 2 + 8.0 * m->d));
+            const unsigned grid = (unsigned)((S + 3) / 4);
+            switch (m->d) {
+                case 64: k_decode<2><<<grid, 128, 0, m->stream>>>(a, ne); break;
+                case 128: k_decode<4><<<grid, 128, 0, m->stream>>>(a, ne); break;
+                default: k_decode<8><<<grid, 128, 0, m->stream>>>(a, ne); break;
+            }
         }
         TRY(check_launch(m, "decode"));
     }
@@ -1212,8 +1340,7 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
     if ((epilogue == kEpiBias || epilogue == kEpiBiasGelu || epilogue == kEpiBiasResid) && !bias)
         return fail(BOA_ERR_ARG, "epilogue needs a bias");
     if ((epilogue == kEpiResid || epilogue == kEpiBiasResid) && !C_in) return fail(BOA_ERR_ARG, "epilogue needs C_in");
-    if (precision != BOA_PREC_FP32 && precision != BOA_PREC_BF16 && precision != BOA_PREC_TF32X3)
-        return fail(BOA_ERR_ARG, "bad precision");
+    if (precision < BOA_PREC_FP32 || precision > BOA_PREC_FP8) return fail(BOA_ERR_ARG, "bad precision");
     boa_model t;
     t.precision = precision;
     cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, 0);
@@ -1241,6 +1368,40 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
                 case kEpiBiasGelu: TRY(gemm_tc<kEpiBiasGelu>(&t, BOA_KC_OTHER, bA.p, bW.p, dB.p, dC.p, nullptr, M, N, K)); break;
                 default: TRY(gemm_tc<kEpiBiasResid>(&t, BOA_KC_OTHER, bA.p, bW.p, dB.p, dC.p, nullptr, M, N, K)); break;
             }
+        } else if (precision == BOA_PREC_FP8) {
+            TRY(t.err.ensure(1));
+            CU(cudaMemset(t.err.p, 0, 4));
+            std::vector<uint8_t> q(N * K);
+            std::vector<float> sc(N);
+            for (size_t n = 0; n < N; n++) {
+                float amax = 0.f;
+                for (size_t k = 0; k < K; k++) amax = std::max(amax, std::fabs(W[n * K + k]));
+                const float inv = amax > 0.f ? 448.0f / amax : 1.0f;
+                sc[n] = amax > 0.f ? amax / 448.0f : 1.0f;
+                for (size_t k = 0; k < K; k++)
+                    q[n * K + k] = (uint8_t)__nv_cvt_float_to_fp8(W[n * K + k] * inv, __NV_SATFINITE, __NV_E4M3);
+            }
+            DevBuf<uint8_t> dq;
+            DevBuf<float> ds;
+            TRY(dq.ensure(N * K));
+            TRY(ds.ensure(N));
+            CU(cudaMemcpy(dq.p, q.data(), N * K, cudaMemcpyHostToDevice));
+            CU(cudaMemcpy(ds.p, sc.data(), N * 4, cudaMemcpyHostToDevice));
+            const __nv_fp8_e4m3* w8 = reinterpret_cast<const __nv_fp8_e4m3*>(dq.p);
+            boa_status r = BOA_OK;
+            switch (epilogue) {
+                case kEpiStore: r = gemm_f8<kEpiStore>(&t, BOA_KC_OTHER, dA.p, w8, ds.p, dB.p, dC.p, M, N, K); break;
+                case kEpiBias: r = gemm_f8<kEpiBias>(&t, BOA_KC_OTHER, dA.p, w8, ds.p, dB.p, dC.p, M, N, K); break;
+                case kEpiResid: r = gemm_f8<kEpiResid>(&t, BOA_KC_OTHER, dA.p, w8, ds.p, dB.p, dC.p, M, N, K); break;
+                case kEpiBiasGelu: r = gemm_f8<kEpiBiasGelu>(&t, BOA_KC_OTHER, dA.p, w8, ds.p, dB.p, dC.p, M, N, K); break;
+                default: r = gemm_f8<kEpiBiasResid>(&t, BOA_KC_OTHER, dA.p, w8, ds.p, dB.p, dC.p, M, N, K); break;
+            }
+            cudaDeviceSynchronize();
+            dq.release();
+            ds.release();
+            t.a8.release();
+            t.a8s.release();
+            TRY(r);
         } else if (precision == BOA_PREC_TF32X3) {
             TRY(t.err.ensure(1));
             CU(cudaMemset(t.err.p, 0, 4));

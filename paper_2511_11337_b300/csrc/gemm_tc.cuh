@@ -97,6 +97,27 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);    // M / 16
 }
 
+// Instruction descriptor, kind::f8f6f4: E4M3 x E4M3 -> FP32, both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_e4m3(int M, int N) {
+    return (1u << 4)                      // D format F32
+         | (0u << 7)                      // A format E4M3
+         | (0u << 10)                     // B format E4M3
+         | ((uint32_t)(N >> 3) << 17)
+         | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// Operand kinds of the 128-byte-per-row tensor-core kernel.
+enum TcKind : int { kKindBF16 = 0, kKindE4M3 = 1 };
+
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
     asm volatile(
@@ -133,31 +154,27 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Residual epilogues read the old C row; threads fetch it into registers
-// while the MMAs run (tiles up to 64 columns).
-template <int BN, int EPI>
-struct TcResidPrefetch {
-    static constexpr bool kOn = (EPI == kEpiResid || EPI == kEpiBiasResid) && BN <= 64;
-    static constexpr int kN = kOn ? BN / 4 : 1;
-    float4 v[kN];
-    __device__ __forceinline__ void load(const float* __restrict__ Cm, int row, int n0, int M, int N) {
-        if (!kOn || row >= M) return;
-#pragma unroll
-        for (int i = 0; i < kN; i++)
-            if (n0 + 4 * i < N) v[i] = *reinterpret_cast<const float4*>(Cm + (size_t)row * N + n0 + 4 * i);
-    }
-};
-
-// Epilogue shared by the tensor-core kernels: the warp reading TMEM lanes
-// 32q .. 32q+31 (rows) pulls the tile's columns 64 at a time (four x16 loads,
-// one wait), applies the epilogue and stores.
+// Epilogue shared by the tensor-core kernels.  Warp q owns accumulator rows
+// (TMEM lanes) 32q .. 32q+31.  Phase 1: it copies them, 16 columns per
+// tcgen05.ld, into its own slice of the (now idle) pipeline shared memory,
+// 16-byte chunks XOR-swizzled by row so the writes are conflict-free.
+// Phase 2: it walks its rows, each lane taking one 16-byte chunk, so every
+// global store of the warp covers whole contiguous row segments; the
+// epilogue arithmetic (scales, bias, GELU, residual) happens here.
+// row_scale / col_scale (FP8 operands): acc * row_scale[m] * col_scale[n].
 template <int BN, int EPI>
 __device__ __forceinline__ void tc_epilogue(uint32_t tmem, int q, int lane, int m0, int n0, int M, int N,
                                             const float* __restrict__ bias, float* __restrict__ Cm,
-                                            __nv_bfloat16* __restrict__ out_bf16,
-                                            const TcResidPrefetch<BN, EPI>& pre) {
+                                            __nv_bfloat16* __restrict__ out_bf16, float* stage,
+                                            const float* __restrict__ row_scale = nullptr,
+                                            const float* __restrict__ col_scale = nullptr) {
     constexpr int kChunks = BN / 16;
-    const int row = m0 + q * 32 + lane;
+    constexpr int kSlots = BN / 4;                       // float4 per row
+    constexpr int kMask = kSlots >= 16 ? 7 : 3;          // swizzle stays inside the row
+    constexpr int kRowsPerIter = 32 / kSlots;            // rows one warp store covers
+    constexpr int kIters = 32 / kRowsPerIter;
+    float4* st = reinterpret_cast<float4*>(stage) + (size_t)q * 32 * kSlots;
+    // phase 1: TMEM -> registers -> shared (row = lane)
 #pragma unroll
     for (int g0 = 0; g0 < kChunks; g0 += 4) {
         uint32_t r[4][16];
@@ -165,36 +182,70 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, int q, int lane, int 
         for (int c = 0; c < 4; c++)
             if (g0 + c < kChunks) tmem_ld16_nowait(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * (g0 + c)), r[c]);
         tmem_wait_ld();
-        if (row >= M) continue;
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             if (g0 + c >= kChunks) break;
 #pragma unroll
-            for (int qq = 0; qq < 16; qq += 4) {
-                const int col = 16 * (g0 + c) + qq;       // column within the tile
-                const int n = n0 + col;
-                if (n >= N) break;                         // N % 4 == 0
-                float4 old = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (EPI == kEpiResid || EPI == kEpiBiasResid) {
-                    if constexpr (TcResidPrefetch<BN, EPI>::kOn) old = pre.v[col / 4];
-                    else old = *reinterpret_cast<const float4*>(Cm + (size_t)row * N + n);
-                }
-                const float* ov = reinterpret_cast<const float*>(&old);
-                float o[4];
+            for (int j = 0; j < 4; j++) {
+                const int f = (g0 + c) * 4 + j;
+                st[lane * kSlots + (f ^ (lane & kMask))] =
+                    make_float4(__uint_as_float(r[c][4 * j]), __uint_as_float(r[c][4 * j + 1]),
+                                __uint_as_float(r[c][4 * j + 2]), __uint_as_float(r[c][4 * j + 3]));
+            }
+        }
+    }
+    __syncwarp();
+    // phase 2: shared -> global, whole row segments per warp store
+    const int f = lane % kSlots;
+    const bool active = lane < kRowsPerIter * kSlots;
+    const int n = n0 + 4 * f;
+    const bool col_ok = active && n < N;                 // N % 4 == 0
+    float4 bv = make_float4(0.f, 0.f, 0.f, 0.f), cs = make_float4(1.f, 1.f, 1.f, 1.f);
+    if (col_ok && (EPI == kEpiBias || EPI == kEpiBiasGelu || EPI == kEpiBiasResid))
+        bv = *reinterpret_cast<const float4*>(bias + n);
+    if (col_ok && col_scale) cs = *reinterpret_cast<const float4*>(col_scale + n);
+    constexpr bool kResid = EPI == kEpiResid || EPI == kEpiBiasResid;
+    constexpr int kBatch = 8;
+#pragma unroll 1
+    for (int it0 = 0; it0 < kIters; it0 += kBatch) {
+        float4 old[kBatch];
+        float rsv[kBatch];
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    float x = __uint_as_float(r[c][qq + j]);
-                    if (EPI == kEpiBias || EPI == kEpiBiasGelu || EPI == kEpiBiasResid) x = __fadd_rn(x, bias[n + j]);
-                    if (EPI == kEpiBiasGelu) x = gelu_f(x);
-                    if (EPI == kEpiResid || EPI == kEpiBiasResid) x = __fadd_rn(ov[j], x);
-                    o[j] = x;
-                }
-                *reinterpret_cast<float4*>(Cm + (size_t)row * N + n) = make_float4(o[0], o[1], o[2], o[3]);
-                if (out_bf16) {
-                    __nv_bfloat162* bp = reinterpret_cast<__nv_bfloat162*>(out_bf16 + (size_t)row * N + n);
-                    bp[0] = __floats2bfloat162_rn(o[0], o[1]);
-                    bp[1] = __floats2bfloat162_rn(o[2], o[3]);
-                }
+        for (int u = 0; u < kBatch; u++) {
+            const int rl = (it0 + u) * kRowsPerIter + lane / kSlots;
+            const int row = m0 + q * 32 + rl;
+            old[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            rsv[u] = 1.f;
+            if (it0 + u < kIters && col_ok && row < M) {
+                if (kResid) old[u] = *reinterpret_cast<const float4*>(Cm + (size_t)row * N + n);
+                if (row_scale) rsv[u] = row_scale[row];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; u++) {
+            if (it0 + u >= kIters) break;
+            const int rl = (it0 + u) * kRowsPerIter + lane / kSlots;
+            const int row = m0 + q * 32 + rl;
+            if (!col_ok || row >= M) continue;
+            const float4 a = st[rl * kSlots + (f ^ (rl & kMask))];
+            float o[4] = {a.x, a.y, a.z, a.w};
+            const float* bp = reinterpret_cast<const float*>(&bv);
+            const float* cp = reinterpret_cast<const float*>(&cs);
+            const float* op = reinterpret_cast<const float*>(&old[u]);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float x = o[j];
+                if (row_scale) x = __fmul_rn(__fmul_rn(x, rsv[u]), cp[j]);
+                if (EPI == kEpiBias || EPI == kEpiBiasGelu || EPI == kEpiBiasResid) x = __fadd_rn(x, bp[j]);
+                if (EPI == kEpiBiasGelu) x = gelu_f(x);
+                if (kResid) x = __fadd_rn(op[j], x);
+                o[j] = x;
+            }
+            *reinterpret_cast<float4*>(Cm + (size_t)row * N + n) = make_float4(o[0], o[1], o[2], o[3]);
+            if (out_bf16) {
+                __nv_bfloat162* bo = reinterpret_cast<__nv_bfloat162*>(out_bf16 + (size_t)row * N + n);
+                bo[0] = __floats2bfloat162_rn(o[0], o[1]);
+                bo[1] = __floats2bfloat162_rn(o[2], o[3]);
             }
         }
     }
@@ -216,11 +267,16 @@ struct TcSmem {
 };
 
 // out_bf16 (optional): a BF16 copy of the stored result (feeds the next GEMM).
-template <int BN, int EPI>
+// KIND selects BF16 operands (K = 64 per stage, kind::f16) or E4M3 operands
+// (K = 128 per stage, kind::f8f6f4, with row / column scales in the
+// epilogue); either way a stage row is 128 bytes.
+template <int BN, int EPI, int KIND>
 __global__ void __launch_bounds__(kTcThreads)
 k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const float* __restrict__ bias, float* __restrict__ Cm, __nv_bfloat16* __restrict__ out_bf16,
-               int M, int N, int K, int* __restrict__ err) {
+               int M, int N, int K, int* __restrict__ err, const float* __restrict__ row_scale,
+               const float* __restrict__ col_scale) {
+    constexpr int kElemK = KIND == kKindE4M3 ? 128 : kTcBK;    // elements per 128-byte stage row
     using L = TcSmem<BN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -233,7 +289,7 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
-    const int nk = K / kTcBK;
+    const int nk = K / kElemK;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -262,13 +318,13 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
             uint8_t* sa = smem + (size_t)s * L::kStage;
             mbar_expect_tx(&full[s], L::kStage);
-            tma_load_2d(&tmA, &full[s], sa, kb * kTcBK, m0);
-            tma_load_2d(&tmB, &full[s], sa + L::kA, kb * kTcBK, n0);
+            tma_load_2d(&tmA, &full[s], sa, kb * kElemK, m0);
+            tma_load_2d(&tmB, &full[s], sa + L::kA, kb * kElemK, n0);
             armed_last = kb;
         }
     } else if (threadIdx.x == 32) {
         // MMA issuer
-        constexpr uint32_t idesc = umma_idesc_bf16(kTcBM, BN);
+        constexpr uint32_t idesc = KIND == kKindE4M3 ? umma_idesc_e4m3(kTcBM, BN) : umma_idesc_bf16(kTcBM, BN);
         bool ok = true;
         for (int kb = 0; kb < nk && ok; kb++) {
             const int s = kb % L::kStages;
@@ -277,9 +333,14 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const uint32_t sa = smem_u32(smem + (size_t)s * L::kStage);
             const uint32_t sb = sa + L::kA;
 #pragma unroll
-            for (int k = 0; k < kTcBK / 16; k++)
-                umma_bf16(tmem, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
-                          (kb | k) != 0 ? 1u : 0u);
+            for (int k = 0; k < 4; k++) {   // 32 bytes of K per instruction: 16 BF16 or 32 E4M3
+                if (KIND == kKindE4M3)
+                    umma_e4m3(tmem, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
+                              (kb | k) != 0 ? 1u : 0u);
+                else
+                    umma_bf16(tmem, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
+                              (kb | k) != 0 ? 1u : 0u);
+            }
             umma_commit(&empty[s]);
         }
         if (!ok) atomicExch(&abort_flag, 1);
@@ -287,8 +348,6 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
 
     // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31
-    TcResidPrefetch<BN, EPI> pre;
-    pre.load(Cm, m0 + warp * 32 + lane, n0, M, N);
     const bool finished = mbar_wait(&done[0], 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
@@ -302,7 +361,8 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if (!finished) mbar_wait(&done[0], 0);
         }
     } else {
-        tc_epilogue<BN, EPI>(tmem, warp, lane, m0, n0, M, N, bias, Cm, out_bf16, pre);
+        tc_epilogue<BN, EPI>(tmem, warp, lane, m0, n0, M, N, bias, Cm, out_bf16, reinterpret_cast<float*>(smem),
+                             row_scale, col_scale);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -461,8 +521,6 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         }
     }
 
-    TcResidPrefetch<BN, EPI> pre;
-    if (warp >= 2) pre.load(Cm, m0 + (warp % 4) * 32 + lane, n0, M, N);
     const bool finished = mbar_wait(&done[0], 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
@@ -474,7 +532,7 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             if (!finished) mbar_wait(&done[0], 0);
         }
     } else if (warp >= 2) {
-        tc_epilogue<BN, EPI>(tmem, warp % 4, lane, m0, n0, M, N, bias, Cm, nullptr, pre);
+        tc_epilogue<BN, EPI>(tmem, warp % 4, lane, m0, n0, M, N, bias, Cm, nullptr, reinterpret_cast<float*>(smem));
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -7,6 +7,7 @@
 // one thread or warp, so results never depend on Tc.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 
@@ -114,43 +115,53 @@ __global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __re
 
 // u[s, t, c] = SiLU(b_c + sum_k w[c][k] xi[s, t-K+1+k, c]); the last K-1
 // inputs of every (stream, channel) persist in win[S][K-1][E] across calls.
-// wt is the tap matrix stored [K][E] (channel innermost, coalesced).  A CTA
-// covers 128 channels of G consecutive streams, loading the taps once.
+// wt is the tap matrix stored [K][E] (channel innermost).  A thread owns four
+// adjacent channels (16-byte loads and stores) of G consecutive streams.
 template <int K, int G>
 __global__ void __launch_bounds__(128)
 k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ wt,
             const float* __restrict__ bconv, float* __restrict__ win,
             float* __restrict__ u, __nv_bfloat16* __restrict__ u_b, int S, int Tc) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= E) return;
-    float wv[K];
+    float4 wv[K];
 #pragma unroll
-    for (int k = 0; k < K; k++) wv[k] = wt[(size_t)k * E + c];
-    const float bc = bconv[c];
+    for (int k = 0; k < K; k++) wv[k] = *reinterpret_cast<const float4*>(wt + (size_t)k * E + c);
+    const float4 bc = *reinterpret_cast<const float4*>(bconv + c);
     for (int g = 0; g < G; g++) {
         const int s = blockIdx.y * G + g;
         if (s >= S) break;
-        float h[K];
+        float4 h[K];
 #pragma unroll
-        for (int k = 0; k < K - 1; k++) h[k] = win[((size_t)s * (K - 1) + k) * E + c];
+        for (int k = 0; k < K - 1; k++) h[k] = *reinterpret_cast<const float4*>(win + ((size_t)s * (K - 1) + k) * E + c);
         size_t row = (size_t)s * Tc;
-        float xi = xz[row * 2 * E + c];
+        float4 xi = *reinterpret_cast<const float4*>(xz + row * 2 * E + c);
         for (int tau = 0; tau < Tc; tau++, row++) {
-            const float xnext = (tau + 1 < Tc) ? xz[(row + 1) * 2 * E + c] : 0.f;
-            float acc = bc;
+            float4 xnext = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (tau + 1 < Tc) xnext = *reinterpret_cast<const float4*>(xz + (row + 1) * 2 * E + c);
+            float o[4];
 #pragma unroll
-            for (int k = 0; k < K - 1; k++) acc = __fmaf_rn(wv[k], h[k], acc);
-            acc = __fmaf_rn(wv[K - 1], xi, acc);
+            for (int j = 0; j < 4; j++) {
+                float acc = reinterpret_cast<const float*>(&bc)[j];
+#pragma unroll
+                for (int k = 0; k < K - 1; k++)
+                    acc = __fmaf_rn(reinterpret_cast<const float*>(&wv[k])[j], reinterpret_cast<const float*>(&h[k])[j], acc);
+                acc = __fmaf_rn(reinterpret_cast<const float*>(&wv[K - 1])[j], reinterpret_cast<const float*>(&xi)[j], acc);
+                o[j] = silu_f(acc);
+            }
 #pragma unroll
             for (int k = 0; k + 1 < K - 1; k++) h[k] = h[k + 1];
             h[K - 2] = xi;
-            const float uo = silu_f(acc);
-            u[row * E + c] = uo;
-            if (u_b) u_b[row * E + c] = __float2bfloat16_rn(uo);
+            *reinterpret_cast<float4*>(u + row * E + c) = make_float4(o[0], o[1], o[2], o[3]);
+            if (u_b) {
+                __nv_bfloat162* bp = reinterpret_cast<__nv_bfloat162*>(u_b + row * E + c);
+                bp[0] = __floats2bfloat162_rn(o[0], o[1]);
+                bp[1] = __floats2bfloat162_rn(o[2], o[3]);
+            }
             xi = xnext;
         }
 #pragma unroll
-        for (int k = 0; k < K - 1; k++) win[((size_t)s * (K - 1) + k) * E + c] = h[k];
+        for (int k = 0; k < K - 1; k++) *reinterpret_cast<float4*>(win + ((size_t)s * (K - 1) + k) * E + c) = h[k];
     }
 }
 
@@ -175,7 +186,8 @@ k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* _
        const float* __restrict__ Dv, float* __restrict__ hstate, float* __restrict__ yg,
        __nv_bfloat16* __restrict__ yg_b, int E, int S, int Tc) {
     constexpr int W = R + 2 * NS;   // dbc row width
-    __shared__ float sm[kScanRowsSmem][W];
+    static_assert(R % 4 == 0 && NS % 4 == 0, "rows are read as float4");
+    __shared__ __align__(16) float sm[kScanRowsSmem][W];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int s_first = blockIdx.y * G;
     const int n_streams = min(G, S - s_first);
@@ -490,9 +502,37 @@ struct DecArgs {
     int S;
 };
 
+// Embedding + first-block LayerNorm of one token by one warp (the same
+// arithmetic as k_embed_ln), used to prepare the next decode step.
+struct NextEmbed {
+    const float* embed;
+    const float* g;
+    const float* b;
+    float* x;
+    float* xn;
+    __nv_bfloat16* xn_b;
+};
+
+template <int VPT>
+__device__ __forceinline__ void warp_embed_ln(const NextEmbed& ne, int tok, size_t row, int lane) {
+    constexpr int d = VPT * 32;
+    float v[VPT], y[VPT];
+#pragma unroll
+    for (int i = 0; i < VPT; i++) v[i] = ne.embed[(size_t)tok * d + lane + 32 * i];
+    warp_layernorm<VPT>(v, ne.g, ne.b, lane, y);
+#pragma unroll
+    for (int i = 0; i < VPT; i++) {
+        ne.x[row * d + lane + 32 * i] = v[i];
+        if (ne.xn_b) ne.xn_b[row * d + lane + 32 * i] = __float2bfloat16_rn(y[i]);
+        else ne.xn[row * d + lane + 32 * i] = y[i];
+    }
+}
+
 // One warp per stream, one step: softmax -> histogram -> decode byte t+1,
-// feed it back as the next step's input; finished streams are masked.
-__global__ void k_decode(DecArgs a) {
+// and prepare the next step's input rows (embedding + first LayerNorm of the
+// decoded byte); finished streams are masked.
+template <int VPT>
+__global__ void k_decode(DecArgs a, NextEmbed ne) {
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (s >= a.S) return;
@@ -522,6 +562,7 @@ __global__ void k_decode(DecArgs a) {
         a.out[a.out_off[s] + a.t + 1] = (uint8_t)sym;
         a.tokens[s] = (uint8_t)sym;
     }
+    if (a.t + 2 < len) warp_embed_ln<VPT>(ne, sym, (size_t)s, lane);
 }
 
 // Coder set-up: encoder state, raw first byte copied through.
@@ -597,6 +638,33 @@ __global__ void k_dec_finish(const uint64_t* cin_size, const uint64_t* lens, Cod
 __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = __float2bfloat16_rn(in[i]);
+}
+
+// Per-row FP8 quantisation of an activation matrix for the E4M3 GEMM:
+// scale[m] = max_k |A[m][k]| / 448 and q[m][k] = e4m3(A[m][k] * (448 / max)),
+// rounded to nearest and saturated; one warp per row, K <= 1024.
+__global__ void k_quant_rows_e4m3(const float* __restrict__ A, __nv_fp8_e4m3* __restrict__ q,
+                                  float* __restrict__ scale, long long M, int K) {
+    const int lane = threadIdx.x & 31;
+    const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= M) return;
+    const float* a = A + row * K;
+    float amax = 0.f;
+    for (int k = 4 * lane; k < K; k += 128) {
+        const float4 v = *reinterpret_cast<const float4*>(a + k);
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    amax = warp_max(amax);
+    const float inv = amax > 0.f ? __fdiv_rn(448.0f, amax) : 1.0f;
+    if (lane == 0) scale[row] = amax > 0.f ? __fdiv_rn(amax, 448.0f) : 1.0f;
+    __nv_fp8_e4m3* o = q + row * K;
+    for (int k = 4 * lane; k < K; k += 128) {
+        const float4 v = *reinterpret_cast<const float4*>(a + k);
+        o[k + 0] = __nv_fp8_e4m3(__fmul_rn(v.x, inv));
+        o[k + 1] = __nv_fp8_e4m3(__fmul_rn(v.y, inv));
+        o[k + 2] = __nv_fp8_e4m3(__fmul_rn(v.z, inv));
+        o[k + 3] = __nv_fp8_e4m3(__fmul_rn(v.w, inv));
+    }
 }
 
 // Gather each stream's used bytes from its output slot into one packed buffer.

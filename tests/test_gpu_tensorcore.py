@@ -178,3 +178,76 @@ def test_tf32x3_paper_scale(api, model_dir):
     assert m.decompress(comp, [len(s) for s in streams]) == streams
     om = O.Model(path)
     assert np.abs(m.logprobs(streams[3][:400]) - om.logprobs(streams[3][:400])).max() <= 1e-3
+
+
+# ------------------------------------------------------------------ FP8 E4M3
+
+def e4m3_quant_rows(X):
+    """Per-row scale max|x| / 448 and E4M3 values (round to nearest even,
+    saturated), computed in float32 as the kernels do."""
+    import torch
+    X = np.ascontiguousarray(X, np.float32)
+    amax = np.abs(X).max(axis=1).astype(np.float32)
+    inv = np.where(amax > 0, np.float32(448.0) / np.where(amax > 0, amax, 1), 1).astype(np.float32)
+    scale = np.where(amax > 0, amax / np.float32(448.0), 1).astype(np.float32)
+    y = np.clip((X * inv[:, None]).astype(np.float32), -448, 448)
+    q = torch.from_numpy(y).to(torch.float8_e4m3fn).float().numpy()
+    return q, scale
+
+
+@pytest.mark.parametrize("shape", [(128, 128, 128), (300, 1024, 256), (4096, 48, 512), (1000, 256, 512),
+                                   (129, 36, 128), (513, 256, 1024)])
+def test_fp8_gemm_kernel(api, shape):
+    M, N, K = shape
+    g = np.random.default_rng(M + 3 * N + K)
+    A = g.normal(0, 1, (M, K)).astype(np.float32)
+    W = g.normal(0, 0.05, (N, K)).astype(np.float32)
+    bias = g.normal(0, 0.1, N).astype(np.float32)
+    C_in = g.normal(0, 1, (M, N)).astype(np.float32)
+    qa, sa = e4m3_quant_rows(A)
+    qw, sw = e4m3_quant_rows(W)
+    exact = (qa.astype(np.float64) @ qw.astype(np.float64).T) * sa[:, None] * sw[None, :]
+    mag = (np.abs(qa.astype(np.float64)) @ np.abs(qw.astype(np.float64)).T) * sa[:, None] * sw[None, :]
+    for epi in range(5):
+        got = api.gemm(A, W, bias, epi, C_in, precision=api.PREC_FP8)
+        ref = exact.copy()
+        if epi in (1, 3, 4):
+            ref = ref + bias
+        if epi == 3:
+            from scipy.special import erf
+            ref = 0.5 * ref * (1 + erf(ref / np.sqrt(2)))
+        if epi in (2, 4):
+            ref = C_in + ref
+        bound = 4 * 2.0 ** -24 * (K + 4) * (mag + np.abs(bias) + np.abs(C_in)) + 1e-6
+        err = np.abs(got - ref)
+        assert (err <= bound).all(), (epi, float(err.max()), float((err / bound).max()))
+
+
+def test_fp8_model(api, model_dir):
+    """FP8 projections (d_model 128, 2 layers): lossless, encoder and decoder
+    in lockstep, code length within 0.5 % of the FP64 oracle."""
+    shape = synth.ModelShape(d_model=128, n_layer=2)
+    path = synth.make_model_file(os.path.join(model_dir, "d128.boaw"), shape, seed=11)
+    m = api.Model(path, precision=api.PREC_FP8)
+    streams = [synth.records_stream(300 + i, n) for i, n in enumerate([3000, 1, 0, 2, 1500, 2048])]
+    n_steps = sum(max(len(s) - 1, 0) for s in streams)
+    m.enable_cdf_trace(True)
+    try:
+        comp = m.compress(streams)
+        enc = m.read_cdf_trace(n_steps)
+        out = m.decompress(comp, [len(s) for s in streams])
+        dec = m.read_cdf_trace(n_steps)
+    finally:
+        m.enable_cdf_trace(False)
+    assert out == streams and np.array_equal(enc, dec)
+    om = O.Model(path)
+    ref = om.compress_batch(streams)
+    gap = (sum(map(len, comp)) - sum(map(len, ref))) / sum(map(len, ref))
+    err = np.abs(m.logprobs(streams[0][:1500]) - om.logprobs(streams[0][:1500])).max()
+    print(f"FP8 max |dlog2p| = {err:.3e}, code-length gap = {gap:+.3e}")
+    assert abs(gap) <= 0.005
+    assert m.compress([streams[4]] * 9)[5] == comp[4]
+    with pytest.raises(api.BoaError):
+        api.Model(os.path.join(model_dir, "tiny.boaw") if os.path.exists(os.path.join(model_dir, "tiny.boaw"))
+                  else synth.make_model_file(os.path.join(model_dir, "t64.boaw"), synth.TINY, seed=1),
+                  precision=api.PREC_FP8)
