@@ -60,8 +60,10 @@ typedef struct {
     int device;                     /* CUDA device ordinal */
     int precision;                  /* boa_precision */
     void* cuda_stream;              /* cudaStream_t to run on; NULL = library-owned stream */
-    size_t max_rows;                /* compression workspace: rows (stream x step) per
+    size_t max_rows;                /* compression workspace: rows (slot x step) per
                                        chunk; 0 = 262144 (about 3 GB at d_model 256) */
+    size_t max_slots;               /* streams in flight at once; 0 = 8192.  Longer inputs are
+                                       queued: a slot takes its next stream when one finishes */
 } boa_opts;
 
 typedef struct boa_model boa_model; /* opaque; owned by the library */
@@ -164,6 +166,79 @@ boa_status boa_profile_enable(boa_model* model, int on, int decode_step_stride);
 boa_status boa_profile_reset(boa_model* model);
 boa_status boa_profile_read(const boa_model* model, int phase, int kernel_class, uint64_t* launches,
                             double* total_ms, double* flops, double* bytes);
+
+/* Launch configuration chosen by boa_autotune. */
+typedef struct {
+    size_t max_rows;        /* compression rows (slot x step) per chunk */
+    int scan_group;         /* decompression scan: streams per CTA */
+    double compress_ms;     /* estimated time for the whole workload */
+    double decompress_ms;
+} boa_tuning;
+
+/* Time candidate launch configurations on a synthetic batch shaped like the
+ * caller's workload (n_streams streams of stream_len bytes; a 512-byte sample
+ * of each is run) and keep the fastest in the model: the compression chunk
+ * size (max_rows in 2^16 .. 2^19) and the decode scan's streams per CTA
+ * (1 .. 16).  Neither knob changes any result: rows are computed the same
+ * way whatever the chunking or grouping.  out (host, may be NULL) receives
+ * the choice and the extrapolated times.  Allocates and frees a scratch
+ * batch on the device.  Errors: BOA_ERR_ARG, BOA_ERR_CUDA, BOA_ERR_OOM. */
+boa_status boa_autotune(boa_model* model, size_t n_streams, size_t stream_len, boa_tuning* out);
+
+/* ------------------------------------------------------------ container
+ * The .boa container of the paper (section "Coders & Parallelisation"): the
+ * input cut into chunks of chunk_len bytes (the last one shorter), each
+ * compressed as one stream (its first byte raw), plus the total length, the
+ * nominal and last chunk lengths, the model fingerprint and a CRC-32
+ * protected index of per-chunk payload offsets and sizes.  Byte layout:
+ * 56-byte header ("BOA1", u32 version 1, u64 fingerprint, u64 total length,
+ * u64 chunk length, u64 chunk count n, u64 last chunk length, u32 CRC-32 of
+ * header bytes 0..47, u32 CRC-32 of the index), n x (u64 offset, u64 size),
+ * payload.  All buffers are host memory owned by the caller. */
+
+/* Capacity boa_pack needs for len bytes in chunks of chunk_len (0 if chunk_len is 0). */
+size_t boa_pack_bound(size_t len, size_t chunk_len);
+
+/* Compress data into a container.  Errors: BOA_ERR_ARG, BOA_ERR_OUTPUT_TOO_SMALL
+ * (cap < boa_pack_bound), and those of boa_compress. */
+boa_status boa_pack(boa_model* model, const uint8_t* data, size_t len, size_t chunk_len, uint8_t* out,
+                    size_t cap, size_t* out_size);
+
+/* Read a container header (no model needed): total length and fingerprint.
+ * Errors: BOA_ERR_FORMAT (not a container), BOA_ERR_CORRUPT (short or header CRC). */
+boa_status boa_unpack_info(const uint8_t* container, size_t size, uint64_t* total_len, uint64_t* fingerprint);
+
+/* Decompress a container into out (cap >= its total length); *out_len gets the
+ * length.  Errors: BOA_ERR_FINGERPRINT (written with another model),
+ * BOA_ERR_CORRUPT (header or index CRC, inconsistent layout, a chunk that does
+ * not decode cleanly), BOA_ERR_OUTPUT_TOO_SMALL, and those of boa_decompress. */
+boa_status boa_unpack(boa_model* model, const uint8_t* container, size_t size, uint8_t* out, size_t cap,
+                      size_t* out_len);
+
+/* CRC-32, IEEE 802.3 polynomial (the container's checksum). */
+uint32_t boa_crc32(const uint8_t* data, size_t n);
+
+/* ------------------------------------------------------------ training
+ * The selective scan for training the predictor (paper App. A recurrence
+ * h_t = exp(delta_t A) h_{t-1} + delta_t B_t u_t, y_t = C_t . h_t + D u_t,
+ * h_0 = 0, and its reverse-mode gradient), on whole sequences with states
+ * recomputed per chunk instead of stored.  All pointers are device memory
+ * (float32) owned by the caller; work is queued on cuda_stream (NULL =
+ * legacy default stream) and the calls return without waiting.  d_state N
+ * must be 16.  Layouts: u, delta, y, dy, du, ddelta [Bsz][T][E]; Bm, Cm
+ * [Bsz][T][N]; A [E][N]; D [E]; hin [Bsz][ceil(T/chunk)][N][E] (states
+ * entering each chunk, written by the forward, read by the backward);
+ * scratch [Bsz][chunk][N][E]; dA_part [Bsz][E][N] and dD_part [Bsz][E]
+ * (sum over Bsz for dA, dD); dB_part, dC_part [Bsz][T][ceil(E/128)][N]
+ * (sum over the third axis for dB, dC).  Errors: BOA_ERR_ARG, BOA_ERR_CUDA. */
+boa_status boa_scan_train_fwd(size_t Bsz, size_t T, size_t E, size_t N, size_t chunk, const float* u,
+                              const float* delta, const float* A, const float* Bm, const float* Cm,
+                              const float* D, float* y, float* hin, void* cuda_stream);
+boa_status boa_scan_train_bwd(size_t Bsz, size_t T, size_t E, size_t N, size_t chunk, const float* u,
+                              const float* delta, const float* A, const float* Bm, const float* Cm,
+                              const float* D, const float* dy, const float* hin, float* scratch,
+                              float* du, float* ddelta, float* dA_part, float* dD_part, float* dB_part,
+                              float* dC_part, void* cuda_stream);
 
 /* Thread-local message describing the last error on this thread. */
 const char* boa_last_error(void);

@@ -232,6 +232,58 @@ void orc_selective_scan(int T, int E, int N, const double* u, const double* delt
     free(h);
 }
 
+/* Gradient of L = sum_t sum_c dy[t][c] y[t][c] through the selective scan
+ * (App. A recurrence, h_0 = 0), by reverse accumulation.  With
+ * a_t = exp(delta_t A) and g_t = dL/dh_t = C_t dy_t + a_{t+1} g_{t+1}:
+ *   dC_t += dy_t h_t (over channels)   da_t = g_t h_{t-1}
+ *   ddelta_t += da_t a_t A + g_t B_t u_t      dA += da_t a_t delta_t
+ *   dB_t += g_t delta_t u_t (over channels)   du_t += g_t delta_t B_t + dy_t D
+ *   dD += dy_t u_t.
+ * All outputs are overwritten. */
+void orc_selective_scan_grad(int T, int E, int N, const double* u, const double* delta, const double* A,
+                             const double* B, const double* C, const double* D, const double* dy, double* du,
+                             double* ddelta, double* dA, double* dB, double* dC, double* dD) {
+    double* h = (double*)calloc((size_t)T * E * N, sizeof(double));      /* h[t][c][n] */
+    double* g = (double*)calloc((size_t)E * N, sizeof(double));
+    for (int t = 0; t < T; t++)
+        for (int c = 0; c < E; c++)
+            for (int n = 0; n < N; n++) {
+                double prev = t > 0 ? h[((size_t)(t - 1) * E + c) * N + n] : 0.0;
+                h[((size_t)t * E + c) * N + n] = exp(delta[(size_t)t * E + c] * A[(size_t)c * N + n]) * prev
+                                                 + delta[(size_t)t * E + c] * B[(size_t)t * N + n] * u[(size_t)t * E + c];
+            }
+    memset(du, 0, sizeof(double) * T * E);
+    memset(ddelta, 0, sizeof(double) * T * E);
+    memset(dA, 0, sizeof(double) * E * N);
+    memset(dB, 0, sizeof(double) * T * N);
+    memset(dC, 0, sizeof(double) * T * N);
+    memset(dD, 0, sizeof(double) * E);
+    for (int t = T - 1; t >= 0; t--) {
+        for (int c = 0; c < E; c++) {
+            const double dl = delta[(size_t)t * E + c], uc = u[(size_t)t * E + c], gy = dy[(size_t)t * E + c];
+            for (int n = 0; n < N; n++) {
+                double* gc = &g[(size_t)c * N + n];
+                const double ht = h[((size_t)t * E + c) * N + n];
+                const double hp = t > 0 ? h[((size_t)(t - 1) * E + c) * N + n] : 0.0;
+                const double an = A[(size_t)c * N + n];
+                const double a = exp(dl * an);
+                *gc += gy * C[(size_t)t * N + n];
+                dC[(size_t)t * N + n] += gy * ht;
+                const double da = *gc * hp;
+                ddelta[(size_t)t * E + c] += da * a * an + *gc * B[(size_t)t * N + n] * uc;
+                dA[(size_t)c * N + n] += da * a * dl;
+                dB[(size_t)t * N + n] += *gc * dl * uc;
+                du[(size_t)t * E + c] += *gc * dl * B[(size_t)t * N + n];
+                *gc *= a;
+            }
+            du[(size_t)t * E + c] += gy * D[c];
+            dD[c] += gy * uc;
+        }
+    }
+    free(h);
+    free(g);
+}
+
 void orc_softmax(const double* l, double* p) {
     double m = l[0], Z = 0.0;
     for (int a = 1; a < 256; a++) if (l[a] > m) m = l[a];

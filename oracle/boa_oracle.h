@@ -36,6 +36,10 @@ void orc_log2_softmax(const double* logits, double* lp);             /* 256 */
 void orc_selective_scan(int T, int E, int N, const double* u, const double* delta,
                         const double* A, const double* B, const double* C,
                         const double* D, double* y);                 /* h_0 = 0 */
+/* Reverse-mode gradient of sum(dy * y) through orc_selective_scan. */
+void orc_selective_scan_grad(int T, int E, int N, const double* u, const double* delta, const double* A,
+                             const double* B, const double* C, const double* D, const double* dy, double* du,
+                             double* ddelta, double* dA, double* dB, double* dC, double* dD);
 void orc_causal_conv(int T, int E, int K, const double* x, const double* w,
                      const double* b, double* out);                  /* zero history, no SiLU */
 

@@ -32,6 +32,7 @@ def lib():
         L.orc_log2_softmax.argtypes = [vp, vp]
         L.orc_selective_scan.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.orc_causal_conv.argtypes = [i32, i32, i32, vp, vp, vp, vp]
+        L.orc_selective_scan_grad.argtypes = [i32, i32, i32] + [vp] * 13
         L.orc_quantise.argtypes = [vp, vp]
         L.orc_quantise_f32.argtypes = [vp, vp]
         L.orc_cdf_from_hist.argtypes = [vp, vp]
@@ -183,6 +184,16 @@ def selective_scan(u, delta, A, B, Cm, D):
     y = np.zeros((T, E))
     lib().orc_selective_scan(T, E, N, _p(u), _p(delta), _p(A), _p(B), _p(Cm), _p(D), _p(y))
     return y
+
+
+def selective_scan_grad(u, delta, A, B, Cm, D, dy):
+    """Gradients of sum(dy * scan(...)) wrt u, delta, A, B, C, D."""
+    u, delta, A, B, Cm, D, dy = map(_f64, (u, delta, A, B, Cm, D, dy))
+    T, E = u.shape
+    N = A.shape[1]
+    out = [np.zeros((T, E)), np.zeros((T, E)), np.zeros((E, N)), np.zeros((T, N)), np.zeros((T, N)), np.zeros(E)]
+    lib().orc_selective_scan_grad(T, E, N, _p(u), _p(delta), _p(A), _p(B), _p(Cm), _p(D), _p(dy), *[_p(o) for o in out])
+    return dict(zip(["u", "delta", "A", "B", "C", "D"], out))
 
 
 def causal_conv(x, w, b):

@@ -24,6 +24,14 @@ SIGNATURES = {
     "boa_decompress_device": (i32, [vp, sz, vp, vp, vp, vp, vp, vp]),
     "boa_last_launch_count": (u64, [vp]),
     "boa_last_error": (C.c_char_p, []),
+    "boa_autotune": (i32, [vp, sz, sz, vp]),
+    "boa_pack_bound": (sz, [sz, sz]),
+    "boa_pack": (i32, [vp, vp, sz, sz, vp, sz, C.POINTER(sz)]),
+    "boa_unpack_info": (i32, [vp, sz, C.POINTER(u64), C.POINTER(u64)]),
+    "boa_unpack": (i32, [vp, vp, sz, vp, sz, C.POINTER(sz)]),
+    "boa_crc32": (C.c_uint32, [vp, sz]),
+    "boa_scan_train_fwd": (i32, [sz, sz, sz, sz, sz] + [vp] * 9),
+    "boa_scan_train_bwd": (i32, [sz, sz, sz, sz, sz] + [vp] * 16),
     "boa_profile_enable": (i32, [vp, i32, i32]),
     "boa_profile_reset": (i32, [vp]),
     "boa_profile_read": (i32, [vp, i32, i32, vp, vp, vp, vp]),

@@ -18,21 +18,32 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def crc32(data: bytes) -> int:
+    buf = np.frombuffer(data, np.uint8) if data else np.zeros(1, np.uint8)
+    return int(load().boa_crc32(_p(buf), len(data)))
+
+
 def max_compressed_size(n: int) -> int:
     return int(load().boa_max_compressed_size(n))
 
 
 class _Opts(C.Structure):
-    _fields_ = [("device", C.c_int), ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("max_rows", C.c_size_t)]
+    _fields_ = [("device", C.c_int), ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("max_rows", C.c_size_t),
+                ("max_slots", C.c_size_t)]
+
+
+class _Tuning(C.Structure):
+    _fields_ = [("max_rows", C.c_size_t), ("scan_group", C.c_int), ("compress_ms", C.c_double),
+                ("decompress_ms", C.c_double)]
 
 
 class Model:
     """A predictor loaded on the GPU (boa_load_model)."""
 
     def __init__(self, path: str, device: int = 0, precision: int = PREC_FP32, cuda_stream: int | None = None,
-                 max_rows: int = 0):
+                 max_rows: int = 0, max_slots: int = 0):
         self._h = C.c_void_p()
-        opts = _Opts(device, precision, cuda_stream, max_rows)
+        opts = _Opts(device, precision, cuda_stream, max_rows, max_slots)
         check(load().boa_load_model(os.fsencode(path), C.byref(opts), C.byref(self._h)))
 
     def close(self):
@@ -107,6 +118,33 @@ class Model:
             sz = _p(in_sizes)
         check(load().boa_decompress_device(self._h, n, C.c_void_p(d_in_ptr), _p(in_offsets), sz, _p(lens),
                                            C.c_void_p(d_out_ptr), _p(out_offsets)))
+
+    # ----------------------------------------------------------- container
+    def pack(self, data: bytes, chunk_len: int = 16384) -> bytes:
+        """boa_pack: one buffer -> .boa container (chunks of chunk_len bytes)."""
+        cap = int(load().boa_pack_bound(len(data), chunk_len))
+        out = np.zeros(max(cap, 1), np.uint8)
+        buf = np.frombuffer(data, np.uint8) if data else np.zeros(1, np.uint8)
+        size = C.c_size_t()
+        check(load().boa_pack(self._h, _p(buf), len(data), chunk_len, _p(out), cap, C.byref(size)))
+        return out[:size.value].tobytes()
+
+    def unpack(self, container: bytes) -> bytes:
+        """boa_unpack: .boa container -> original bytes."""
+        buf = np.frombuffer(container, np.uint8) if container else np.zeros(1, np.uint8)
+        total, fp = C.c_uint64(), C.c_uint64()
+        check(load().boa_unpack_info(_p(buf), len(container), C.byref(total), C.byref(fp)))
+        out = np.zeros(max(int(total.value), 1), np.uint8)
+        n = C.c_size_t()
+        check(load().boa_unpack(self._h, _p(buf), len(container), _p(out), int(total.value), C.byref(n)))
+        return out[:n.value].tobytes()
+
+    def autotune(self, n_streams: int, stream_len: int) -> dict:
+        """boa_autotune: pick chunk size and decode scan grouping for this shape."""
+        t = _Tuning()
+        check(load().boa_autotune(self._h, n_streams, stream_len, C.byref(t)))
+        return {"max_rows": int(t.max_rows), "scan_group": int(t.scan_group),
+                "compress_ms_est": t.compress_ms, "decompress_ms_est": t.decompress_ms}
 
     # ----------------------------------------------------------- benchmark hooks
     KERNEL_CLASSES = ["embed_ln", "gemm_in_proj", "conv_silu", "gemm_x_proj", "scan", "gemm_out_proj",

@@ -28,6 +28,7 @@
 #include "gemm_fp32.cuh"
 #include "gemm_tc.cuh"
 #include "kernels.cuh"
+#include "scan_train.cuh"
 
 using namespace boa;
 
@@ -154,11 +155,14 @@ struct boa_model {
     DevBuf<float> a8s;           // their per-row scales
     DevBuf<int> err;
     DevBuf<CoderState> st;
+    DevBuf<SlotState> slots;
+    DevBuf<int> sched, slot_beg;
     DevBuf<uint8_t> tokens, d_in, d_out, d_pack;
     DevBuf<uint32_t> flags;
     DevBuf<uint64_t> in_off, out_off, lens, sizes, trace_off, trace, pack_off;
     HostBuf<uint8_t> h_in, h_out;
     HostBuf<uint64_t> h_u64, h_pack;
+    HostBuf<int> h_sched;
     HostBuf<uint32_t> h_u32;
 
     bool trace_on = false;
@@ -177,6 +181,9 @@ struct boa_model {
     uint64_t prof_launches[2][BOA_KC_COUNT] = {};
     double prof_ms[2][BOA_KC_COUNT] = {}, prof_flops[2][BOA_KC_COUNT] = {}, prof_bytes[2][BOA_KC_COUNT] = {};
     size_t max_rows = 1u << 18;
+    size_t max_slots = 8192;        // streams in flight
+    bool use_graphs = true;         // decode step loop as CUDA graphs (when not profiling)
+    int scan_group = 0;             // decode scan streams per CTA; 0 = default
 };
 
 static uint64_t fnv1a64(const uint8_t* p, size_t n) {
@@ -255,12 +262,12 @@ extern "C" uint64_t boa_last_launch_count(const boa_model* m) { return m ? m->la
 static void free_workspace(boa_model* m) {
     m->x.release(); m->xn.release(); m->xz.release(); m->u.release(); m->dbc.release();
     m->yg.release(); m->logits.release(); m->hid.release(); m->h.release(); m->conv.release();
-    m->st.release(); m->tokens.release(); m->d_in.release(); m->d_out.release(); m->flags.release();
+    m->st.release(); m->slots.release(); m->sched.release(); m->slot_beg.release(); m->tokens.release(); m->d_in.release(); m->d_out.release(); m->flags.release();
     m->in_off.release(); m->out_off.release(); m->lens.release(); m->sizes.release();
     m->trace_off.release(); m->trace.release(); m->d_pack.release(); m->pack_off.release();
     m->xn_b.release(); m->u_b.release(); m->yg_b.release(); m->x_b.release(); m->hid_b.release(); m->err.release();
     m->a8.release(); m->a8s.release();
-    m->h_in.release(); m->h_out.release(); m->h_u64.release(); m->h_pack.release(); m->h_u32.release();
+    m->h_in.release(); m->h_out.release(); m->h_u64.release(); m->h_pack.release(); m->h_u32.release(); m->h_sched.release();
 }
 
 extern "C" void boa_free_model(boa_model* m) {
@@ -317,7 +324,7 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
     const size_t total = 256 * (size_t)d + nl * per_layer + 256 * (size_t)d + 256;
     if (buf.size() != 40 + total * 4) return fail(BOA_ERR_FORMAT, "weight file size %zu, expected %zu", buf.size(), 40 + total * 4);
 
-    boa_opts o = {0, BOA_PREC_FP32, nullptr, 0};
+    boa_opts o = {0, BOA_PREC_FP32, nullptr, 0, 0};
     if (opts) o = *opts;
     if (o.precision < BOA_PREC_FP32 || o.precision > BOA_PREC_FP8)
         return fail(BOA_ERR_ARG, "precision %d not supported", o.precision);
@@ -377,6 +384,7 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
     m->device = o.device;
     m->precision = o.precision;
     if (o.max_rows) m->max_rows = std::max<size_t>(o.max_rows, 1);
+    if (o.max_slots) m->max_slots = std::max<size_t>(o.max_slots, 1);
     m->d = d; m->nl = nl; m->N = N; m->K = K; m->E = E; m->r = r; m->ffn_mult = ffn; m->F = F; m->R2 = R2;
     m->fingerprint = fnv1a64(buf.data(), buf.size());
     cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, o.device);
@@ -769,9 +777,14 @@ static boa_status ln_ln(boa_model* m, long long rows, int l) {
     return check_launch(m, "ln_ln");
 }
 
-// Streams per CTA for the per-channel kernels: one step over many streams
-// (decompression) groups 8 streams so the per-channel weights load once.
-static int stream_group(int S, int Tc) { return (Tc == 1 && S >= 1024) ? 8 : 1; }
+// Streams per CTA for the scan: one step over many streams (decompression)
+// groups several streams so the per-channel weights load once.  The group
+// size is a tuning knob (boa_autotune); it never changes a result.
+static int stream_group(const boa_model* m, int S, int Tc) {
+    if (Tc != 1) return 1;
+    if (m->scan_group > 0) return m->scan_group;
+    return S >= 1024 ? 8 : 1;
+}
 
 static boa_status conv(boa_model* m, int l, int S, int Tc) {
     const DevLayer& L = m->layers[l];
@@ -794,7 +807,7 @@ static boa_status conv(boa_model* m, int l, int S, int Tc) {
 
 static boa_status scan(boa_model* m, int l, int S, int Tc) {
     const DevLayer& L = m->layers[l];
-    const int G = stream_group(S, Tc);
+    const int G = stream_group(m, S, Tc);
     dim3 grid((m->E + kScanThreads - 1) / kScanThreads, (S + G - 1) / G);
     float* hs = m->h.p + (size_t)l * S * m->N * m->E;
     const double rows = (double)S * Tc;
@@ -804,11 +817,16 @@ static boa_status scan(boa_model* m, int l, int S, int Tc) {
 #define SCAN_CASE(RR, GG)                                                                                         \
     k_scan<16, RR, GG><<<grid, kScanThreads, 0, m->stream>>>(m->u.p, m->xz.p, m->dbc.p, L.dt_w, L.dt_b, L.A2, L.D, \
                                                              hs, m->yg.p, ygb, m->E, S, Tc)
-    if (G == 8) {
-        switch (m->r) { case 4: SCAN_CASE(4, 8); break; case 8: SCAN_CASE(8, 8); break; default: SCAN_CASE(16, 8); break; }
-    } else {
-        switch (m->r) { case 4: SCAN_CASE(4, 1); break; case 8: SCAN_CASE(8, 1); break; default: SCAN_CASE(16, 1); break; }
+#define SCAN_G(GG) \
+    switch (m->r) { case 4: SCAN_CASE(4, GG); break; case 8: SCAN_CASE(8, GG); break; default: SCAN_CASE(16, GG); break; }
+    switch (G) {
+        case 2: SCAN_G(2); break;
+        case 4: SCAN_G(4); break;
+        case 8: SCAN_G(8); break;
+        case 16: SCAN_G(16); break;
+        default: SCAN_G(1); break;
     }
+#undef SCAN_G
 #undef SCAN_CASE
     return check_launch(m, "scan");
 }
@@ -919,13 +937,19 @@ static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
     TRY(m->h.ensure((size_t)m->nl * S * m->N * E));
     TRY(m->conv.ensure((size_t)m->nl * S * (m->K - 1) * E));
     TRY(m->st.ensure(S));
-    TRY(m->tokens.ensure(S));
-    TRY(m->flags.ensure(S));
-    TRY(m->in_off.ensure(S + 1));
-    TRY(m->out_off.ensure(S + 1));
-    TRY(m->lens.ensure(S));
-    TRY(m->sizes.ensure(S));
-    TRY(m->trace_off.ensure(S));
+    TRY(m->slots.ensure(S));
+    TRY(m->slot_beg.ensure(S + 1));
+    return BOA_OK;
+}
+
+static boa_status ensure_streams(boa_model* m, size_t n) {
+    TRY(m->flags.ensure(n));
+    TRY(m->in_off.ensure(n + 1));
+    TRY(m->out_off.ensure(n + 1));
+    TRY(m->lens.ensure(n));
+    TRY(m->sizes.ensure(n));
+    TRY(m->trace_off.ensure(n));
+    TRY(m->sched.ensure(n));
     return BOA_OK;
 }
 
@@ -962,19 +986,94 @@ static boa_status upload_index(boa_model* m, size_t S, const uint64_t* in_off, c
     return BOA_OK;
 }
 
+// Slot schedule: streams of length >= 2 go, longest first, to the slot with
+// the least work so far (ties to the lower slot); each slot runs its list in
+// order.  The assignment only balances work: a stream's bytes do not depend
+// on its slot.
+struct Schedule {
+    int S = 0;
+    std::vector<int> sched, beg;
+    std::vector<std::vector<int>> lists;
+};
+
+static void build_schedule(const uint64_t* lens, size_t n, size_t max_slots, Schedule& out) {
+    std::vector<int> order;
+    for (size_t i = 0; i < n; i++)
+        if (lens[i] >= 2) order.push_back((int)i);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lens[a] > lens[b]; });
+    const int S = (int)std::min(order.size(), max_slots);
+    out.S = S;
+    out.lists.assign(S, {});
+    std::vector<std::pair<uint64_t, int>> heap;   // (load, slot), min-heap
+    for (int s = 0; s < S; s++) heap.push_back({0, s});
+    auto cmp = [](const std::pair<uint64_t, int>& a, const std::pair<uint64_t, int>& b) { return a > b; };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (int i : order) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        auto top = heap.back();
+        heap.pop_back();
+        out.lists[top.second].push_back(i);
+        top.first += lens[i] - 1;
+        heap.push_back(top);
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    out.sched.clear();
+    out.beg.assign(S + 1, 0);
+    for (int s = 0; s < S; s++) {
+        out.beg[s] = (int)out.sched.size();
+        out.sched.insert(out.sched.end(), out.lists[s].begin(), out.lists[s].end());
+    }
+    out.beg[S] = (int)out.sched.size();
+}
+
+static boa_status upload_schedule(boa_model* m, const Schedule& sc) {
+    TRY(m->h_sched.ensure(sc.sched.size() + sc.beg.size() + 1));
+    int* hp = m->h_sched.p;
+    memcpy(hp, sc.sched.data(), sc.sched.size() * 4);
+    memcpy(hp + sc.sched.size(), sc.beg.data(), sc.beg.size() * 4);
+    if (!sc.sched.empty())
+        CU(cudaMemcpyAsync(m->sched.p, hp, sc.sched.size() * 4, cudaMemcpyHostToDevice, m->stream));
+    CU(cudaMemcpyAsync(m->slot_beg.p, hp + sc.sched.size(), sc.beg.size() * 4, cudaMemcpyHostToDevice, m->stream));
+    return BOA_OK;
+}
+
 static boa_status zero_state(boa_model* m, size_t S) {
     CU(cudaMemsetAsync(m->h.p, 0, (size_t)m->nl * S * m->N * m->E * 4, m->stream));
     CU(cudaMemsetAsync(m->conv.p, 0, (size_t)m->nl * S * (m->K - 1) * m->E * 4, m->stream));
     return BOA_OK;
 }
 
-static boa_status compress_impl(boa_model* m, size_t S, const uint8_t* d_in, const uint64_t* in_off,
+static StreamTable stream_table(boa_model* m, bool decoding) {
+    StreamTable tb;
+    tb.in_off = m->in_off.p;
+    tb.in_size = decoding ? m->sizes.p : nullptr;
+    tb.lens = m->lens.p;
+    tb.out_off = m->out_off.p;
+    tb.sizes = m->sizes.p;
+    tb.flags = m->flags.p;
+    tb.trace = m->trace_on ? m->trace.p : nullptr;
+    tb.trace_off = m->trace_off.p;
+    return tb;
+}
+
+static SlotMem slot_mem(boa_model* m, int S) {
+    SlotMem sm;
+    sm.h = m->h.p;
+    sm.conv = m->conv.p;
+    sm.layers = m->nl;
+    sm.S = S;
+    sm.h_per = m->N * m->E;
+    sm.conv_per = (m->K - 1) * m->E;
+    return sm;
+}
+
+static boa_status compress_impl(boa_model* m, size_t n, const uint8_t* d_in, const uint64_t* in_off,
                                 uint8_t* d_out, const uint64_t* out_off, uint64_t* out_sizes) {
-    if (S == 0) return BOA_OK;
-    if (S > (1u << 30)) return fail(BOA_ERR_ARG, "too many streams");
-    std::vector<uint64_t> lens(S);
+    if (n == 0) return BOA_OK;
+    if (n > (1u << 30)) return fail(BOA_ERR_ARG, "too many streams");
+    std::vector<uint64_t> lens(n);
     uint64_t maxlen = 0;
-    for (size_t i = 0; i < S; i++) {
+    for (size_t i = 0; i < n; i++) {
         if (in_off[i + 1] < in_off[i] || out_off[i + 1] < out_off[i]) return fail(BOA_ERR_ARG, "offsets must be non-decreasing");
         lens[i] = in_off[i + 1] - in_off[i];
         if (out_off[i + 1] - out_off[i] < boa_max_compressed_size(lens[i]))
@@ -985,91 +1084,168 @@ static boa_status compress_impl(boa_model* m, size_t S, const uint8_t* d_in, con
     m->launches = 0;
     m->prof_step = true;
     m->prof_phase = 0;
+    Schedule sc;
+    build_schedule(lens.data(), n, m->max_slots, sc);
+    const int S = std::max(sc.S, 1);
     const int Tc = (int)std::max<uint64_t>(1, std::min<uint64_t>(maxlen > 1 ? maxlen - 1 : 1, m->max_rows / S));
-    TRY(ensure_workspace(m, S, S * (size_t)Tc));
-    TRY(upload_index(m, S, in_off, out_off, lens.data()));
-    TRY(zero_state(m, S));
-    const int tb = 128;
-    k_enc_init<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(d_in, m->in_off.p, m->lens.p, d_out, m->out_off.p,
-                                                                   m->st.p, (int)S);
-    TRY(check_launch(m, "enc_init"));
-    for (uint64_t t0 = 0; t0 + 1 < maxlen; t0 += Tc) {
-        const int tc = (int)std::min<uint64_t>(Tc, maxlen - 1 - t0);
-        TokenSrc ts{d_in, m->in_off.p, m->lens.p, nullptr, (long long)t0};
-        TRY(forward(m, ts, (int)S, tc));
-        EncArgs a{m->logits.p, d_in, m->in_off.p, m->lens.p, d_out, m->out_off.p, m->st.p,
-                  m->trace_on ? m->trace.p : nullptr, m->trace_off.p, (long long)t0, (int)S, tc};
-        {
-            ProfScope ps(m, BOA_KC_ENCODE, (double)S * tc * 256 * 8, (double)S * tc * (256 * 4 + 2));
-            k_encode<<<(unsigned)((S + 3) / 4), 128, 0, m->stream>>>(a);
-        }
-        TRY(check_launch(m, "encode"));
+    uint64_t chunks = 0;
+    for (auto& lst : sc.lists) {
+        uint64_t c = 0;
+        for (int i : lst) c += (lens[i] - 1 + Tc - 1) / Tc;
+        chunks = std::max(chunks, c);
     }
-    k_enc_finish<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(m->lens.p, d_out, m->out_off.p, m->st.p,
-                                                                     m->sizes.p, (int)S);
-    TRY(check_launch(m, "enc_finish"));
-    TRY(m->h_u32.ensure(S));
-    CU(cudaMemcpyAsync(out_sizes, m->sizes.p, S * 8, cudaMemcpyDeviceToHost, m->stream));
+    TRY(ensure_workspace(m, S, (size_t)S * Tc));
+    TRY(ensure_streams(m, n));
+    TRY(upload_index(m, n, in_off, out_off, lens.data()));
+    TRY(upload_schedule(m, sc));
+    TRY(zero_state(m, S));
+    StreamTable tb = stream_table(m, false);
+    SlotMem mem = slot_mem(m, S);
+    const int tb128 = 128;
+    k_enc_trivial<<<(unsigned)((n + tb128 - 1) / tb128), tb128, 0, m->stream>>>((int)n, d_in, tb, d_out);
+    TRY(check_launch(m, "enc_trivial"));
+    if (sc.S > 0) {
+        const unsigned wgrid = (unsigned)((S + 3) / 4);
+        k_enc_slots<<<wgrid, 128, 0, m->stream>>>(S, 1, 0, m->sched.p, m->slot_beg.p, m->slots.p, m->st.p, d_in, tb,
+                                                 d_out, mem);
+        TRY(check_launch(m, "enc_slots"));
+        TokenSrc ts{d_in, m->in_off.p, m->lens.p, m->slots.p};
+        for (uint64_t c = 0; c < chunks; c++) {
+            TRY(forward(m, ts, S, Tc));
+            {
+                ProfScope ps(m, BOA_KC_ENCODE, (double)S * Tc * 256 * 8, (double)S * Tc * (256 * 4 + 2));
+                k_encode<<<wgrid, 128, 0, m->stream>>>(m->logits.p, S, Tc, m->slots.p, m->st.p, d_in, tb, d_out);
+            }
+            TRY(check_launch(m, "encode"));
+            k_enc_slots<<<wgrid, 128, 0, m->stream>>>(S, 0, Tc, m->sched.p, m->slot_beg.p, m->slots.p, m->st.p, d_in,
+                                                     tb, d_out, mem);
+            TRY(check_launch(m, "enc_slots"));
+        }
+    }
+    TRY(m->h_u32.ensure(n));
+    CU(cudaMemcpyAsync(out_sizes, m->sizes.p, n * 8, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, n * 4, cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     prof_collect(m);
-    return check_tc_error(m);
+    TRY(check_tc_error(m));
+    for (size_t i = 0; i < n; i++)
+        if (lens[i] >= 2 && m->h_u32.p[i])
+            return fail(BOA_ERR_CUDA, "stream %zu: encoder status %u", i, m->h_u32.p[i]);
+    return BOA_OK;
 }
 
-static boa_status decompress_impl(boa_model* m, size_t S, const uint8_t* d_in, const uint64_t* in_off,
+template <int VPT>
+static void launch_dec_init(boa_model* m, int S, const uint8_t* cin, const StreamTable& tb, uint8_t* out,
+                            const NextEmbed& ne) {
+    k_dec_slots_init<VPT><<<(unsigned)((S + 3) / 4), 128, 0, m->stream>>>(S, m->sched.p, m->slot_beg.p, m->slots.p,
+                                                                         m->st.p, cin, tb, out, ne);
+}
+
+template <int VPT>
+static void launch_decode(boa_model* m, int S, const uint8_t* cin, const StreamTable& tb, uint8_t* out,
+                          const NextEmbed& ne, const SlotMem& mem) {
+    k_decode<VPT><<<(unsigned)((S + 3) / 4), 128, 0, m->stream>>>(m->logits.p, S, m->sched.p, m->slot_beg.p,
+                                                                 m->slots.p, m->st.p, cin, tb, out, ne, mem);
+}
+
+static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, const uint64_t* in_off,
                                   const uint64_t* in_sizes, const uint64_t* lens, uint8_t* d_out,
                                   const uint64_t* out_off) {
-    if (S == 0) return BOA_OK;
-    if (S > (1u << 30)) return fail(BOA_ERR_ARG, "too many streams");
-    uint64_t maxlen = 0;
-    std::vector<uint64_t> csz(S);
-    for (size_t i = 0; i < S; i++) {
+    if (n == 0) return BOA_OK;
+    if (n > (1u << 30)) return fail(BOA_ERR_ARG, "too many streams");
+    std::vector<uint64_t> csz(n);
+    for (size_t i = 0; i < n; i++) {
         if (in_off[i + 1] < in_off[i] || out_off[i + 1] < out_off[i]) return fail(BOA_ERR_ARG, "offsets must be non-decreasing");
         csz[i] = in_sizes ? in_sizes[i] : in_off[i + 1] - in_off[i];
         if (csz[i] > in_off[i + 1] - in_off[i]) return fail(BOA_ERR_ARG, "stream %zu: in_sizes exceeds its slot", i);
         if (out_off[i + 1] - out_off[i] < lens[i]) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "stream %zu: output slot too small", i);
-        maxlen = std::max(maxlen, lens[i]);
+        if (lens[i] >= 2 && csz[i] < 1) return fail(BOA_ERR_CORRUPT, "stream %zu: empty coded stream", i);
     }
     m->launches = 0;
     m->prof_phase = 1;
+    Schedule sc;
+    build_schedule(lens, n, m->max_slots, sc);
+    const int S = std::max(sc.S, 1);
+    uint64_t steps = 0;
+    for (auto& lst : sc.lists) {
+        uint64_t c = 0;
+        for (int i : lst) c += lens[i] - 1;
+        steps = std::max(steps, c);
+    }
     TRY(ensure_workspace(m, S, S));
-    TRY(upload_index(m, S, in_off, out_off, lens, csz.data()));
+    TRY(ensure_streams(m, n));
+    TRY(upload_index(m, n, in_off, out_off, lens, csz.data()));
+    TRY(upload_schedule(m, sc));
     TRY(zero_state(m, S));
-    const int tb = 128;
-    k_dec_init<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(d_in, m->in_off.p, m->sizes.p, m->lens.p, d_out,
-                                                                   m->out_off.p, m->tokens.p, m->st.p, (int)S);
-    TRY(check_launch(m, "dec_init"));
+    StreamTable tb = stream_table(m, true);
+    SlotMem mem = slot_mem(m, S);
     const DevLayer& L0 = m->layers[0];
     NextEmbed ne{m->embed, L0.ln_a_w, L0.ln_a_b, m->x.p, m->xn.p,
                  m->precision == BOA_PREC_BF16 ? m->xn_b.p : nullptr};
-    for (uint64_t t = 0; t + 1 < maxlen; t++) {
-        m->prof_step = (t % (uint64_t)m->prof_stride) == 0;
-        // step 0 embeds the raw first bytes; later steps were embedded by the
-        // previous step's decode kernel
-        TokenSrc ts{nullptr, m->in_off.p, m->lens.p, m->tokens.p, (long long)t};
-        TRY(forward(m, ts, (int)S, 1, /*embedded=*/t > 0));
-        DecArgs a{m->logits.p, d_in, m->in_off.p, m->sizes.p, m->lens.p, d_out, m->out_off.p, m->tokens.p, m->st.p,
-                  m->trace_on ? m->trace.p : nullptr, m->trace_off.p, (long long)t, (int)S};
-        {
-            ProfScope ps(m, BOA_KC_DECODE, (double)S * 256 * 8, (double)S * (256 * 4 + 2 + 8.0 * m->d));
-            const unsigned grid = (unsigned)((S + 3) / 4);
-            switch (m->d) {
-                case 64: k_decode<2><<<grid, 128, 0, m->stream>>>(a, ne); break;
-                case 128: k_decode<4><<<grid, 128, 0, m->stream>>>(a, ne); break;
-                default: k_decode<8><<<grid, 128, 0, m->stream>>>(a, ne); break;
-            }
+    const int tb128 = 128;
+    k_dec_trivial<<<(unsigned)((n + tb128 - 1) / tb128), tb128, 0, m->stream>>>((int)n, d_in, tb, d_out);
+    TRY(check_launch(m, "dec_trivial"));
+    if (sc.S > 0) {
+        switch (m->d) {
+            case 64: launch_dec_init<2>(m, S, d_in, tb, d_out, ne); break;
+            case 128: launch_dec_init<4>(m, S, d_in, tb, d_out, ne); break;
+            default: launch_dec_init<8>(m, S, d_in, tb, d_out, ne); break;
         }
-        TRY(check_launch(m, "decode"));
+        TRY(check_launch(m, "dec_init"));
+        TokenSrc ts{nullptr, m->in_off.p, m->lens.p, m->slots.p};
+        // One decode step: every argument is fixed for the whole call (slot
+        // positions live in device memory), so without kernel profiling the
+        // step loop runs as a CUDA graph of kGraphSteps steps.
+        auto step = [&](uint64_t t) -> boa_status {
+            m->prof_step = (t % (uint64_t)m->prof_stride) == 0;
+            TRY(forward(m, ts, S, 1, /*embedded=*/true));
+            {
+                ProfScope ps(m, BOA_KC_DECODE, (double)S * 256 * 8, (double)S * (256 * 4 + 2 + 8.0 * m->d));
+                switch (m->d) {
+                    case 64: launch_decode<2>(m, S, d_in, tb, d_out, ne, mem); break;
+                    case 128: launch_decode<4>(m, S, d_in, tb, d_out, ne, mem); break;
+                    default: launch_decode<8>(m, S, d_in, tb, d_out, ne, mem); break;
+                }
+            }
+            return check_launch(m, "decode");
+        };
+        uint64_t t = 0;
+        const uint64_t kGraphSteps = 32;
+        if (!m->prof_on && m->use_graphs && steps >= 2 * kGraphSteps) {
+            // one eager step first: lazily created resources (workspace
+            // growth, kernel attributes) must not be created under capture
+            TRY(step(t++));
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            const uint64_t before = m->launches;
+            CU(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+            boa_status cs = BOA_OK;
+            for (uint64_t k = 0; k < kGraphSteps && cs == BOA_OK; k++) cs = step(k);
+            cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
+            if (cs != BOA_OK) { if (g) cudaGraphDestroy(g); return cs; }
+            if (ce != cudaSuccess) return fail(BOA_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return fail(BOA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            const uint64_t per_graph = m->launches - before;
+            m->launches = before;
+            for (; t + kGraphSteps <= steps; t += kGraphSteps) {
+                ce = cudaGraphLaunch(ge, m->stream);
+                if (ce != cudaSuccess) { cudaGraphExecDestroy(ge); return fail(BOA_ERR_CUDA, "graph launch: %s", cudaGetErrorString(ce)); }
+                m->launches += per_graph;
+            }
+            CU(cudaStreamSynchronize(m->stream));
+            cudaGraphExecDestroy(ge);
+        }
+        for (; t < steps; t++) TRY(step(t));
+        m->prof_step = true;
     }
-    m->prof_step = true;
-    k_dec_finish<<<(unsigned)((S + tb - 1) / tb), tb, 0, m->stream>>>(m->sizes.p, m->lens.p, m->st.p, m->flags.p,
-                                                                     (int)S);
-    TRY(check_launch(m, "dec_finish"));
-    TRY(m->h_u32.ensure(S));
-    CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, S * 4, cudaMemcpyDeviceToHost, m->stream));
+    TRY(m->h_u32.ensure(n));
+    CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, n * 4, cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     prof_collect(m);
     TRY(check_tc_error(m));
-    for (size_t i = 0; i < S; i++)
+    for (size_t i = 0; i < n; i++)
         if (m->h_u32.p[i]) return fail(BOA_ERR_CORRUPT, "stream %zu did not decode cleanly (flags %u)", i, m->h_u32.p[i]);
     return BOA_OK;
 }
@@ -1190,6 +1366,108 @@ extern "C" boa_status boa_profile_read(const boa_model* m, int phase, int cls, u
     return BOA_OK;
 }
 
+// ------------------------------------------------------------ training scan
+
+extern "C" boa_status boa_scan_train_fwd(size_t Bsz, size_t T, size_t E, size_t N, size_t chunk, const float* u,
+                                         const float* delta, const float* A, const float* Bm, const float* Cm,
+                                         const float* D, float* y, float* hin, void* stream) {
+    if (N != 16 || chunk == 0 || !u || !delta || !A || !Bm || !Cm || !D || !y || !hin)
+        return fail(BOA_ERR_ARG, "boa_scan_train_fwd: bad argument (d_state must be 16)");
+    if (Bsz == 0 || T == 0 || E == 0) return BOA_OK;
+    dim3 grid((unsigned)((E + kTrainThreads - 1) / kTrainThreads), (unsigned)Bsz);
+    k_scan_train_fwd<16><<<grid, kTrainThreads, 0, (cudaStream_t)stream>>>((int)T, (int)E, (int)chunk, u, delta, A, Bm,
+                                                                          Cm, D, y, hin);
+    CU(cudaGetLastError());
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_scan_train_bwd(size_t Bsz, size_t T, size_t E, size_t N, size_t chunk, const float* u,
+                                         const float* delta, const float* A, const float* Bm, const float* Cm,
+                                         const float* D, const float* dy, const float* hin, float* scratch,
+                                         float* du, float* ddelta, float* dA_part, float* dD_part, float* dB_part,
+                                         float* dC_part, void* stream) {
+    if (N != 16 || chunk == 0 || !u || !delta || !A || !Bm || !Cm || !D || !dy || !hin || !scratch || !du ||
+        !ddelta || !dA_part || !dD_part || !dB_part || !dC_part)
+        return fail(BOA_ERR_ARG, "boa_scan_train_bwd: bad argument (d_state must be 16)");
+    if (Bsz == 0 || T == 0 || E == 0) return BOA_OK;
+    dim3 grid((unsigned)((E + kTrainThreads - 1) / kTrainThreads), (unsigned)Bsz);
+    k_scan_train_bwd<16><<<grid, kTrainThreads, 0, (cudaStream_t)stream>>>((int)T, (int)E, (int)chunk, u, delta, A, Bm,
+                                                                          Cm, D, dy, hin, scratch, du, ddelta,
+                                                                          dA_part, dD_part, dB_part, dC_part);
+    CU(cudaGetLastError());
+    return BOA_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+
+extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream_len, boa_tuning* out) {
+    if (!m || n_streams == 0 || stream_len < 2) return fail(BOA_ERR_ARG, "bad argument");
+    CU(cudaSetDevice(m->device));
+    const size_t len = std::min<size_t>(stream_len, 512);   // a short sample of every stream
+    const size_t n = std::min(n_streams, m->max_slots);
+    std::vector<uint64_t> in_off(n + 1), out_off(n + 1), lens(n, len), sizes(n);
+    for (size_t i = 0; i <= n; i++) {
+        in_off[i] = i * len;
+        out_off[i] = i * boa_max_compressed_size(len);
+    }
+    DevBuf<uint8_t> din, dout, ddec;
+    TRY(din.ensure(n * len));
+    TRY(dout.ensure(out_off[n]));
+    TRY(ddec.ensure(n * len));
+    {
+        std::vector<uint8_t> h(n * len);
+        uint64_t x = 0x9E3779B97F4A7C15ull;
+        for (auto& b : h) { x = x * 6364136223846793005ull + 1442695040888963407ull; b = (uint8_t)(x >> 56); }
+        CU(cudaMemcpy(din.p, h.data(), h.size(), cudaMemcpyHostToDevice));
+    }
+    const bool prof = m->prof_on;
+    m->prof_on = false;
+    cudaEvent_t a, b;
+    CU(cudaEventCreate(&a));
+    CU(cudaEventCreate(&b));
+    auto timed = [&](auto&& fn, double& ms) -> boa_status {
+        TRY(fn());   // warm
+        CU(cudaEventRecord(a, m->stream));
+        TRY(fn());
+        CU(cudaEventRecord(b, m->stream));
+        CU(cudaEventSynchronize(b));
+        float f = 0.f;
+        CU(cudaEventElapsedTime(&f, a, b));
+        ms = f;
+        return BOA_OK;
+    };
+    boa_status st = BOA_OK;
+    boa_tuning best{m->max_rows, m->scan_group, 1e30, 1e30};
+    const size_t rows_cand[] = {1u << 16, 1u << 17, 1u << 18, 1u << 19};
+    for (size_t r : rows_cand) {
+        if (st != BOA_OK) break;
+        m->max_rows = r;
+        double ms = 0;
+        st = timed([&] { return compress_impl(m, n, din.p, in_off.data(), dout.p, out_off.data(), sizes.data()); }, ms);
+        if (st == BOA_OK && ms < best.compress_ms) { best.compress_ms = ms; best.max_rows = r; }
+    }
+    m->max_rows = best.max_rows;
+    const int g_cand[] = {1, 2, 4, 8, 16};
+    for (int g : g_cand) {
+        if (st != BOA_OK) break;
+        m->scan_group = g;
+        double ms = 0;
+        st = timed([&] { return decompress_impl(m, n, dout.p, out_off.data(), sizes.data(), lens.data(), ddec.p,
+                                                in_off.data()); }, ms);
+        if (st == BOA_OK && ms < best.decompress_ms) { best.decompress_ms = ms; best.scan_group = g; }
+    }
+    m->scan_group = best.scan_group;
+    m->prof_on = prof;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    din.release(); dout.release(); ddec.release();
+    if (st != BOA_OK) return st;
+    best.compress_ms *= (double)n_streams / n * (double)(stream_len - 1) / (len - 1);
+    best.decompress_ms *= (double)n_streams / n * (double)(stream_len - 1) / (len - 1);
+    if (out) *out = best;
+    return BOA_OK;
+}
+
 // ------------------------------------------------------------ test hooks
 
 extern "C" boa_status boa_debug_encode_cdfs(size_t n_seq, const size_t* n_syms, const uint32_t* cdfs,
@@ -1304,6 +1582,7 @@ extern "C" boa_status boa_debug_logprobs(boa_model* m, const uint8_t* stream, si
     const size_t T = len - 1;
     const int Tc = (int)std::min<size_t>(T, m->max_rows);
     TRY(ensure_workspace(m, 1, Tc));
+    TRY(ensure_streams(m, 1));
     TRY(m->d_in.ensure(len));
     DevBuf<float> lp;
     TRY(lp.ensure(T * 256));
@@ -1313,10 +1592,12 @@ extern "C" boa_status boa_debug_logprobs(boa_model* m, const uint8_t* stream, si
     boa_status st = BOA_OK;
     cudaError_t e = cudaMemcpyAsync(m->d_in.p, stream, len, cudaMemcpyHostToDevice, m->stream);
     if (e != cudaSuccess) st = fail(BOA_ERR_CUDA, "%s", cudaGetErrorString(e));
+    TokenSrc ts{m->d_in.p, m->in_off.p, m->lens.p, m->slots.p};
     for (size_t t0 = 0; st == BOA_OK && t0 < T; t0 += Tc) {
         const int tc = (int)std::min<size_t>(Tc, T - t0);
-        TokenSrc ts{m->d_in.p, m->in_off.p, m->lens.p, nullptr, (long long)t0};
-        st = forward(m, ts, 1, tc);
+        k_set_slot<<<1, 1, 0, m->stream>>>(m->slots.p, 0, (long long)t0);
+        st = check_launch(m, "set_slot");
+        if (st == BOA_OK) st = forward(m, ts, 1, tc);
         if (st == BOA_OK) {
             k_log2_softmax<<<(unsigned)((tc + 7) / 8), 256, 0, m->stream>>>(m->logits.p, lp.p + t0 * 256, tc);
             st = check_launch(m, "log2_softmax");
@@ -1572,5 +1853,131 @@ extern "C" boa_status boa_decode_cdfs_static(size_t n_seq, const size_t* n_syms,
     CU(cudaMemcpyAsync(&h_or, flag_or, 4, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     if (h_or) return fail(BOA_ERR_CORRUPT, "a sequence did not decode cleanly (flags %u)", h_or);
+    return BOA_OK;
+}
+
+// ------------------------------------------------------------ .boa container
+//
+// Layout (little-endian), after the paper's container description (section
+// "Coders & Parallelisation"):
+//   0  "BOA1"                      magic
+//   4  u32 version (1)
+//   8  u64 model fingerprint
+//  16  u64 total uncompressed length
+//  24  u64 nominal chunk length
+//  32  u64 number of chunks n
+//  40  u64 length of the last chunk
+//  48  u32 CRC-32 of bytes 0..47
+//  52  u32 CRC-32 of the index
+//  56  index: n x (u64 payload offset, u64 compressed size)
+//  56 + 16 n  payload: each chunk's bytes (raw first byte + coded bytes)
+
+static const uint32_t kBoaVersion = 1;
+static const size_t kHeaderBytes = 56;
+
+// CRC-32 with the IEEE 802.3 polynomial (reflected 0xEDB88320, initial and
+// final XOR 0xFFFFFFFF), bitwise.
+extern "C" uint32_t boa_crc32(const uint8_t* p, size_t n) {
+    uint32_t c = 0xFFFFFFFFu;
+    for (size_t i = 0; i < n; i++) {
+        c ^= p[i];
+        for (int k = 0; k < 8; k++) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+    }
+    return c ^ 0xFFFFFFFFu;
+}
+
+static void put64(uint8_t* p, uint64_t v) { for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+static void put32(uint8_t* p, uint32_t v) { for (int i = 0; i < 4; i++) p[i] = (uint8_t)(v >> (8 * i)); }
+static uint64_t get64(const uint8_t* p) { uint64_t v = 0; for (int i = 7; i >= 0; i--) v = (v << 8) | p[i]; return v; }
+static uint32_t get32(const uint8_t* p) { uint32_t v = 0; for (int i = 3; i >= 0; i--) v = (v << 8) | p[i]; return v; }
+
+extern "C" size_t boa_pack_bound(size_t len, size_t chunk_len) {
+    if (chunk_len == 0) return 0;
+    const size_t n = (len + chunk_len - 1) / chunk_len;
+    size_t b = kHeaderBytes + 16 * n;
+    for (size_t i = 0; i < n; i++) b += boa_max_compressed_size(std::min(chunk_len, len - i * chunk_len));
+    return b;
+}
+
+extern "C" boa_status boa_pack(boa_model* m, const uint8_t* data, size_t len, size_t chunk_len, uint8_t* out,
+                               size_t cap, size_t* out_size) {
+    if (!m || (len && !data) || !out || !out_size || chunk_len == 0) return fail(BOA_ERR_ARG, "bad argument");
+    if (cap < boa_pack_bound(len, chunk_len)) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "capacity below boa_pack_bound");
+    const size_t n = (len + chunk_len - 1) / chunk_len;
+    std::vector<const uint8_t*> ptrs(n);
+    std::vector<size_t> lens(n), caps(n), sizes(n);
+    std::vector<uint8_t*> outs(n);
+    // chunks are compressed straight into the payload area at worst-case
+    // offsets, then packed down
+    size_t at = kHeaderBytes + 16 * n;
+    std::vector<size_t> slot(n);
+    for (size_t i = 0; i < n; i++) {
+        ptrs[i] = data + i * chunk_len;
+        lens[i] = std::min(chunk_len, len - i * chunk_len);
+        caps[i] = boa_max_compressed_size(lens[i]);
+        slot[i] = at;
+        outs[i] = out + at;
+        at += caps[i];
+    }
+    if (n) TRY(boa_compress(m, n, ptrs.data(), lens.data(), outs.data(), caps.data(), sizes.data()));
+    uint8_t* idx = out + kHeaderBytes;
+    size_t pay = 0, w = kHeaderBytes + 16 * n;
+    for (size_t i = 0; i < n; i++) {
+        if (w != slot[i]) memmove(out + w, out + slot[i], sizes[i]);
+        put64(idx + 16 * i, pay);
+        put64(idx + 16 * i + 8, sizes[i]);
+        w += sizes[i];
+        pay += sizes[i];
+    }
+    memcpy(out, "BOA1", 4);
+    put32(out + 4, kBoaVersion);
+    put64(out + 8, m->fingerprint);
+    put64(out + 16, len);
+    put64(out + 24, chunk_len);
+    put64(out + 32, n);
+    put64(out + 40, n ? lens[n - 1] : 0);
+    put32(out + 48, boa_crc32(out, 48));
+    put32(out + 52, boa_crc32(idx, 16 * n));
+    *out_size = w;
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_unpack_info(const uint8_t* c, size_t size, uint64_t* total_len, uint64_t* fingerprint) {
+    if (!c || size < kHeaderBytes) return fail(BOA_ERR_CORRUPT, "container shorter than its header");
+    if (memcmp(c, "BOA1", 4) != 0 || get32(c + 4) != kBoaVersion) return fail(BOA_ERR_FORMAT, "not a .boa container");
+    if (get32(c + 48) != boa_crc32(c, 48)) return fail(BOA_ERR_CORRUPT, "header CRC mismatch");
+    if (total_len) *total_len = get64(c + 16);
+    if (fingerprint) *fingerprint = get64(c + 8);
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_unpack(boa_model* m, const uint8_t* c, size_t size, uint8_t* out, size_t cap,
+                                 size_t* out_len) {
+    if (!m || !out_len || (cap && !out)) return fail(BOA_ERR_ARG, "bad argument");
+    uint64_t total = 0, fp = 0;
+    TRY(boa_unpack_info(c, size, &total, &fp));
+    if (fp != m->fingerprint) return fail(BOA_ERR_FINGERPRINT, "container was written with a different model");
+    const uint64_t chunk = get64(c + 24), n = get64(c + 32), last = get64(c + 40);
+    if (chunk == 0 || n != (total + chunk - 1) / chunk || (n && last != total - (n - 1) * chunk))
+        return fail(BOA_ERR_CORRUPT, "inconsistent chunk layout");
+    if (n > (size - kHeaderBytes) / 16) return fail(BOA_ERR_CORRUPT, "index runs past the container");
+    const uint8_t* idx = c + kHeaderBytes;
+    if (get32(c + 52) != boa_crc32(idx, 16 * n)) return fail(BOA_ERR_CORRUPT, "index CRC mismatch");
+    if (cap < total) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "output needs %llu bytes", (unsigned long long)total);
+    const uint8_t* pay = idx + 16 * n;
+    const size_t pay_size = size - kHeaderBytes - 16 * n;
+    std::vector<const uint8_t*> ptrs(n);
+    std::vector<size_t> sizes(n), lens(n);
+    std::vector<uint8_t*> outs(n);
+    for (uint64_t i = 0; i < n; i++) {
+        const uint64_t o = get64(idx + 16 * i), z = get64(idx + 16 * i + 8);
+        if (o > pay_size || z > pay_size - o) return fail(BOA_ERR_CORRUPT, "chunk %llu lies outside the payload", (unsigned long long)i);
+        ptrs[i] = pay + o;
+        sizes[i] = z;
+        lens[i] = i + 1 < n ? chunk : last;
+        outs[i] = out + i * chunk;
+    }
+    if (n) TRY(boa_decompress(m, n, ptrs.data(), sizes.data(), lens.data(), outs.data()));
+    *out_len = total;
     return BOA_OK;
 }

@@ -40,20 +40,29 @@ __device__ __forceinline__ void warp_layernorm(const float (&x)[VPT], const floa
     }
 }
 
-// Token source for a row: compression reads the stream bytes, decompression
-// the token array holding each stream's last decoded byte.
+// Streams run in a fixed pool of slots (row block s of every launch belongs
+// to slot s).  A slot works through its own list of streams, one after the
+// other; t is the position in the current stream: the first step of the
+// current chunk when compressing, the step being decoded when decompressing.
+struct SlotState {
+    int idx;        // index into the schedule (the slot's current list entry)
+    int stream;     // current stream, -1 once the slot's list is exhausted
+    long long t;
+};
+
+// Token source for a compression row (slot s, step tau of the chunk).
 struct TokenSrc {
-    const uint8_t* data;      // packed stream bytes (compression) or nullptr
-    const uint64_t* offsets;  // [S+1]
-    const uint64_t* lens;     // [S]
-    const uint8_t* tokens;    // [S] (decompression)
-    long long t0;             // first step of the chunk
+    const uint8_t* data;        // packed stream bytes
+    const uint64_t* offsets;    // [n+1]
+    const uint64_t* lens;       // [n]
+    const SlotState* slots;     // [S]
 };
 
 __device__ __forceinline__ int row_token(const TokenSrc& ts, int s, int tau) {
-    if (ts.tokens) return ts.tokens[s];
-    long long t = ts.t0 + tau;
-    return (t + 1 < (long long)ts.lens[s]) ? ts.data[ts.offsets[s] + t] : 0;
+    const SlotState ss = ts.slots[s];
+    if (ss.stream < 0) return 0;
+    const long long t = ss.t + tau;
+    return (t + 1 < (long long)ts.lens[ss.stream]) ? ts.data[ts.offsets[ss.stream] + t] : 0;
 }
 
 // x = embed[token]; xn = LN_a(x)   (Alg. 1: ByteEmbed, then the first block's norm)
@@ -442,65 +451,126 @@ __device__ __forceinline__ void warp_find_symbol(const uint32_t (&f)[8], uint32_
 
 // ------------------------------------------------------- coder kernels
 
-struct EncArgs {
-    const float* logits;        // [S*Tc][256]
-    const uint8_t* data;        // packed input
-    const uint64_t* in_off;     // [S+1]
-    const uint64_t* lens;       // [S]
-    uint8_t* out;               // packed output
-    const uint64_t* out_off;    // [S+1]
-    CoderState* st;             // [S]
-    uint64_t* trace;            // [sum(len-1)] or nullptr
-    const uint64_t* trace_off;  // [S]
-    long long t0;
-    int S, Tc;
+// Per-stream bookkeeping shared by the slot kernels.
+struct StreamTable {
+    const uint64_t* in_off;     // [n+1] input slots (raw bytes, or coded bytes when decoding)
+    const uint64_t* in_size;    // [n] coded bytes per input slot (decoding) or nullptr
+    const uint64_t* lens;       // [n] uncompressed lengths
+    const uint64_t* out_off;    // [n+1] output slots
+    uint64_t* sizes;            // [n] compressed sizes (encoding)
+    uint32_t* flags;            // [n] per-stream status bits
+    uint64_t* trace;            // per-step CDF hashes or nullptr
+    const uint64_t* trace_off;  // [n]
 };
 
-// One warp per stream: for every step of the chunk, softmax -> histogram ->
-// encode the true next byte (paper "Encoder"; first byte stored raw).
-__global__ void k_encode(EncArgs a) {
+// Carried model state of one slot: SSM state [L][S][N][E] and conv window
+// [L][S][K-1][E] (the slot's part of each layer is contiguous).
+struct SlotMem {
+    float* h;
+    float* conv;
+    int layers, S, h_per, conv_per;   // floats per (layer, slot)
+};
+
+__device__ __forceinline__ void warp_zero_slot(const SlotMem& sm, int s, int lane) {
+    for (int l = 0; l < sm.layers; l++) {
+        float* hp = sm.h + ((size_t)l * sm.S + s) * sm.h_per;
+        for (int i = lane; i < sm.h_per; i += 32) hp[i] = 0.f;
+        float* cp = sm.conv + ((size_t)l * sm.S + s) * sm.conv_per;
+        for (int i = lane; i < sm.conv_per; i += 32) cp[i] = 0.f;
+    }
+}
+
+// Streams of length 0 or 1 never enter a slot: 0 bytes, or the raw byte.
+__global__ void k_enc_trivial(int n, const uint8_t* __restrict__ data, StreamTable tb, uint8_t* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t len = tb.lens[i];
+    if (len == 0) tb.sizes[i] = 0;
+    if (len == 1) {
+        out[tb.out_off[i]] = data[tb.in_off[i]];
+        tb.sizes[i] = 1;
+    }
+}
+
+// Slot bookkeeping between compression chunks, one warp per slot.  init:
+// take the first stream of the slot's list.  Otherwise advance the chunk
+// start by tc; a stream whose last step is done is flushed (4 bytes of L,
+// paper "Encoder"; its size recorded) and the slot moves to its next stream:
+// coder reset, raw first byte written, model state zeroed.
+__global__ void k_enc_slots(int S, int init, long long tc, const int* __restrict__ sched,
+                            const int* __restrict__ slot_beg, SlotState* slots, CoderState* st,
+                            const uint8_t* __restrict__ data, StreamTable tb, uint8_t* __restrict__ out, SlotMem mem) {
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (s >= a.S) return;
-    const long long len = (long long)a.lens[s];
-    if (len < 2) return;
-    CoderState st;
-    if (lane == 0) st = a.st[s];
-    uint8_t* out = a.out + a.out_off[s] + 1;
-    const uint64_t cap = a.out_off[s + 1] - a.out_off[s] - 1;
-    const uint8_t* in = a.data + a.in_off[s];
-    for (int tau = 0; tau < a.Tc; tau++) {
-        const long long t = a.t0 + tau;
+    if (s >= S) return;
+    SlotState ss = slots[s];
+    bool start = false;
+    if (init) {
+        ss.idx = slot_beg[s];
+        start = true;
+    } else if (ss.stream >= 0) {
+        ss.t += tc;
+        if (ss.t + 1 >= (long long)tb.lens[ss.stream]) {
+            if (lane == 0) {
+                CoderState c = st[s];
+                const uint64_t o = tb.out_off[ss.stream];
+                const uint64_t cap = tb.out_off[ss.stream + 1] - o - 1;
+                rc_flush(c, out + o + 1, cap);
+                tb.sizes[ss.stream] = 1 + c.pos;
+                tb.flags[ss.stream] = c.flags;
+            }
+            ss.idx++;
+            start = true;
+        }
+    }
+    if (start) {
+        ss.stream = ss.idx < slot_beg[s + 1] ? sched[ss.idx] : -1;
+        ss.t = 0;
+        if (ss.stream >= 0) {
+            if (lane == 0) {
+                CoderState c;
+                c.L = 0; c.R = 1ull << 32; c.C = 0; c.pos = 0; c.flags = 0; c.pad = 0;
+                st[s] = c;
+                out[tb.out_off[ss.stream]] = data[tb.in_off[ss.stream]];
+            }
+            if (!init) warp_zero_slot(mem, s, lane);
+        }
+    }
+    if (lane == 0) slots[s] = ss;
+}
+
+// One warp per slot: for every step of the chunk, softmax -> histogram ->
+// encode the true next byte of the slot's current stream (paper "Encoder").
+__global__ void k_encode(const float* __restrict__ logits, int S, int Tc, const SlotState* __restrict__ slots,
+                         CoderState* st, const uint8_t* __restrict__ data, StreamTable tb, uint8_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (s >= S) return;
+    const SlotState ss = slots[s];
+    if (ss.stream < 0) return;
+    const long long len = (long long)tb.lens[ss.stream];
+    CoderState c;
+    if (lane == 0) c = st[s];
+    const uint64_t o = tb.out_off[ss.stream];
+    uint8_t* op = out + o + 1;
+    const uint64_t cap = tb.out_off[ss.stream + 1] - o - 1;
+    const uint8_t* in = data + tb.in_off[ss.stream];
+    for (int tau = 0; tau < Tc; tau++) {
+        const long long t = ss.t + tau;
         if (t + 1 >= len) break;
         uint32_t f[8], cbase;
-        warp_logits_to_hist(a.logits + ((size_t)s * a.Tc + tau) * 256, lane, f, cbase);
-        if (a.trace) {
-            uint64_t hsh = warp_hist_hash(f, lane);
-            if (lane == 0) a.trace[a.trace_off[s] + t] = hsh;
+        warp_logits_to_hist(logits + ((size_t)s * Tc + tau) * 256, lane, f, cbase);
+        if (tb.trace) {
+            const uint64_t hsh = warp_hist_hash(f, lane);
+            if (lane == 0) tb.trace[tb.trace_off[ss.stream] + t] = hsh;
         }
         const int sym = in[t + 1];
         uint32_t c_lo, freq;
         warp_sym_range(f, cbase, sym, lane, c_lo, freq);
-        if (lane == 0) rc_encode(st, c_lo, freq, out, cap);
+        if (lane == 0) rc_encode(c, c_lo, freq, op, cap);
     }
-    if (lane == 0) a.st[s] = st;
+    if (lane == 0) st[s] = c;
 }
-
-struct DecArgs {
-    const float* logits;        // [S][256]
-    const uint8_t* cin;         // packed coded input
-    const uint64_t* cin_off;    // [S+1] slot offsets
-    const uint64_t* cin_size;   // [S] coded bytes at the start of each slot
-    const uint64_t* lens;       // [S] decoded lengths
-    uint8_t* out;               // packed output
-    const uint64_t* out_off;    // [S+1]
-    uint8_t* tokens;            // [S] next-step input byte
-    CoderState* st;
-    uint64_t* trace;
-    const uint64_t* trace_off;
-    long long t;                // step: this call decodes byte t+1
-    int S;
-};
 
 // Embedding + first-block LayerNorm of one token by one warp (the same
 // arithmetic as k_embed_ln), used to prepare the next decode step.
@@ -528,111 +598,111 @@ __device__ __forceinline__ void warp_embed_ln(const NextEmbed& ne, int tok, size
     }
 }
 
-// One warp per stream, one step: softmax -> histogram -> decode byte t+1,
-// and prepare the next step's input rows (embedding + first LayerNorm of the
-// decoded byte); finished streams are masked.
+// Decoder start for the stream now in slot s: raw first byte to the output,
+// code value from the first 4 coded bytes, next-step input rows prepared.
 template <int VPT>
-__global__ void k_decode(DecArgs a, NextEmbed ne) {
+__device__ __forceinline__ void warp_dec_start(int s, int stream, const uint8_t* __restrict__ cin, const StreamTable& tb,
+                                               uint8_t* __restrict__ out, CoderState* st, const NextEmbed& ne,
+                                               int lane) {
+    const uint64_t size = tb.in_size[stream];
+    const uint8_t first = cin[tb.in_off[stream]];   // size >= 1 (checked on the host)
+    if (lane == 0) {
+        CoderState c;
+        rc_decoder_init(c, cin + tb.in_off[stream] + 1, size - 1);
+        st[s] = c;
+        out[tb.out_off[stream]] = first;
+    }
+    warp_embed_ln<VPT>(ne, first, (size_t)s, lane);
+}
+
+// Point slot 0 at (stream, t): the teacher-forced log-probability pass.
+__global__ void k_set_slot(SlotState* slots, int stream, long long t) {
+    SlotState ss;
+    ss.idx = 0; ss.stream = stream; ss.t = t;
+    slots[0] = ss;
+}
+
+__global__ void k_dec_trivial(int n, const uint8_t* __restrict__ cin, StreamTable tb, uint8_t* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t len = tb.lens[i], size = tb.in_size[i];
+    if (len == 0) tb.flags[i] = size == 0 ? 0u : (uint32_t)kFlagCorrupt;
+    if (len == 1) {
+        if (size >= 1) out[tb.out_off[i]] = cin[tb.in_off[i]];
+        tb.flags[i] = size == 1 ? 0u : (uint32_t)kFlagCorrupt;
+    }
+}
+
+template <int VPT>
+__global__ void k_dec_slots_init(int S, const int* __restrict__ sched, const int* __restrict__ slot_beg,
+                                 SlotState* slots, CoderState* st, const uint8_t* __restrict__ cin, StreamTable tb,
+                                 uint8_t* __restrict__ out, NextEmbed ne) {
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (s >= a.S) return;
-    const long long len = (long long)a.lens[s];
-    if (a.t + 1 >= len) return;
+    if (s >= S) return;
+    SlotState ss;
+    ss.idx = slot_beg[s];
+    ss.stream = ss.idx < slot_beg[s + 1] ? sched[ss.idx] : -1;
+    ss.t = 0;
+    if (ss.stream >= 0) warp_dec_start<VPT>(s, ss.stream, cin, tb, out, st, ne, lane);
+    if (lane == 0) slots[s] = ss;
+}
+
+// One warp per slot, one step: softmax -> histogram -> decode byte t+1 of the
+// slot's stream (paper "Decoder"), then prepare the next step's input rows.
+// A completed stream is checked (every coded byte consumed) and the slot
+// moves to its next stream with zeroed model state; slots whose lists are
+// exhausted are masked.
+template <int VPT>
+__global__ void k_decode(const float* __restrict__ logits, int S, const int* __restrict__ sched,
+                         const int* __restrict__ slot_beg, SlotState* slots, CoderState* st,
+                         const uint8_t* __restrict__ cin, StreamTable tb, uint8_t* __restrict__ out, NextEmbed ne,
+                         SlotMem mem) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (s >= S) return;
+    SlotState ss = slots[s];
+    if (ss.stream < 0) return;
+    const int stream = ss.stream;
+    const long long len = (long long)tb.lens[stream];
+    const long long t = ss.t;
     uint32_t f[8], cbase;
-    warp_logits_to_hist(a.logits + (size_t)s * 256, lane, f, cbase);
-    if (a.trace) {
-        uint64_t hsh = warp_hist_hash(f, lane);
-        if (lane == 0) a.trace[a.trace_off[s] + a.t] = hsh;
+    warp_logits_to_hist(logits + (size_t)s * 256, lane, f, cbase);
+    if (tb.trace) {
+        const uint64_t hsh = warp_hist_hash(f, lane);
+        if (lane == 0) tb.trace[tb.trace_off[stream] + t] = hsh;
     }
-    const uint8_t* in = a.cin + a.cin_off[s] + 1;
-    const uint64_t size = a.cin_size[s] - 1;
-    CoderState st;
+    const uint8_t* in = cin + tb.in_off[stream] + 1;
+    const uint64_t size = tb.in_size[stream] - 1;
+    CoderState c;
     uint32_t x = 0;
     if (lane == 0) {
-        st = a.st[s];
-        x = rc_target(st);
+        c = st[s];
+        x = rc_target(c);
     }
     x = __shfl_sync(0xffffffffu, x, 0);
     int sym;
     uint32_t c_lo, freq;
     warp_find_symbol(f, cbase, x, lane, sym, c_lo, freq);
     if (lane == 0) {
-        rc_decode_update(st, c_lo, freq, in, size);
-        a.st[s] = st;
-        a.out[a.out_off[s] + a.t + 1] = (uint8_t)sym;
-        a.tokens[s] = (uint8_t)sym;
+        rc_decode_update(c, c_lo, freq, in, size);
+        st[s] = c;
+        out[tb.out_off[stream] + t + 1] = (uint8_t)sym;
     }
-    if (a.t + 2 < len) warp_embed_ln<VPT>(ne, sym, (size_t)s, lane);
-}
-
-// Coder set-up: encoder state, raw first byte copied through.
-__global__ void k_enc_init(const uint8_t* data, const uint64_t* in_off, const uint64_t* lens, uint8_t* out,
-                           const uint64_t* out_off, CoderState* st, int S) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    CoderState c;
-    c.L = 0; c.R = 1ull << 32; c.C = 0; c.pos = 0; c.flags = 0; c.pad = 0;
-    if (lens[s] >= 1) {
-        if (out_off[s + 1] > out_off[s]) out[out_off[s]] = data[in_off[s]];
-        else c.flags |= kFlagOverflow;
-    }
-    st[s] = c;
-}
-
-__global__ void k_enc_finish(const uint64_t* lens, uint8_t* out, const uint64_t* out_off, CoderState* st,
-                             uint64_t* sizes, int S) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    CoderState c = st[s];
-    uint64_t size = lens[s] == 0 ? 0 : 1;
-    if (lens[s] >= 2) {
-        uint64_t cap = out_off[s + 1] - out_off[s] - 1;
-        rc_flush(c, out + out_off[s] + 1, cap);
-        size = 1 + c.pos;
-    }
-    st[s] = c;
-    sizes[s] = size;
-}
-
-// Decoder set-up: raw first byte to output and token; code value from the
-// first 4 coded bytes.
-__global__ void k_dec_init(const uint8_t* cin, const uint64_t* cin_off, const uint64_t* cin_size,
-                           const uint64_t* lens, uint8_t* out, const uint64_t* out_off, uint8_t* tokens,
-                           CoderState* st, int S) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    CoderState c;
-    c.L = 0; c.R = 1ull << 32; c.C = 0; c.pos = 0; c.flags = 0; c.pad = 0;
-    const uint64_t size = cin_size[s];
-    tokens[s] = 0;
-    if (lens[s] >= 1) {
-        if (size >= 1) {
-            out[out_off[s]] = cin[cin_off[s]];
-            tokens[s] = cin[cin_off[s]];
-        } else {
-            c.flags |= kFlagCorrupt;
+    if (t + 2 < len) {
+        ss.t = t + 1;
+        warp_embed_ln<VPT>(ne, sym, (size_t)s, lane);
+    } else {
+        if (lane == 0) tb.flags[stream] = c.flags | (c.pos != size ? (uint32_t)kFlagCorrupt : 0u);
+        ss.idx++;
+        ss.stream = ss.idx < slot_beg[s + 1] ? sched[ss.idx] : -1;
+        ss.t = 0;
+        if (ss.stream >= 0) {
+            warp_zero_slot(mem, s, lane);
+            warp_dec_start<VPT>(s, ss.stream, cin, tb, out, st, ne, lane);
         }
     }
-    if (lens[s] >= 2) {
-        rc_decoder_init(c, cin + cin_off[s] + 1, size >= 1 ? size - 1 : 0);
-    } else if (size != (lens[s] == 0 ? 0u : 1u)) {
-        c.flags |= kFlagCorrupt;
-    }
-    st[s] = c;
-}
-
-// Decoder wrap-up: every coded byte must have been consumed exactly.
-__global__ void k_dec_finish(const uint64_t* cin_size, const uint64_t* lens, CoderState* st, uint32_t* flags_out,
-                             int S) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    CoderState c = st[s];
-    uint32_t fl = c.flags;
-    if (lens[s] >= 2) {
-        const uint64_t size = cin_size[s];
-        if (c.pos != size - 1) fl |= kFlagCorrupt;
-    }
-    flags_out[s] = fl;
+    if (lane == 0) slots[s] = ss;
 }
 
 __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, size_t n) {

@@ -60,3 +60,32 @@ def test_product_path_does_not_import_oracle():
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 assert not pat.search(open(os.path.join(dirpath, f)).read()), f
+
+
+def test_container_checksum_is_crc32():
+    """The container checksum is CRC-32 (IEEE 802.3): check value of
+    "123456789" is 0xCBF43926, and it agrees with zlib on random data."""
+    import zlib
+
+    import numpy as np
+
+    from paper_2511_11337_b300 import api
+    assert api.crc32(b"123456789") == 0xCBF43926
+    assert api.crc32(b"") == 0
+    data = np.random.default_rng(0).integers(0, 256, 10007, dtype=np.uint8).tobytes()
+    assert api.crc32(data) == zlib.crc32(data)
+
+
+def test_container_header_checks_without_gpu():
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_2511_11337_b300 import _lib
+    lib = _lib.load()
+    assert lib.boa_pack_bound(0, 16) == 56
+    assert lib.boa_pack_bound(33, 16) == 56 + 3 * 16 + 2 * (1 + 5 * 15 + 4) + 1
+    junk = np.zeros(100, np.uint8)
+    t, f = C.c_uint64(), C.c_uint64()
+    assert lib.boa_unpack_info(junk.ctypes.data_as(C.c_void_p), 100, C.byref(t), C.byref(f)) == 3
+    assert lib.boa_unpack_info(junk.ctypes.data_as(C.c_void_p), 10, C.byref(t), C.byref(f)) == 7

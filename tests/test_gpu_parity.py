@@ -238,3 +238,50 @@ def test_paper_scale_full_size(api, paper_model_path):
         assert m.compress([streams[i]])[0] == comp[i]
     lp = m.logprobs(streams[1234][:300])
     assert np.abs(lp - om.logprobs(streams[1234][:300])).max() <= LOG2P_TOL
+
+
+# --------------------------------------------- uneven lengths, slot queueing
+
+def test_more_streams_than_slots_is_byte_identical(api, tiny_model_path):
+    """Streams queue for a small pool of slots; each slot resets its model
+    state between streams.  A stream's bytes do not depend on the slot count
+    or on which streams share its slot."""
+    g = np.random.default_rng(12)
+    lens = [int(x) for x in g.integers(0, 1500, 37)] + [0, 1, 2, 3, 2048]
+    streams = [synth.records_stream(700 + i, n) if n else b"" for i, n in enumerate(lens)]
+    ref = api.Model(tiny_model_path).compress(streams)
+    for slots in (1, 3, 7, 64):
+        m = api.Model(tiny_model_path, max_slots=slots)
+        comp = m.compress(streams)
+        assert comp == ref, slots
+        assert m.decompress(comp, lens) == streams
+    m = api.Model(tiny_model_path, max_slots=5)
+    n_steps = sum(max(n - 1, 0) for n in lens)
+    m.enable_cdf_trace(True)
+    try:
+        comp = m.compress(streams)
+        enc = m.read_cdf_trace(n_steps)
+        m.decompress(comp, lens)
+        dec = m.read_cdf_trace(n_steps)
+    finally:
+        m.enable_cdf_trace(False)
+    assert np.array_equal(enc, dec)
+
+
+def test_mixed_uneven_workload(api, model_dir):
+    """A scaled-down uneven mix: 160 ATLAS-like / CMS-like streams with
+    log-uniform lengths 64 B - 16 KB through 48 slots on the benchmark's
+    model; lossless, and sampled streams within 0.5 % of the oracle."""
+    path = os.path.join(model_dir, "paper.boaw")
+    if not os.path.exists(path):
+        synth.make_model_file(path, synth.PAPER_SCALE, seed=2)
+    streams = synth.mixed_workload(160, seed=3001, lo_log2=6, hi_log2=14)
+    lens = [len(s) for s in streams]
+    m = api.Model(path, max_slots=48)
+    comp = m.compress(streams)
+    assert m.decompress(comp, lens) == streams
+    om = O.Model(path)
+    short = [i for i, n in enumerate(lens) if 300 < n < 1500][:3]
+    ref = om.compress_batch([streams[i] for i in short])
+    got = sum(len(comp[i]) for i in short)
+    assert abs(got - sum(map(len, ref))) / sum(map(len, ref)) <= GAP_TOL

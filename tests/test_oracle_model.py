@@ -237,3 +237,29 @@ def test_logprobs_match_steps(tiny_model_path):
     ref = np.array([O.log2_softmax(l) for l in _oracle_logits(tiny_model_path, data)])
     assert np.array_equal(lp, ref)
     assert np.allclose(np.exp2(lp).sum(1), 1.0, rtol=0, atol=1e-12)
+
+
+def test_scan_gradient_matches_central_differences():
+    """The oracle's reverse-mode scan gradient against central finite
+    differences of the oracle's forward scan, for every input element."""
+    g = np.random.default_rng(21)
+    T, E, N = 7, 3, 2
+    ins = {"u": g.normal(size=(T, E)), "delta": np.log1p(np.exp(g.normal(size=(T, E)))),
+           "A": -np.exp(g.normal(size=(E, N))), "B": g.normal(size=(T, N)), "C": g.normal(size=(T, N)),
+           "D": g.normal(size=E)}
+    dy = g.normal(size=(T, E))
+    grad = O.selective_scan_grad(ins["u"], ins["delta"], ins["A"], ins["B"], ins["C"], ins["D"], dy)
+
+    def loss(v):
+        y = O.selective_scan(v["u"], v["delta"], v["A"], v["B"], v["C"], v["D"])
+        return float((dy * y).sum())
+
+    h = 1e-6
+    for name, arr in ins.items():
+        for idx in np.ndindex(arr.shape):
+            plus = {k: a.copy() for k, a in ins.items()}
+            minus = {k: a.copy() for k, a in ins.items()}
+            plus[name][idx] += h
+            minus[name][idx] -= h
+            fd = (loss(plus) - loss(minus)) / (2 * h)
+            assert abs(fd - grad[name][idx]) <= 1e-6 * (1 + abs(fd)), (name, idx, fd, grad[name][idx])
