@@ -4,10 +4,16 @@
 Workload: a 64 MiB synthetic ATLAS-like jet table (row-major 5 x f32 rows,
 Poisson(6) jets per event) cut into 4096 streams of 16 KB, compressed and
 decompressed with a random-init Mamba predictor (d_model 256, 3 layers,
-d_state 16, expand 2), FP32 throughout.  One step = compress all streams +
-decompress all streams (the whole hot path); value = uncompressed MB
-(10^6 bytes) / step time, inputs resident in HBM.  The L2 is flushed (a
-256 MiB write) before every timed step.
+d_state 16, expand 2).  One step = compress all streams + decompress all
+streams (the whole hot path); value = uncompressed MB (10^6 bytes) / step
+time, inputs resident in HBM.  The L2 is flushed (a 256 MiB write) before
+every timed step.
+
+The headline form computes the projections with FP32 accuracy on the tensor
+cores (3xTF32 split; everything else FP32), held to the same log-probability
+bound as the plain FP32 CUDA-core form.  The other forms (plain FP32, BF16,
+FP8) are reported beside it with their own accuracy against the oracle.
+`--report precision` runs the 4 MB records subset through every form.
 
 `--impl reference` times the FP64 CPU oracle on the host cores instead (a
 bounded sample of the same workload per step).
@@ -34,8 +40,9 @@ from paper_2511_11337_b300 import synth  # noqa: E402
 METRIC = "compress & decompress MB/s on 1 B300 at <=0.5% code-length gap vs FP64 oracle"
 UNIT = "MB/s"
 N_STREAMS, STREAM_LEN = 4096, 16384
-WORKLOAD = "ATLAS-like jet table, 64 MiB as 4096 x 16 KB streams; Mamba d_model=256, 3 layers, d_state=16, expand=2 (1.45 M params), FP32"
+WORKLOAD = "ATLAS-like jet table, 64 MiB as 4096 x 16 KB streams; Mamba d_model=256, 3 layers, d_state=16, expand=2 (1.45 M params)"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+PREC = {"fp32": 0, "bf16": 1, "tf32x3": 2, "fp8": 3}
 
 
 def env_rank():
@@ -163,6 +170,95 @@ def run_reference(args):
     }))
 
 
+# ---------------------------------------------------------------- precision forms
+
+FORM_DESC = {"fp32": "plain FP32 on the CUDA cores", "tf32x3": "FP32-accurate 3xTF32 on the tensor cores",
+             "bf16": "BF16 projections on the tensor cores", "fp8": "FP8 E4M3 projections on the tensor cores"}
+
+
+def form_accuracy(streams, forms, path, n_lp=4, lp_len=256, n_gap=16, gap_len=2048):
+    """Against the FP64 oracle: max |d log2 p| over the first lp_len bytes of
+    n_lp streams, and the code-length gap over gap_len-byte prefixes of n_gap
+    streams (oracle on the host cores, one thread per stream)."""
+    from oracle import oracle as O
+    from paper_2511_11337_b300 import api
+    om = O.Model(path)
+    lp_ref = [om.logprobs(s[:lp_len]) for s in streams[:n_lp]]
+    gap_in = [s[:gap_len] for s in streams[:n_gap]]
+    ref_total = sum(map(len, om.compress_batch(gap_in, n_threads=min(len(gap_in), os.cpu_count() or 1))))
+    out = {}
+    for f in forms:
+        m = api.Model(path, precision=PREC[f])
+        err = max(float(np.abs(m.logprobs(s[:lp_len]) - r).max()) for s, r in zip(streams[:n_lp], lp_ref))
+        got = sum(map(len, m.compress(gap_in)))
+        m.close()
+        out[f] = {"form": FORM_DESC[f], "max_abs_dlog2p": err, "code_length_gap": (got - ref_total) / ref_total,
+                  "accuracy_sample": f"log2 p: first {lp_len} B of {n_lp} streams; gap: first {gap_len} B of {n_gap} streams"}
+    return out
+
+
+def form_speed(form, path, d_in, in_off, d_out, out_off, d_dec, lens, stream):
+    """One warm-up and one timed step of another precision form."""
+    import torch
+    from paper_2511_11337_b300 import api
+    m = api.Model(path, cuda_stream=stream.cuda_stream, precision=PREC[form])
+    total = int(in_off[-1])
+    res = {}
+    for k in range(2):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        a.record(stream)
+        sizes = m.compress_device(d_in.data_ptr(), in_off, d_out.data_ptr(), out_off)
+        b.record(stream)
+        m.decompress_device(d_out.data_ptr(), out_off, lens, d_dec.data_ptr(), in_off, in_sizes=sizes)
+        c.record(stream)
+        torch.cuda.synchronize()
+        if k == 1:
+            tc, td = a.elapsed_time(b) / 1e3, b.elapsed_time(c) / 1e3
+            res = {"round_trip_MBps": total / 1e6 / (tc + td), "compress_MBps": total / 1e6 / tc,
+                   "decompress_MBps": total / 1e6 / td, "lossless": bool(torch.equal(d_dec, d_in))}
+    m.close()
+    return res
+
+
+def run_precision_report(args):
+    """The 4 MB records subset (256 streams x 16 KB, seeds 4000 + i) on the
+    small records model (d_model 64, 2 layers) through every form: code-length
+    gap on the whole subset and max |d log2 p| on 16 x 1 KB, against the FP64
+    oracle, and round-trip MB/s on the GPU."""
+    import torch
+    from oracle import oracle as O
+    from paper_2511_11337_b300 import api
+    path = synth.make_model_file(os.path.join(tempfile.mkdtemp(), "tiny.boaw"), synth.TINY, seed=1)
+    streams = synth.records_workload(256, 16384, seed_base=4000)
+    om = O.Model(path)
+    t0 = time.perf_counter()
+    ref = om.compress_batch(streams, n_threads=os.cpu_count() or 1)
+    t_oracle = time.perf_counter() - t0
+    ref_total = sum(map(len, ref))
+    lp_ref = [om.logprobs(s[:1024]) for s in streams[:16]]
+    total = sum(map(len, streams))
+    rows = {}
+    for f in ("fp32", "tf32x3", "bf16", "fp8"):
+        m = api.Model(path, precision=PREC[f])
+        comp = m.compress(streams)
+        ok = m.decompress(comp, [len(s) for s in streams]) == streams
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        comp = m.compress(streams)
+        m.decompress(comp, [len(s) for s in streams])
+        dt = time.perf_counter() - t0
+        err = max(float(np.abs(m.logprobs(s[:1024]) - r).max()) for s, r in zip(streams[:16], lp_ref))
+        got = sum(map(len, comp))
+        rows[f] = {"form": FORM_DESC[f], "lossless": ok, "compressed_bytes": got,
+                   "bits_per_byte": 8 * got / total, "code_length_gap": (got - ref_total) / ref_total,
+                   "max_abs_dlog2p": err, "round_trip_MBps_host_api": total / 1e6 / dt}
+        m.close()
+    print(json.dumps({"report": "precision forms", "workload": "records subset, 256 x 16 KB (seeds 4000+i), "
+                      "model d_model 64, 2 layers", "oracle_bits_per_byte": 8 * ref_total / total,
+                      "oracle_s": t_oracle, "forms": rows}))
+
+
 # ---------------------------------------------------------------- GPU leg
 
 def run_boa(args):
@@ -182,7 +278,7 @@ def run_boa(args):
     total = len(buf)
 
     stream = torch.cuda.Stream()
-    prec = {"fp32": api.PREC_FP32, "bf16": api.PREC_BF16, "tf32x3": api.PREC_TF32X3, "fp8": api.PREC_FP8}[args.precision]
+    prec = PREC[args.precision]
     model = api.Model(path, device=local, cuda_stream=stream.cuda_stream, max_rows=args.max_rows, precision=prec)
     flat, in_off = api.pack(streams)
     lens = np.diff(in_off)
@@ -277,9 +373,14 @@ def run_boa(args):
         name = f"{dom[1]} ({dom[0]})"
         if dom[1].startswith("gemm") and args.precision in ("bf16", "tf32x3", "fp8"):
             achieved = p["flops"] / (p["ms"] / 1e3) / 1e12
-            pk = peaks["bf16_tflops_sustained"]
+            # a contraction's peak for its own dtype: the measured BF16 rate
+            # times the nominal dense ratio (FP8 4.5/2.25, TF32 1.1/2.25; the
+            # 3xTF32 form issues three TF32 products per FP32 product)
+            ratio = {"bf16": 1.0, "fp8": 2.0, "tf32x3": (1.1 / 2.25) / 3.0}[args.precision]
+            pk = peaks["bf16_tflops_sustained"] * ratio
             roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                    "kernel": name, "peak_source": f"bf16_tflops_sustained ({peak_src})"}
+                    "kernel": name,
+                    "peak_source": f"bf16_tflops_sustained ({peak_src}) x {ratio:.4f} for {args.precision}"}
         elif dom[1].startswith("gemm"):
             achieved = p["flops"] / (p["ms"] / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -306,10 +407,22 @@ def run_boa(args):
         cpu = {"value": v_cpu, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"first {args.cpu_prefix} B of {threads} of the 4096 streams ({nb} B), compress + decompress, {dt:.1f} s"}
 
+    forms = {}
+    if world == 1 and args.forms:
+        names = [f for f in args.forms.split(",") if f and f != args.precision]
+        acc = form_accuracy(streams, [args.precision] + names, path)
+        forms[args.precision] = dict(acc[args.precision], round_trip_MBps=value,
+                                     compress_MBps=total / 1e6 / (phase_ms["compress"] / 1e3),
+                                     decompress_MBps=total / 1e6 / (phase_ms["decompress"] / 1e3))
+        model.close()
+        for f in names:
+            forms[f] = dict(acc[f], **form_speed(f, path, d_in, in_off, d_out, out_off, d_dec, lens, stream))
+
     clocks = clk.summary()
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16 projections, f32 elsewhere",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "f32 (projections as 3xTF32 on tensor cores)",
+                  "bf16": "bf16 projections, f32 elsewhere", "fp8": "e4m3 projections, f32 elsewhere"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD if (args.streams, args.stream_len) == (N_STREAMS, STREAM_LEN) else
                    f"reduced: {args.streams} x {args.stream_len} B of the jet table, same model",
@@ -327,6 +440,7 @@ def run_boa(args):
         "roofline": roof,
         "kernel_breakdown": breakdown,
         "cpu_baseline": cpu,
+        "precision_forms": forms,
         "clocks": clocks,
     }
     print(json.dumps(out))
@@ -344,12 +458,16 @@ def main():
     ap.add_argument("--streams", type=int, default=N_STREAMS)
     ap.add_argument("--stream-len", type=int, default=STREAM_LEN)
     ap.add_argument("--max-rows", type=int, default=0)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32x3", "fp8"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "bf16", "tf32x3", "fp8"])
+    ap.add_argument("--forms", default="fp32,bf16,fp8", help="other precision forms to report ('' for none)")
+    ap.add_argument("--report", default="", choices=["", "precision"])
     ap.add_argument("--cpu-prefix", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.report == "precision":
+        run_precision_report(args)
     else:
         run_boa(args)
 

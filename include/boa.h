@@ -280,7 +280,8 @@ boa_status boa_debug_logprobs(boa_model* model, const uint8_t* stream, size_t le
  * A per row of A (BOA_PREC_FP8).  epilogue: 0 store, 1 + bias[n],
  * 2 C_in + acc, 3 GELU(acc + bias[n]), 4 C_in + (acc + bias[n]).  All pointers
  * host memory; N % 4 == 0; K % 8 == 0 (FP32), K % 64 == 0 (BF16),
- * K % 32 == 0 (TF32X3) or K % 16 == 0 (FP8).  Device 0. */
+ * K % 32 == 0 (TF32X3) or K % 16 == 0 (FP8; K is zero-padded to a multiple
+ * of 128 inside).  Device 0. */
 boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K, const float* A, const float* W,
                           const float* bias, int epilogue, const float* C_in, float* C_out);
 

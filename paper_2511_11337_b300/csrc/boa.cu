@@ -378,8 +378,6 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
     size_t head_o = copy_t(256, d);
     size_t head_b_o = copy(256);
 
-    if (o.precision == BOA_PREC_FP8 && d < 128)
-        return fail(BOA_ERR_FORMAT, "FP8 projections need d_model >= 128 (K-blocks of 128 E4M3 values)");
     boa_model* m = new boa_model();
     m->device = o.device;
     m->precision = o.precision;
@@ -514,9 +512,10 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
         mats.push_back({head_src, (size_t)256, (size_t)d});
         size_t tb = 0, ts = 0;
         std::vector<size_t> atb, ats;
+        auto kpad = [](size_t k) { return (k + 127) / 128 * 128; };
         for (auto& mt : mats) {
             atb.push_back(tb); ats.push_back(ts);
-            tb += (mt.rows * mt.cols + 255) / 256 * 256;
+            tb += (mt.rows * kpad(mt.cols) + 255) / 256 * 256;
             ts += (mt.rows + 63) / 64 * 64;
         }
         std::vector<uint8_t> hq(tb, 0);
@@ -530,7 +529,7 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
                 const float inv = amax > 0.f ? 448.0f / amax : 1.0f;
                 hs[ats[i] + rr] = amax > 0.f ? amax / 448.0f : 1.0f;
                 for (size_t k = 0; k < Cc; k++)
-                    hq[atb[i] + rr * Cc + k] = (uint8_t)__nv_cvt_float_to_fp8(w[k] * inv, __NV_SATFINITE, __NV_E4M3);
+                    hq[atb[i] + rr * kpad(Cc) + k] = (uint8_t)__nv_cvt_float_to_fp8(w[k] * inv, __NV_SATFINITE, __NV_E4M3);
             }
         }
         if (cudaMalloc(&m->w8, tb) != cudaSuccess || cudaMalloc(&m->w8s, ts * 4) != cudaSuccess ||
@@ -682,25 +681,26 @@ template <int EPI>
 static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_e4m3* W, const float* wscale,
                           const float* bias, float* C, long long M, int N, int K) {
     if (M <= 0) return BOA_OK;
-    if (N % 4 != 0 || K % 128 != 0 || K > 1024) return fail(BOA_ERR_FORMAT, "fp8 gemm shape N=%d K=%d unsupported", N, K);
-    TRY(m->a8.ensure((size_t)M * K));
+    if (N % 4 != 0 || K % 16 != 0 || K > 1024) return fail(BOA_ERR_FORMAT, "fp8 gemm shape N=%d K=%d unsupported", N, K);
+    const int Kp = (K + 127) / 128 * 128;     // W is stored with the same zero padding
+    TRY(m->a8.ensure((size_t)M * Kp));
     TRY(m->a8s.ensure((size_t)M));
     {
         ProfScope pq(m, BOA_KC_OTHER, 3.0 * M * K, 5.0 * M * K + 4.0 * M);
         k_quant_rows_e4m3<<<(unsigned)((M + 7) / 8), 256, 0, m->stream>>>(
-            A, reinterpret_cast<__nv_fp8_e4m3*>(m->a8.p), m->a8s.p, M, K);
+            A, reinterpret_cast<__nv_fp8_e4m3*>(m->a8.p), m->a8s.p, M, K, Kp);
     }
     TRY(check_launch(m, "quant_rows"));
     const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
     ProfScope ps(m, cls, 2.0 * M * N * K, ((double)M * K + (double)K * N) + 4.0 * (double)M * N * (resid ? 2 : 1));
     const int BN = tc_bn(N);
     CUtensorMap ta, tb;
-    TRY(tmap_2d(m, m->a8.p, (uint64_t)M, (uint64_t)K, kTcBM, 1, &ta));
-    TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 1, &tb));
+    TRY(tmap_2d(m, m->a8.p, (uint64_t)M, (uint64_t)Kp, kTcBM, 1, &ta));
+    TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)Kp, (uint32_t)BN, 1, &tb));
     switch (BN) {
-        case 48: launch_tc<48, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, K, m->a8s.p, wscale); break;
-        case 64: launch_tc<64, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, K, m->a8s.p, wscale); break;
-        default: launch_tc<128, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, K, m->a8s.p, wscale); break;
+        case 48: launch_tc<48, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->a8s.p, wscale); break;
+        case 64: launch_tc<64, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->a8s.p, wscale); break;
+        default: launch_tc<128, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->a8s.p, wscale); break;
     }
     return check_launch(m, "gemm_f8");
 }
@@ -1652,7 +1652,8 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
         } else if (precision == BOA_PREC_FP8) {
             TRY(t.err.ensure(1));
             CU(cudaMemset(t.err.p, 0, 4));
-            std::vector<uint8_t> q(N * K);
+            const size_t Kp = (K + 127) / 128 * 128;
+            std::vector<uint8_t> q(N * Kp, 0);
             std::vector<float> sc(N);
             for (size_t n = 0; n < N; n++) {
                 float amax = 0.f;
@@ -1660,13 +1661,13 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
                 const float inv = amax > 0.f ? 448.0f / amax : 1.0f;
                 sc[n] = amax > 0.f ? amax / 448.0f : 1.0f;
                 for (size_t k = 0; k < K; k++)
-                    q[n * K + k] = (uint8_t)__nv_cvt_float_to_fp8(W[n * K + k] * inv, __NV_SATFINITE, __NV_E4M3);
+                    q[n * Kp + k] = (uint8_t)__nv_cvt_float_to_fp8(W[n * K + k] * inv, __NV_SATFINITE, __NV_E4M3);
             }
             DevBuf<uint8_t> dq;
             DevBuf<float> ds;
-            TRY(dq.ensure(N * K));
+            TRY(dq.ensure(N * Kp));
             TRY(ds.ensure(N));
-            CU(cudaMemcpy(dq.p, q.data(), N * K, cudaMemcpyHostToDevice));
+            CU(cudaMemcpy(dq.p, q.data(), N * Kp, cudaMemcpyHostToDevice));
             CU(cudaMemcpy(ds.p, sc.data(), N * 4, cudaMemcpyHostToDevice));
             const __nv_fp8_e4m3* w8 = reinterpret_cast<const __nv_fp8_e4m3*>(dq.p);
             boa_status r = BOA_OK;

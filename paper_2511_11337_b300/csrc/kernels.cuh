@@ -712,9 +712,10 @@ __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restric
 
 // Per-row FP8 quantisation of an activation matrix for the E4M3 GEMM:
 // scale[m] = max_k |A[m][k]| / 448 and q[m][k] = e4m3(A[m][k] * (448 / max)),
-// rounded to nearest and saturated; one warp per row, K <= 1024.
+// rounded to nearest and saturated; q has Kp >= K columns, the extra ones
+// zero (the GEMM's K blocks are 128 wide).  One warp per row, K <= 1024.
 __global__ void k_quant_rows_e4m3(const float* __restrict__ A, __nv_fp8_e4m3* __restrict__ q,
-                                  float* __restrict__ scale, long long M, int K) {
+                                  float* __restrict__ scale, long long M, int K, int Kp) {
     const int lane = threadIdx.x & 31;
     const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (row >= M) return;
@@ -727,13 +728,17 @@ __global__ void k_quant_rows_e4m3(const float* __restrict__ A, __nv_fp8_e4m3* __
     amax = warp_max(amax);
     const float inv = amax > 0.f ? __fdiv_rn(448.0f, amax) : 1.0f;
     if (lane == 0) scale[row] = amax > 0.f ? __fdiv_rn(amax, 448.0f) : 1.0f;
-    __nv_fp8_e4m3* o = q + row * K;
-    for (int k = 4 * lane; k < K; k += 128) {
-        const float4 v = *reinterpret_cast<const float4*>(a + k);
-        o[k + 0] = __nv_fp8_e4m3(__fmul_rn(v.x, inv));
-        o[k + 1] = __nv_fp8_e4m3(__fmul_rn(v.y, inv));
-        o[k + 2] = __nv_fp8_e4m3(__fmul_rn(v.z, inv));
-        o[k + 3] = __nv_fp8_e4m3(__fmul_rn(v.w, inv));
+    __nv_fp8_e4m3* o = q + row * Kp;
+    for (int k = 4 * lane; k < Kp; k += 128) {
+        if (k < K) {
+            const float4 v = *reinterpret_cast<const float4*>(a + k);
+            o[k + 0] = __nv_fp8_e4m3(__fmul_rn(v.x, inv));
+            o[k + 1] = __nv_fp8_e4m3(__fmul_rn(v.y, inv));
+            o[k + 2] = __nv_fp8_e4m3(__fmul_rn(v.z, inv));
+            o[k + 3] = __nv_fp8_e4m3(__fmul_rn(v.w, inv));
+        } else {
+            o[k + 0] = o[k + 1] = o[k + 2] = o[k + 3] = __nv_fp8_e4m3(0.0f);
+        }
     }
 }
 
