@@ -45,6 +45,22 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x m
 PREC = {"fp32": 0, "bf16": 1, "tf32x3": 2, "fp8": 3}
 
 
+def shard_range(n: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous share [lo, hi) of n independent streams for one rank."""
+    lo = n * rank // world
+    return lo, n * (rank + 1) // world
+
+
+def reduce_max(value: float, dist, device) -> float:
+    """Max over ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -273,9 +289,12 @@ def run_boa(args):
 
     tmpd = tempfile.mkdtemp()
     path = synth.make_model_file(os.path.join(tmpd, "paper.boaw"), synth.PAPER_SCALE, seed=2)
-    buf = synth.atlas_workload(args.streams, args.stream_len, seed=2000 + rank)
-    streams = synth.split_equal(buf, args.streams)
-    total = len(buf)
+    # The job is world x 64 MiB of independent streams; each rank compresses
+    # its contiguous share (weak scaling, no data-path collective).
+    lo, hi = shard_range(world * args.streams, rank, world)
+    buf = synth.atlas_workload(args.streams, args.stream_len, seed=2000 + lo // args.streams)
+    streams = synth.split_equal(buf, args.streams)[: hi - lo]
+    total = sum(map(len, streams))
 
     stream = torch.cuda.Stream()
     prec = PREC[args.precision]
@@ -329,9 +348,7 @@ def run_boa(args):
     prof = model.profile_read()
     ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = reduce_max(ms, dist, "cuda")
         dist.barrier()
     assert torch.equal(d_dec, d_in), "round trip failed in timed region"
     comp_total = int(np.sum(sizes))

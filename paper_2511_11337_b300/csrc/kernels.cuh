@@ -214,6 +214,49 @@ k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* _
     const int total = n_streams * Tc;       // rows this CTA visits, stream-major
     const size_t row0 = (size_t)s_first * Tc;
     float h[NS];
+    if (Tc == 1) {
+        // One step per stream (decompression): the next stream's state is
+        // fetched before the current one is computed, so state loads stay in
+        // flight during the arithmetic.
+        __syncthreads();
+        for (int i = threadIdx.x; i < total * W; i += blockDim.x) sm[i / W][i % W] = dbc[(row0 + i / W) * W + i % W];
+        __syncthreads();
+        if (!live) return;
+        float hn[NS];
+#pragma unroll
+        for (int n = 0; n < NS; n++) hn[n] = hstate[((size_t)s_first * NS + n) * E + c];
+        for (int rr = 0; rr < total; rr++) {
+            const int s = s_first + rr;
+            const size_t row = row0 + rr;
+#pragma unroll
+            for (int n = 0; n < NS; n++) h[n] = hn[n];
+            if (rr + 1 < total) {
+#pragma unroll
+                for (int n = 0; n < NS; n++) hn[n] = hstate[((size_t)(s + 1) * NS + n) * E + c];
+            }
+            const float uc = u[row * E + c];
+            const float z = xz[row * 2 * E + E + c];
+            float pre = 0.f;
+#pragma unroll
+            for (int j = 0; j < R; j++) pre = __fmaf_rn(wdt[j], sm[rr][j], pre);
+            const float delta = softplus_f(__fadd_rn(pre, bdt));
+            const float du = __fmul_rn(delta, uc);
+            float y = 0.f;
+#pragma unroll
+            for (int n = 0; n < NS; n++) {
+                const float da = ex2_approx(__fmul_rn(delta, a2[n]));
+                h[n] = __fmaf_rn(da, h[n], __fmul_rn(du, sm[rr][R + n]));
+                y = __fmaf_rn(sm[rr][R + NS + n], h[n], y);
+            }
+            y = __fmaf_rn(dv, uc, y);
+            const float o = __fmul_rn(y, silu_f(z));
+            if (yg_b) yg_b[row * E + c] = __float2bfloat16_rn(o);
+            else yg[row * E + c] = o;
+#pragma unroll
+            for (int n = 0; n < NS; n++) hstate[((size_t)s * NS + n) * E + c] = h[n];
+        }
+        return;
+    }
     for (int r0 = 0; r0 < total; r0 += kScanRowsSmem) {
         const int nr = min(kScanRowsSmem, total - r0);
         __syncthreads();
