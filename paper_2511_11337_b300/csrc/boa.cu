@@ -642,17 +642,28 @@ static boa_status tmap_2d(boa_model* m, const void* ptr, uint64_t rows, uint64_t
 // same MMA shape in compression and decompression.
 static int tc_bn(int N) { return N >= 512 ? 128 : N > 48 ? 64 : 48; }
 
+template <int BN, int EPI, int KIND, bool DEEP>
+static void launch_tc_cfg(boa_model* m, dim3 grid, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias,
+                          float* C, __nv_bfloat16* outb, long long M, int N, int K, const float* rs, const float* cs) {
+    using L = TcSmem<BN, DEEP>;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L::kBytes);
+    });
+    k_gemm_tc_bf16<BN, EPI, KIND, DEEP><<<grid, kTcThreads, L::kBytes, m->stream>>>(ta, tb, bias, C, outb, (int)M, N,
+                                                                                    K, m->err.p, rs, cs);
+}
+
+// Grids smaller than the SM count take the deep-pipeline variant.
 template <int BN, int EPI, int KIND>
 static void launch_tc(boa_model* m, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, float* C,
                       __nv_bfloat16* outb, long long M, int N, int K, const float* rs, const float* cs) {
-    using L = TcSmem<BN>;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(k_gemm_tc_bf16<BN, EPI, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
-    });
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
-    k_gemm_tc_bf16<BN, EPI, KIND><<<grid, kTcThreads, L::kBytes, m->stream>>>(ta, tb, bias, C, outb, (int)M, N, K,
-                                                                              m->err.p, rs, cs);
+    if ((long long)grid.x * grid.y < m->num_sms)
+        launch_tc_cfg<BN, EPI, KIND, true>(m, grid, ta, tb, bias, C, outb, M, N, K, rs, cs);
+    else
+        launch_tc_cfg<BN, EPI, KIND, false>(m, grid, ta, tb, bias, C, outb, M, N, K, rs, cs);
 }
 
 template <int EPI>
@@ -705,16 +716,27 @@ static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_
     return check_launch(m, "gemm_f8");
 }
 
+template <int BN, int EPI, bool DEEP>
+static void launch_t3_cfg(boa_model* m, dim3 grid, const CUtensorMap& ta, const CUtensorMap& th, const CUtensorMap& tl,
+                          const float* bias, float* C, long long M, int N, int K) {
+    using L = T3Smem<BN, DEEP>;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_gemm_tc_tf32x3<BN, EPI, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L::kBytes);
+    });
+    k_gemm_tc_tf32x3<BN, EPI, DEEP><<<grid, kT3Threads, L::kBytes, m->stream>>>(ta, th, tl, bias, C, (int)M, N, K,
+                                                                                m->err.p);
+}
+
 template <int BN, int EPI>
 static void launch_t3(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th, const CUtensorMap& tl,
                       const float* bias, float* C, long long M, int N, int K) {
-    using L = T3Smem<BN>;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(k_gemm_tc_tf32x3<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
-    });
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
-    k_gemm_tc_tf32x3<BN, EPI><<<grid, kT3Threads, L::kBytes, m->stream>>>(ta, th, tl, bias, C, (int)M, N, K, m->err.p);
+    if ((long long)grid.x * grid.y < m->num_sms)
+        launch_t3_cfg<BN, EPI, true>(m, grid, ta, th, tl, bias, C, M, N, K);
+    else
+        launch_t3_cfg<BN, EPI, false>(m, grid, ta, th, tl, bias, C, M, N, K);
 }
 
 // FP32-accurate tensor-core GEMM (3xTF32); A is FP32, W pre-split.

@@ -251,15 +251,18 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, int q, int lane, int 
     }
 }
 
-template <int BN>
+// DEEP = false: about 110 KB of stages so that two CTAs share an SM (one's
+// epilogue overlaps the other's loads and MMAs; TMEM 2 x kTmemCols <= 512).
+// DEEP = true: up to about 200 KB (one CTA per SM), for grids smaller than
+// the SM count, where every K block's loads should be in flight at once.
+// The stage count never changes the MMA sequence, only the overlap.
+template <int BN, bool DEEP = false>
 struct TcSmem {
     static constexpr int kA = kTcBM * kTcBK * 2;     // 16 KB
     static constexpr int kB = BN * kTcBK * 2;
     static constexpr int kStage = kA + kB;
-    // about 110 KB of stages so that two CTAs share an SM (one's epilogue
-    // overlaps the other's loads and MMAs); TMEM: 2 x kTmemCols <= 512
-    static constexpr int kStagesRaw = (110 * 1024) / kStage;
-    static constexpr int kStages = kStagesRaw < 2 ? 2 : (kStagesRaw > 6 ? 6 : kStagesRaw);
+    static constexpr int kStagesRaw = ((DEEP ? 200 : 110) * 1024) / kStage;
+    static constexpr int kStages = kStagesRaw < 2 ? 2 : (kStagesRaw > 8 ? 8 : kStagesRaw);
     static constexpr int kTmemCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     // stages, then barriers (full, empty, done) and the TMEM address slot
     static constexpr int kBars = 2 * kStages + 1;
@@ -270,14 +273,14 @@ struct TcSmem {
 // KIND selects BF16 operands (K = 64 per stage, kind::f16) or E4M3 operands
 // (K = 128 per stage, kind::f8f6f4, with row / column scales in the
 // epilogue); either way a stage row is 128 bytes.
-template <int BN, int EPI, int KIND>
+template <int BN, int EPI, int KIND, bool DEEP = false>
 __global__ void __launch_bounds__(kTcThreads)
 k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const float* __restrict__ bias, float* __restrict__ Cm, __nv_bfloat16* __restrict__ out_bf16,
                int M, int N, int K, int* __restrict__ err, const float* __restrict__ row_scale,
                const float* __restrict__ col_scale) {
     constexpr int kElemK = KIND == kKindE4M3 ? 128 : kTcBK;    // elements per 128-byte stage row
-    using L = TcSmem<BN>;
+    using L = TcSmem<BN, DEEP>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)L::kStages * L::kStage);
@@ -407,23 +410,23 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
-template <int BN>
+template <int BN, bool DEEP = false>
 struct T3Smem {
     static constexpr int kA = kTcBM * kT3BK * 4;     // 16 KB (fp32 -> hi in place)
     static constexpr int kB = BN * kT3BK * 4;
     static constexpr int kStage = 2 * kA + 2 * kB;   // A_hi, A_lo, B_hi, B_lo
-    static constexpr int kStages = 2;
+    static constexpr int kStages = DEEP ? (200 * 1024) / kStage : 2;
     static constexpr int kTmemCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     static constexpr int kBars = 3 * kStages + 1;    // full, converted, empty, done
     static constexpr size_t kBytes = 1024 + (size_t)kStages * kStage + 8 * kBars + 16;
 };
 
-template <int BN, int EPI>
+template <int BN, int EPI, bool DEEP = false>
 __global__ void __launch_bounds__(kT3Threads)
 k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
                  const __grid_constant__ CUtensorMap tmBlo, const float* __restrict__ bias, float* __restrict__ Cm,
                  int M, int N, int K, int* __restrict__ err) {
-    using L = T3Smem<BN>;
+    using L = T3Smem<BN, DEEP>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)L::kStages * L::kStage);
