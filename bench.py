@@ -314,6 +314,7 @@ def run_boa(args):
         model.decompress_device(d_out.data_ptr(), out_off, lens, d_dec.data_ptr(), in_off, in_sizes=sizes)
         return sizes, n1 + model.last_launch_count
 
+    tuning = model.autotune(len(streams), args.stream_len) if args.autotune else None
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -445,7 +446,7 @@ def run_boa(args):
                    f"reduced: {args.streams} x {args.stream_len} B of the jet table, same model",
                    "streams": args.streams, "stream_len": args.stream_len, "bytes_per_gpu": total,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "flushed (256 MiB write) before every timed step"},
+                   "l2": "flushed (256 MiB write) before every timed step", "autotuned": tuning},
         "compression_ratio": total / comp_total,
         "compressed_bytes": comp_total,
         "wall_s_timed": t_wall,
@@ -478,6 +479,7 @@ def main():
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "bf16", "tf32x3", "fp8"])
     ap.add_argument("--forms", default="fp32,bf16,fp8", help="other precision forms to report ('' for none)")
     ap.add_argument("--report", default="", choices=["", "precision"])
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--cpu-prefix", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

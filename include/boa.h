@@ -170,7 +170,8 @@ boa_status boa_profile_read(const boa_model* model, int phase, int kernel_class,
 /* Launch configuration chosen by boa_autotune. */
 typedef struct {
     size_t max_rows;        /* compression rows (slot x step) per chunk */
-    int scan_group;         /* decompression scan: streams per CTA */
+    int scan_group;         /* decompression scan: 0 = four channels per thread, one stream
+                               per CTA; G > 0 = one channel per thread, G streams per CTA */
     double compress_ms;     /* estimated time for the whole workload */
     double decompress_ms;
 } boa_tuning;
@@ -178,9 +179,10 @@ typedef struct {
 /* Time candidate launch configurations on a synthetic batch shaped like the
  * caller's workload (n_streams streams of stream_len bytes; a 512-byte sample
  * of each is run) and keep the fastest in the model: the compression chunk
- * size (max_rows in 2^16 .. 2^19) and the decode scan's streams per CTA
- * (1 .. 16).  Neither knob changes any result: rows are computed the same
- * way whatever the chunking or grouping.  out (host, may be NULL) receives
+ * size (max_rows in 2^16 .. 2^19) and the decode scan variant (four
+ * channels per thread, or one channel per thread with 1 .. 16 streams per
+ * CTA).  Neither knob changes any result: rows are computed the same way
+ * whatever the chunking, grouping or variant.  out (host, may be NULL) receives
  * the choice and the extrapolated times.  Allocates and frees a scratch
  * batch on the device.  Errors: BOA_ERR_ARG, BOA_ERR_CUDA, BOA_ERR_OOM. */
 boa_status boa_autotune(boa_model* model, size_t n_streams, size_t stream_len, boa_tuning* out);

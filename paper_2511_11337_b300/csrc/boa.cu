@@ -183,7 +183,7 @@ struct boa_model {
     size_t max_rows = 1u << 18;
     size_t max_slots = 8192;        // streams in flight
     bool use_graphs = true;         // decode step loop as CUDA graphs (when not profiling)
-    int scan_group = 0;             // decode scan streams per CTA; 0 = default
+    int scan_group = 0;             // decode scan variant (see stream_group)
 };
 
 static uint64_t fnv1a64(const uint8_t* p, size_t n) {
@@ -799,13 +799,12 @@ static boa_status ln_ln(boa_model* m, long long rows, int l) {
     return check_launch(m, "ln_ln");
 }
 
-// Streams per CTA for the scan: one step over many streams (decompression)
-// groups several streams so the per-channel weights load once.  The group
-// size is a tuning knob (boa_autotune); it never changes a result.
+// Decode-step scan variant, a tuning knob (boa_autotune) that never changes
+// a result: 0 = four channels per thread, one stream per CTA (k_scan_step4);
+// G > 0 = one channel per thread, G streams per CTA (k_scan).
 static int stream_group(const boa_model* m, int S, int Tc) {
     if (Tc != 1) return 1;
-    if (m->scan_group > 0) return m->scan_group;
-    return S >= 1024 ? 8 : 1;
+    return m->scan_group;
 }
 
 static boa_status conv(boa_model* m, int l, int S, int Tc) {
@@ -830,12 +829,22 @@ static boa_status conv(boa_model* m, int l, int S, int Tc) {
 static boa_status scan(boa_model* m, int l, int S, int Tc) {
     const DevLayer& L = m->layers[l];
     const int G = stream_group(m, S, Tc);
-    dim3 grid((m->E + kScanThreads - 1) / kScanThreads, (S + G - 1) / G);
     float* hs = m->h.p + (size_t)l * S * m->N * m->E;
     const double rows = (double)S * Tc;
     ProfScope ps(m, BOA_KC_SCAN, rows * m->E * (2.0 * m->r + 5.0 * m->N + 12),
                  4.0 * (rows * (3.0 * m->E + m->R2) + 2.0 * S * m->N * m->E));
     __nv_bfloat16* ygb = m->precision == BOA_PREC_BF16 ? m->yg_b.p : nullptr;
+    if (G == 0 && Tc == 1) {
+        dim3 g4((m->E + 4 * kScanThreads - 1) / (4 * kScanThreads), S);
+#define STEP4_CASE(RR)                                                                                       \
+    k_scan_step4<16, RR><<<g4, kScanThreads, 0, m->stream>>>(m->u.p, m->xz.p, m->dbc.p, L.dt_w, L.dt_b, L.A2, \
+                                                             L.D, hs, m->yg.p, ygb, m->E)
+        switch (m->r) { case 4: STEP4_CASE(4); break; case 8: STEP4_CASE(8); break; default: STEP4_CASE(16); break; }
+#undef STEP4_CASE
+        return check_launch(m, "scan_step4");
+    }
+    const int Gd = std::max(G, 1);
+    dim3 grid((m->E + kScanThreads - 1) / kScanThreads, (S + Gd - 1) / Gd);
 #define SCAN_CASE(RR, GG)                                                                                         \
     k_scan<16, RR, GG><<<grid, kScanThreads, 0, m->stream>>>(m->u.p, m->xz.p, m->dbc.p, L.dt_w, L.dt_b, L.A2, L.D, \
                                                              hs, m->yg.p, ygb, m->E, S, Tc)
@@ -1469,7 +1478,7 @@ extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream
         if (st == BOA_OK && ms < best.compress_ms) { best.compress_ms = ms; best.max_rows = r; }
     }
     m->max_rows = best.max_rows;
-    const int g_cand[] = {1, 2, 4, 8, 16};
+    const int g_cand[] = {0, 1, 2, 4, 8, 16};
     for (int g : g_cand) {
         if (st != BOA_OK) break;
         m->scan_group = g;

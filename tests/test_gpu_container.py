@@ -52,7 +52,7 @@ def test_autotune_keeps_bytes(api, tiny_model_path):
     m = api.Model(tiny_model_path)
     before = m.compress(streams)
     t = m.autotune(len(streams), 1024)
-    assert t["max_rows"] in (1 << 16, 1 << 17, 1 << 18, 1 << 19) and t["scan_group"] in (1, 2, 4, 8, 16)
+    assert t["max_rows"] in (1 << 16, 1 << 17, 1 << 18, 1 << 19) and t["scan_group"] in (0, 1, 2, 4, 8, 16)
     after = m.compress(streams)
     assert after == before
     assert m.decompress(after, [len(s) for s in streams]) == streams
