@@ -347,6 +347,7 @@ def run_boa(args):
         t_wall = time.perf_counter() - t_wall
     model.profile(False)
     prof = model.profile_read()
+    prof_steps = model.profile_steps()
     ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
     if dist:
         ms = reduce_max(ms, dist, "cuda")
@@ -377,11 +378,13 @@ def run_boa(args):
     value = world * total / 1e6 / (ms / 1e3)
     peaks, peak_src = measured_peaks()
     # Per-(phase, class) device time per step: compression launches are all
-    # timed; decompression launches every `stride`-th step, so scale by it.
+    # timed; of the decode steps (CUDA graphs of 32) one eager step per graph
+    # launch is timed, so scale by all steps / timed steps.
     est = {}
     for phase, d in prof.items():
+        timed, total = prof_steps[phase]
         for k, v in d.items():
-            scale = (stride if phase == "decompress" else 1) / args.steps
+            scale = (total / timed if timed else 0.0) / args.steps
             est[(phase, k)] = dict(v, ms_step=v["ms"] * scale)
     step_est = sum(v["ms_step"] for v in est.values())
     dom = max(est, key=lambda k: est[k]["ms_step"]) if est else None
@@ -457,6 +460,7 @@ def run_boa(args):
         "decompress_MBps": total / 1e6 / (phase_ms["decompress"] / 1e3) if phase_ms["decompress"] else None,
         "roofline": roof,
         "kernel_breakdown": breakdown,
+        "profiled_steps": {ph: {"timed": a, "all": b} for ph, (a, b) in prof_steps.items()},
         "cpu_baseline": cpu,
         "precision_forms": forms,
         "clocks": clocks,

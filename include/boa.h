@@ -156,22 +156,34 @@ typedef enum {
     BOA_KC_COUNT = 12
 } boa_kernel_class;
 
-/* Benchmark hook: when on, every kernel launch of compress / decompress is
- * bracketed by a pair of CUDA events on the model's stream (decompression:
- * only every decode_step_stride-th step), and per-(phase, class) totals
+/* Benchmark hook: when on, kernel launches of timed steps are bracketed by a
+ * pair of CUDA events on the model's stream, and per-(phase, class) totals
  * accumulate: launches timed, summed device milliseconds, and the
  * algorithmic FLOPs and DRAM bytes those launches must at least perform.
- * phase: 0 = compression, 1 = decompression.  Reset clears totals. */
+ * phase: 0 = compression (every chunk is timed), 1 = decompression: where
+ * the decode step loop runs as CUDA graphs of 32 steps, the eager step
+ * before each graph launch (and the first step) is timed; otherwise every
+ * decode_step_stride-th step.  A timed decode step runs its lanes one after
+ * another on the model's stream.  Reset clears totals and step counts. */
 boa_status boa_profile_enable(boa_model* model, int on, int decode_step_stride);
 boa_status boa_profile_reset(boa_model* model);
 boa_status boa_profile_read(const boa_model* model, int phase, int kernel_class, uint64_t* launches,
                             double* total_ms, double* flops, double* bytes);
 
+/* Steps (compression chunks, decode steps) of a phase since the last reset:
+ * how many were timed and how many ran in all (host out, may be NULL). */
+boa_status boa_profile_steps(const boa_model* model, int phase, uint64_t* timed, uint64_t* total);
+
 /* Launch configuration chosen by boa_autotune. */
 typedef struct {
     size_t max_rows;        /* compression rows (slot x step) per chunk */
-    int scan_group;         /* decompression scan: 0 = four channels per thread, one stream
-                               per CTA; G > 0 = one channel per thread, G streams per CTA */
+    int scan_variant;       /* decompression scan kernel: 0 = persistent, bulk-copy fed;
+                               1 = four channels per thread, one stream per CTA;
+                               2 = one channel per thread, one stream per CTA;
+                               3 = one channel per thread, eight streams per CTA */
+    int decode_lanes;       /* decompression: slots split into this many independent
+                               groups whose steps run on separate CUDA streams
+                               (0 = automatic: 2 from 2048 slots, else 1) */
     double compress_ms;     /* estimated time for the whole workload */
     double decompress_ms;
 } boa_tuning;
@@ -179,13 +191,21 @@ typedef struct {
 /* Time candidate launch configurations on a synthetic batch shaped like the
  * caller's workload (n_streams streams of stream_len bytes; a 512-byte sample
  * of each is run) and keep the fastest in the model: the compression chunk
- * size (max_rows in 2^16 .. 2^19) and the decode scan variant (four
- * channels per thread, or one channel per thread with 1 .. 16 streams per
- * CTA).  Neither knob changes any result: rows are computed the same way
- * whatever the chunking, grouping or variant.  out (host, may be NULL) receives
+ * size (max_rows in 2^16 .. 2^19), the decode scan kernel (scan_variant)
+ * and the decode lanes (1, 2 or 4).  No knob changes any result: rows are
+ * computed the same way whatever the chunking, kernel or lane split.  out (host, may be NULL) receives
  * the choice and the extrapolated times.  Allocates and frees a scratch
  * batch on the device.  Errors: BOA_ERR_ARG, BOA_ERR_CUDA, BOA_ERR_OOM. */
 boa_status boa_autotune(boa_model* model, size_t n_streams, size_t stream_len, boa_tuning* out);
+
+/* Apply a launch configuration (for instance one saved from an earlier
+ * boa_autotune): max_rows in 1 .. 2^24, scan_variant in 0 .. 3,
+ * decode_lanes in 0 .. 16; the _ms fields are ignored.  Results do not
+ * depend on it.  Errors: BOA_ERR_ARG. */
+boa_status boa_set_tuning(boa_model* model, const boa_tuning* tuning);
+
+/* The configuration in use (host out; the _ms fields are zero). */
+boa_status boa_get_tuning(const boa_model* model, boa_tuning* out);
 
 /* ------------------------------------------------------------ container
  * The .boa container of the paper (section "Coders & Parallelisation"): the

@@ -25,6 +25,8 @@ SIGNATURES = {
     "boa_last_launch_count": (u64, [vp]),
     "boa_last_error": (C.c_char_p, []),
     "boa_autotune": (i32, [vp, sz, sz, vp]),
+    "boa_set_tuning": (i32, [vp, vp]),
+    "boa_get_tuning": (i32, [vp, vp]),
     "boa_pack_bound": (sz, [sz, sz]),
     "boa_pack": (i32, [vp, vp, sz, sz, vp, sz, C.POINTER(sz)]),
     "boa_unpack_info": (i32, [vp, sz, C.POINTER(u64), C.POINTER(u64)]),
@@ -35,6 +37,7 @@ SIGNATURES = {
     "boa_profile_enable": (i32, [vp, i32, i32]),
     "boa_profile_reset": (i32, [vp]),
     "boa_profile_read": (i32, [vp, i32, i32, vp, vp, vp, vp]),
+    "boa_profile_steps": (i32, [vp, i32, vp, vp]),
     "boa_debug_encode_cdfs": (i32, [sz, vp, vp, vp, vp, sz, vp]),
     "boa_debug_decode_cdfs": (i32, [sz, vp, vp, vp, sz, vp, vp]),
     "boa_debug_quantise": (i32, [sz, vp, vp]),

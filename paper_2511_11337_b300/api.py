@@ -33,7 +33,7 @@ class _Opts(C.Structure):
 
 
 class _Tuning(C.Structure):
-    _fields_ = [("max_rows", C.c_size_t), ("scan_group", C.c_int), ("compress_ms", C.c_double),
+    _fields_ = [("max_rows", C.c_size_t), ("scan_variant", C.c_int), ("decode_lanes", C.c_int), ("compress_ms", C.c_double),
                 ("decompress_ms", C.c_double)]
 
 
@@ -140,11 +140,24 @@ class Model:
         return out[:n.value].tobytes()
 
     def autotune(self, n_streams: int, stream_len: int) -> dict:
-        """boa_autotune: pick chunk size and decode scan grouping for this shape."""
+        """boa_autotune: pick the chunk size and the decode scan kernel for this shape."""
         t = _Tuning()
         check(load().boa_autotune(self._h, n_streams, stream_len, C.byref(t)))
-        return {"max_rows": int(t.max_rows), "scan_group": int(t.scan_group),
-                "compress_ms_est": t.compress_ms, "decompress_ms_est": t.decompress_ms}
+        return {"max_rows": int(t.max_rows), "scan_variant": int(t.scan_variant),
+                "decode_lanes": int(t.decode_lanes), "compress_ms_est": t.compress_ms,
+                "decompress_ms_est": t.decompress_ms}
+
+    def set_tuning(self, max_rows: int, scan_variant: int, decode_lanes: int = 0) -> None:
+        """boa_set_tuning: apply a launch configuration (results do not depend on it)."""
+        t = _Tuning(max_rows, scan_variant, decode_lanes, 0.0, 0.0)
+        check(load().boa_set_tuning(self._h, C.byref(t)))
+
+    def tuning(self) -> dict:
+        """boa_get_tuning: the configuration in use."""
+        t = _Tuning()
+        check(load().boa_get_tuning(self._h, C.byref(t)))
+        return {"max_rows": int(t.max_rows), "scan_variant": int(t.scan_variant),
+                "decode_lanes": int(t.decode_lanes)}
 
     # ----------------------------------------------------------- benchmark hooks
     KERNEL_CLASSES = ["embed_ln", "gemm_in_proj", "conv_silu", "gemm_x_proj", "scan", "gemm_out_proj",
@@ -167,6 +180,15 @@ class Model:
                 if n.value:
                     d[name] = {"launches": int(n.value), "ms": ms.value, "flops": fl.value, "bytes": by.value}
             out[pname] = d
+        return out
+
+    def profile_steps(self) -> dict:
+        """{phase: (timed steps, all steps)} since the last profile_reset."""
+        out = {}
+        for ph, pname in enumerate(("compress", "decompress")):
+            a, b = C.c_uint64(), C.c_uint64()
+            check(load().boa_profile_steps(self._h, ph, C.byref(a), C.byref(b)))
+            out[pname] = (int(a.value), int(b.value))
         return out
 
     # ----------------------------------------------------------- test hooks

@@ -28,6 +28,7 @@
 #include "gemm_fp32.cuh"
 #include "gemm_tc.cuh"
 #include "kernels.cuh"
+#include "scan_step.cuh"
 #include "scan_train.cuh"
 
 using namespace boa;
@@ -115,6 +116,22 @@ struct HostBuf {
     }
 };
 
+// The slice of the workspace that one sequence of launches works on: slots
+// [s0, s0 + n) of the schedule, their rows (slot-major, Tc rows per slot),
+// their SSM and conv state, and the stream the kernels go to.  Without
+// decode lanes one view covers every slot on the model's stream.
+struct View {
+    float *x = nullptr, *xn = nullptr, *xz = nullptr, *u = nullptr, *dbc = nullptr, *yg = nullptr;
+    float *logits = nullptr, *hid = nullptr, *h = nullptr, *conv = nullptr, *a8s = nullptr;
+    __nv_bfloat16 *xn_b = nullptr, *u_b = nullptr, *yg_b = nullptr, *x_b = nullptr, *hid_b = nullptr;
+    uint8_t* a8 = nullptr;
+    SlotState* slots = nullptr;
+    CoderState* st = nullptr;
+    const int* slot_beg = nullptr;
+    size_t S_all = 0;              // slots in the state arrays (their layer stride)
+    cudaStream_t stream = nullptr;
+};
+
 struct boa_model {
     int device = 0;
     int precision = BOA_PREC_FP32;
@@ -183,7 +200,14 @@ struct boa_model {
     size_t max_rows = 1u << 18;
     size_t max_slots = 8192;        // streams in flight
     bool use_graphs = true;         // decode step loop as CUDA graphs (when not profiling)
-    int scan_group = 0;             // decode scan variant (see stream_group)
+    int scan_variant = 0;           // decode-step scan kernel (see scan())
+    int decode_lanes = 0;           // independent slot groups per decode step (0 = automatic)
+    size_t kp8 = 0;                 // row stride of the FP8 activation scratch
+
+    View v;                         // what the launchers work on
+    std::vector<cudaStream_t> lane_streams;
+    std::vector<cudaEvent_t> lane_events;   // [0] fork, [1 + p] lane p done
+    uint64_t prof_steps[2][2] = {};         // [phase][timed, all] steps of the step loops
 };
 
 static uint64_t fnv1a64(const uint8_t* p, size_t n) {
@@ -216,14 +240,14 @@ struct ProfScope {
     ProfScope(boa_model* m_, int cls_, double flops_, double bytes_) : m(m_), cls(cls_), flops(flops_), bytes(bytes_) {
         if (m->prof_on && m->prof_step) {
             a = prof_event(m);
-            if (a) cudaEventRecord(a, m->stream);
+            if (a) cudaEventRecord(a, m->v.stream);
         }
     }
     ~ProfScope() {
         if (!a) return;
         cudaEvent_t b = prof_event(m);
         if (!b) return;
-        cudaEventRecord(b, m->stream);
+        cudaEventRecord(b, m->v.stream);
         m->prof_pending.push_back({m->prof_phase, cls, a, b, flops, bytes});
     }
 };
@@ -276,6 +300,8 @@ extern "C" void boa_free_model(boa_model* m) {
     if (m->stream) cudaStreamSynchronize(m->stream);
     free_workspace(m);
     for (auto e : m->ev_pool) cudaEventDestroy(e);
+    for (auto e : m->lane_events) cudaEventDestroy(e);
+    for (auto ls : m->lane_streams) cudaStreamDestroy(ls);
     if (m->weights) cudaFree(m->weights);
     if (m->wb) cudaFree(m->wb);
     if (m->w3) cudaFree(m->w3);
@@ -581,13 +607,13 @@ static boa_status gemm(boa_model* m, int cls, const float* A, const float* Wt, c
     const long long waves = 2LL * m->num_sms;
     if (N >= 128 && t128 >= waves) {
         dim3 grid((N + 127) / 128, (unsigned)((M + 127) / 128));
-        k_gemm_fp32<128, 128, EPI><<<grid, kGemmThreads, 0, m->stream>>>(A, Wt, bias, C, (int)M, N, K);
+        k_gemm_fp32<128, 128, EPI><<<grid, kGemmThreads, 0, m->v.stream>>>(A, Wt, bias, C, (int)M, N, K);
     } else if (t12864 >= waves) {
         dim3 grid((N + 63) / 64, (unsigned)((M + 127) / 128));
-        k_gemm_fp32<128, 64, EPI><<<grid, kGemmThreads, 0, m->stream>>>(A, Wt, bias, C, (int)M, N, K);
+        k_gemm_fp32<128, 64, EPI><<<grid, kGemmThreads, 0, m->v.stream>>>(A, Wt, bias, C, (int)M, N, K);
     } else {
         dim3 grid((N + 63) / 64, (unsigned)((M + 63) / 64));
-        k_gemm_fp32<64, 64, EPI><<<grid, kGemmThreads, 0, m->stream>>>(A, Wt, bias, C, (int)M, N, K);
+        k_gemm_fp32<64, 64, EPI><<<grid, kGemmThreads, 0, m->v.stream>>>(A, Wt, bias, C, (int)M, N, K);
     }
     return check_launch(m, "gemm");
 }
@@ -651,7 +677,7 @@ static void launch_tc_cfg(boa_model* m, dim3 grid, const CUtensorMap& ta, const 
         cudaFuncSetAttribute(k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L::kBytes);
     });
-    k_gemm_tc_bf16<BN, EPI, KIND, DEEP><<<grid, kTcThreads, L::kBytes, m->stream>>>(ta, tb, bias, C, outb, (int)M, N,
+    k_gemm_tc_bf16<BN, EPI, KIND, DEEP><<<grid, kTcThreads, L::kBytes, m->v.stream>>>(ta, tb, bias, C, outb, (int)M, N,
                                                                                     K, m->err.p, rs, cs);
 }
 
@@ -694,24 +720,23 @@ static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_
     if (M <= 0) return BOA_OK;
     if (N % 4 != 0 || K % 16 != 0 || K > 1024) return fail(BOA_ERR_FORMAT, "fp8 gemm shape N=%d K=%d unsupported", N, K);
     const int Kp = (K + 127) / 128 * 128;     // W is stored with the same zero padding
-    TRY(m->a8.ensure((size_t)M * Kp));
-    TRY(m->a8s.ensure((size_t)M));
+    if (!m->v.a8 || (size_t)Kp > m->kp8) return fail(BOA_ERR_ARG, "FP8 activation scratch not sized for K=%d", K);
     {
         ProfScope pq(m, BOA_KC_OTHER, 3.0 * M * K, 5.0 * M * K + 4.0 * M);
-        k_quant_rows_e4m3<<<(unsigned)((M + 7) / 8), 256, 0, m->stream>>>(
-            A, reinterpret_cast<__nv_fp8_e4m3*>(m->a8.p), m->a8s.p, M, K, Kp);
+        k_quant_rows_e4m3<<<(unsigned)((M + 7) / 8), 256, 0, m->v.stream>>>(
+            A, reinterpret_cast<__nv_fp8_e4m3*>(m->v.a8), m->v.a8s, M, K, Kp);
     }
     TRY(check_launch(m, "quant_rows"));
     const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
     ProfScope ps(m, cls, 2.0 * M * N * K, ((double)M * K + (double)K * N) + 4.0 * (double)M * N * (resid ? 2 : 1));
     const int BN = tc_bn(N);
     CUtensorMap ta, tb;
-    TRY(tmap_2d(m, m->a8.p, (uint64_t)M, (uint64_t)Kp, kTcBM, 1, &ta));
+    TRY(tmap_2d(m, m->v.a8, (uint64_t)M, (uint64_t)Kp, kTcBM, 1, &ta));
     TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)Kp, (uint32_t)BN, 1, &tb));
     switch (BN) {
-        case 48: launch_tc<48, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->a8s.p, wscale); break;
-        case 64: launch_tc<64, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->a8s.p, wscale); break;
-        default: launch_tc<128, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->a8s.p, wscale); break;
+        case 48: launch_tc<48, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
+        case 64: launch_tc<64, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
+        default: launch_tc<128, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
     }
     return check_launch(m, "gemm_f8");
 }
@@ -725,7 +750,7 @@ static void launch_t3_cfg(boa_model* m, dim3 grid, const CUtensorMap& ta, const 
         cudaFuncSetAttribute(k_gemm_tc_tf32x3<BN, EPI, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L::kBytes);
     });
-    k_gemm_tc_tf32x3<BN, EPI, DEEP><<<grid, kT3Threads, L::kBytes, m->stream>>>(ta, th, tl, bias, C, (int)M, N, K,
+    k_gemm_tc_tf32x3<BN, EPI, DEEP><<<grid, kT3Threads, L::kBytes, m->v.stream>>>(ta, th, tl, bias, C, (int)M, N, K,
                                                                                 m->err.p);
 }
 
@@ -762,18 +787,18 @@ template <int VPT>
 static void launch_embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc, const DevLayer& L0) {
     const long long rows = (long long)S * Tc;
     const bool tc = m->precision == BOA_PREC_BF16;
-    k_embed_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->stream>>>(ts, S, Tc, m->embed, L0.ln_a_w, L0.ln_a_b,
-                                                                      m->x.p, m->xn.p, tc ? m->xn_b.p : nullptr);
+    k_embed_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->v.stream>>>(ts, S, Tc, m->embed, L0.ln_a_w, L0.ln_a_b,
+                                                                        m->v.x, m->v.xn, tc ? m->v.xn_b : nullptr);
 }
 
 template <int VPT>
 static void launch_ln_ln(boa_model* m, long long rows, const DevLayer& L, const DevLayer* next) {
     const bool tc = m->precision == BOA_PREC_BF16;
     // the BF16 copy of x feeds the head (last block) or the next block's FFN
-    __nv_bfloat16* xb = (tc && (!next || m->F)) ? m->x_b.p : nullptr;
-    k_ln_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->stream>>>(
-        rows, m->x.p, L.ln_b_w, L.ln_b_b, next ? next->ln_a_w : nullptr, next ? next->ln_a_b : nullptr, m->xn.p, xb,
-        tc ? m->xn_b.p : nullptr);
+    __nv_bfloat16* xb = (tc && (!next || m->F)) ? m->v.x_b : nullptr;
+    k_ln_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->v.stream>>>(
+        rows, m->v.x, L.ln_b_w, L.ln_b_b, next ? next->ln_a_w : nullptr, next ? next->ln_a_b : nullptr, m->v.xn, xb,
+        tc ? m->v.xn_b : nullptr);
 }
 
 static boa_status embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc) {
@@ -799,24 +824,16 @@ static boa_status ln_ln(boa_model* m, long long rows, int l) {
     return check_launch(m, "ln_ln");
 }
 
-// Decode-step scan variant, a tuning knob (boa_autotune) that never changes
-// a result: 0 = four channels per thread, one stream per CTA (k_scan_step4);
-// G > 0 = one channel per thread, G streams per CTA (k_scan).
-static int stream_group(const boa_model* m, int S, int Tc) {
-    if (Tc != 1) return 1;
-    return m->scan_group;
-}
-
 static boa_status conv(boa_model* m, int l, int S, int Tc) {
     const DevLayer& L = m->layers[l];
     const int G = 1;                                  // one stream per thread: more loads in flight
     dim3 grid((m->E + 511) / 512, (S + G - 1) / G);   // 4 channels per thread
-    float* win = m->conv.p + (size_t)l * S * (m->K - 1) * m->E;
+    float* win = m->v.conv + (size_t)l * m->v.S_all * (m->K - 1) * m->E;
     const double rows = (double)S * Tc;
     ProfScope ps(m, BOA_KC_CONV, rows * m->E * (2.0 * m->K + 4), 4.0 * (2 * rows * m->E + 2.0 * S * (m->K - 1) * m->E));
-    __nv_bfloat16* ub = m->precision == BOA_PREC_BF16 ? m->u_b.p : nullptr;
+    __nv_bfloat16* ub = m->precision == BOA_PREC_BF16 ? m->v.u_b : nullptr;
 #define CONV_CASE(KK, GG) \
-    k_conv_silu<KK, GG><<<grid, 128, 0, m->stream>>>(m->xz.p, m->E, L.conv_w, L.conv_b, win, m->u.p, ub, S, Tc)
+    k_conv_silu<KK, GG><<<grid, 128, 0, m->v.stream>>>(m->v.xz, m->E, L.conv_w, L.conv_b, win, m->v.u, ub, S, Tc)
     if (G == 8) {
         switch (m->K) { case 2: CONV_CASE(2, 8); break; case 3: CONV_CASE(3, 8); break; default: CONV_CASE(4, 8); break; }
     } else {
@@ -826,38 +843,89 @@ static boa_status conv(boa_model* m, int l, int S, int Tc) {
     return check_launch(m, "conv");
 }
 
+// Decode-step scan kernels (scan_variant, a tuning knob of boa_autotune; none
+// changes a result, every variant performs k_scan's per-channel arithmetic):
+//   0  persistent, bulk-copy fed (k_scan_step_bulk)
+//   1  four channels per thread, one stream per CTA (k_scan_step4)
+//   2  one channel per thread, one stream per CTA (k_scan, G = 1)
+//   3  one channel per thread, eight streams per CTA (k_scan, G = 8)
+// Chunks of more than one step (compression) always take k_scan with G = 1.
+
+// Ring stages and CTAs per SM for k_scan_step_bulk: about 512 threads per SM
+// and at least two stages per CTA within 227 KB of shared memory.
+static void step_bulk_shape(int E, int N, int r, int& cps, int& stages) {
+    const size_t stage = 4 * (size_t)step_stage_floats(N, r, E);
+    const int threads = E / 2;
+    cps = std::max(1, std::min(8, 512 / threads));
+    const size_t budget = 227 * 1024;
+    while (cps > 1 && (2 * stage + 1024) * cps > budget) cps--;
+    stages = (int)std::min<size_t>(kStepMaxStages, (budget / cps - 1024) / stage);
+}
+
+template <int RR>
+static boa_status launch_step_bulk(boa_model* m, const DevLayer& L, float* hs, __nv_bfloat16* ygb, int S) {
+    int cps = 1, stages = 2;
+    step_bulk_shape(m->E, m->N, m->r, cps, stages);
+    const size_t smem = (size_t)stages * 4 * step_stage_floats(m->N, RR, m->E);
+    // opt in to the largest dynamic shared memory this kernel can have
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        cudaFuncAttributes fa{};
+        int dev = 0, optin = 0;
+        attr_err = cudaFuncGetAttributes(&fa, k_scan_step_bulk<16, RR>);
+        if (attr_err == cudaSuccess) attr_err = cudaGetDevice(&dev);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(k_scan_step_bulk<16, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            optin - (int)fa.sharedSizeBytes);
+    });
+    if (attr_err != cudaSuccess) return fail(BOA_ERR_CUDA, "decode scan set-up: %s", cudaGetErrorString(attr_err));
+    const int grid = (int)std::min<long long>(S, (long long)m->num_sms * cps);
+    k_scan_step_bulk<16, RR><<<grid, m->E / 2, smem, m->v.stream>>>(m->v.u, m->v.xz, m->v.dbc, L.dt_w, L.dt_b, L.A2,
+                                                                   L.D, hs, m->v.yg, ygb, m->E, S, stages, m->err.p);
+    return BOA_OK;
+}
+
 static boa_status scan(boa_model* m, int l, int S, int Tc) {
     const DevLayer& L = m->layers[l];
-    const int G = stream_group(m, S, Tc);
-    float* hs = m->h.p + (size_t)l * S * m->N * m->E;
+    float* hs = m->v.h + (size_t)l * m->v.S_all * m->N * m->E;
     const double rows = (double)S * Tc;
     ProfScope ps(m, BOA_KC_SCAN, rows * m->E * (2.0 * m->r + 5.0 * m->N + 12),
                  4.0 * (rows * (3.0 * m->E + m->R2) + 2.0 * S * m->N * m->E));
-    __nv_bfloat16* ygb = m->precision == BOA_PREC_BF16 ? m->yg_b.p : nullptr;
-    if (G == 0 && Tc == 1) {
+    __nv_bfloat16* ygb = m->precision == BOA_PREC_BF16 ? m->v.yg_b : nullptr;
+    const int v = Tc == 1 ? m->scan_variant : 2;
+    if (v == 0) {
+        switch (m->r) {
+            case 4: TRY(launch_step_bulk<4>(m, L, hs, ygb, S)); break;
+            case 8: TRY(launch_step_bulk<8>(m, L, hs, ygb, S)); break;
+            default: TRY(launch_step_bulk<16>(m, L, hs, ygb, S)); break;
+        }
+        return check_launch(m, "scan_step_bulk");
+    }
+    if (v == 1) {
         dim3 g4((m->E + 4 * kScanThreads - 1) / (4 * kScanThreads), S);
 #define STEP4_CASE(RR)                                                                                       \
-    k_scan_step4<16, RR><<<g4, kScanThreads, 0, m->stream>>>(m->u.p, m->xz.p, m->dbc.p, L.dt_w, L.dt_b, L.A2, \
-                                                             L.D, hs, m->yg.p, ygb, m->E)
+    k_scan_step4<16, RR><<<g4, kScanThreads, 0, m->v.stream>>>(m->v.u, m->v.xz, m->v.dbc, L.dt_w, L.dt_b, L.A2, \
+                                                               L.D, hs, m->v.yg, ygb, m->E)
         switch (m->r) { case 4: STEP4_CASE(4); break; case 8: STEP4_CASE(8); break; default: STEP4_CASE(16); break; }
 #undef STEP4_CASE
         return check_launch(m, "scan_step4");
     }
-    const int Gd = std::max(G, 1);
-    dim3 grid((m->E + kScanThreads - 1) / kScanThreads, (S + Gd - 1) / Gd);
+    const int G = v == 3 ? 8 : 1;
+    dim3 grid((m->E + kScanThreads - 1) / kScanThreads, (S + G - 1) / G);
 #define SCAN_CASE(RR, GG)                                                                                         \
-    k_scan<16, RR, GG><<<grid, kScanThreads, 0, m->stream>>>(m->u.p, m->xz.p, m->dbc.p, L.dt_w, L.dt_b, L.A2, L.D, \
-                                                             hs, m->yg.p, ygb, m->E, S, Tc)
-#define SCAN_G(GG) \
-    switch (m->r) { case 4: SCAN_CASE(4, GG); break; case 8: SCAN_CASE(8, GG); break; default: SCAN_CASE(16, GG); break; }
-    switch (G) {
-        case 2: SCAN_G(2); break;
-        case 4: SCAN_G(4); break;
-        case 8: SCAN_G(8); break;
-        case 16: SCAN_G(16); break;
-        default: SCAN_G(1); break;
+    k_scan<16, RR, GG><<<grid, kScanThreads, 0, m->v.stream>>>(m->v.u, m->v.xz, m->v.dbc, L.dt_w, L.dt_b, L.A2, L.D, \
+                                                               hs, m->v.yg, ygb, m->E, S, Tc)
+#define SCAN_R(GG)                      \
+    switch (m->r) {                     \
+        case 4: SCAN_CASE(4, GG); break; \
+        case 8: SCAN_CASE(8, GG); break; \
+        default: SCAN_CASE(16, GG); break; \
     }
-#undef SCAN_G
+    if (G == 8) { SCAN_R(8) } else { SCAN_R(1) }
+#undef SCAN_R
 #undef SCAN_CASE
     return check_launch(m, "scan");
 }
@@ -874,68 +942,70 @@ static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc, bool 
         const DevLayer& L = m->layers[l];
         if (tc) {
             const auto& B = m->blayers[l];
-            TRY(gemm_tc<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn_b.p, B.in_w, nullptr, m->xz.p, nullptr, rows, 2 * E, d));
+            TRY(gemm_tc<kEpiStore>(m, BOA_KC_GEMM_IN, m->v.xn_b, B.in_w, nullptr, m->v.xz, nullptr, rows, 2 * E, d));
             TRY(conv(m, l, S, Tc));
-            TRY(gemm_tc<kEpiStore>(m, BOA_KC_GEMM_X, m->u_b.p, B.x_w, nullptr, m->dbc.p, nullptr, rows, m->R2, E));
+            TRY(gemm_tc<kEpiStore>(m, BOA_KC_GEMM_X, m->v.u_b, B.x_w, nullptr, m->v.dbc, nullptr, rows, m->R2, E));
             TRY(scan(m, l, S, Tc));
-            TRY(gemm_tc<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg_b.p, B.out_w, nullptr, m->x.p, m->F ? m->x_b.p : nullptr,
+            TRY(gemm_tc<kEpiResid>(m, BOA_KC_GEMM_OUT, m->v.yg_b, B.out_w, nullptr, m->v.x, m->F ? m->v.x_b : nullptr,
                                    rows, d, E));
             if (m->F) {
-                TRY(gemm_tc<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x_b.p, B.w1, L.b1, m->hid.p, m->hid_b.p, rows, m->F, d));
-                TRY(gemm_tc<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid_b.p, B.w2, L.b2, m->x.p, nullptr, rows, d, m->F));
+                TRY(gemm_tc<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->v.x_b, B.w1, L.b1, m->v.hid, m->v.hid_b, rows, m->F, d));
+                TRY(gemm_tc<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->v.hid_b, B.w2, L.b2, m->v.x, nullptr, rows, d, m->F));
             }
         } else if (m->precision == BOA_PREC_FP8) {
             const auto& Q = m->qlayers[l];
-            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn.p, Q.in_w, Q.in_s, nullptr, m->xz.p, rows, 2 * E, d));
+            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_IN, m->v.xn, Q.in_w, Q.in_s, nullptr, m->v.xz, rows, 2 * E, d));
             TRY(conv(m, l, S, Tc));
-            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_X, m->u.p, Q.x_w, Q.x_s, nullptr, m->dbc.p, rows, m->R2, E));
+            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_X, m->v.u, Q.x_w, Q.x_s, nullptr, m->v.dbc, rows, m->R2, E));
             TRY(scan(m, l, S, Tc));
-            TRY(gemm_f8<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg.p, Q.out_w, Q.out_s, nullptr, m->x.p, rows, d, E));
+            TRY(gemm_f8<kEpiResid>(m, BOA_KC_GEMM_OUT, m->v.yg, Q.out_w, Q.out_s, nullptr, m->v.x, rows, d, E));
             if (m->F) {
-                TRY(gemm_f8<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x.p, Q.w1, Q.w1_s, L.b1, m->hid.p, rows, m->F, d));
-                TRY(gemm_f8<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid.p, Q.w2, Q.w2_s, L.b2, m->x.p, rows, d, m->F));
+                TRY(gemm_f8<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->v.x, Q.w1, Q.w1_s, L.b1, m->v.hid, rows, m->F, d));
+                TRY(gemm_f8<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->v.hid, Q.w2, Q.w2_s, L.b2, m->v.x, rows, d, m->F));
             }
         } else if (m->precision == BOA_PREC_TF32X3) {
             const auto& T = m->tlayers[l];
-            TRY(gemm_t3<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn.p, T.in_hi, T.in_lo, nullptr, m->xz.p, rows, 2 * E, d));
+            TRY(gemm_t3<kEpiStore>(m, BOA_KC_GEMM_IN, m->v.xn, T.in_hi, T.in_lo, nullptr, m->v.xz, rows, 2 * E, d));
             TRY(conv(m, l, S, Tc));
-            TRY(gemm_t3<kEpiStore>(m, BOA_KC_GEMM_X, m->u.p, T.x_hi, T.x_lo, nullptr, m->dbc.p, rows, m->R2, E));
+            TRY(gemm_t3<kEpiStore>(m, BOA_KC_GEMM_X, m->v.u, T.x_hi, T.x_lo, nullptr, m->v.dbc, rows, m->R2, E));
             TRY(scan(m, l, S, Tc));
-            TRY(gemm_t3<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg.p, T.out_hi, T.out_lo, nullptr, m->x.p, rows, d, E));
+            TRY(gemm_t3<kEpiResid>(m, BOA_KC_GEMM_OUT, m->v.yg, T.out_hi, T.out_lo, nullptr, m->v.x, rows, d, E));
             if (m->F) {
-                TRY(gemm_t3<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x.p, T.w1_hi, T.w1_lo, L.b1, m->hid.p, rows, m->F, d));
-                TRY(gemm_t3<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid.p, T.w2_hi, T.w2_lo, L.b2, m->x.p, rows, d, m->F));
+                TRY(gemm_t3<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->v.x, T.w1_hi, T.w1_lo, L.b1, m->v.hid, rows, m->F, d));
+                TRY(gemm_t3<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->v.hid, T.w2_hi, T.w2_lo, L.b2, m->v.x, rows, d, m->F));
             }
         } else {
-            TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_IN, m->xn.p, L.in_wt, nullptr, m->xz.p, rows, 2 * E, d));
+            TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_IN, m->v.xn, L.in_wt, nullptr, m->v.xz, rows, 2 * E, d));
             TRY(conv(m, l, S, Tc));
-            TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_X, m->u.p, L.x_wt, nullptr, m->dbc.p, rows, m->R2, E));
+            TRY(gemm<kEpiStore>(m, BOA_KC_GEMM_X, m->v.u, L.x_wt, nullptr, m->v.dbc, rows, m->R2, E));
             TRY(scan(m, l, S, Tc));
-            TRY(gemm<kEpiResid>(m, BOA_KC_GEMM_OUT, m->yg.p, L.out_wt, nullptr, m->x.p, rows, d, E));
+            TRY(gemm<kEpiResid>(m, BOA_KC_GEMM_OUT, m->v.yg, L.out_wt, nullptr, m->v.x, rows, d, E));
             if (m->F) {
-                TRY(gemm<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->x.p, L.w1t, L.b1, m->hid.p, rows, m->F, d));
-                TRY(gemm<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->hid.p, L.w2t, L.b2, m->x.p, rows, d, m->F));
+                TRY(gemm<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->v.x, L.w1t, L.b1, m->v.hid, rows, m->F, d));
+                TRY(gemm<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->v.hid, L.w2t, L.b2, m->v.x, rows, d, m->F));
             }
         }
         TRY(ln_ln(m, rows, l));
     }
-    if (tc) return gemm_tc<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x_b.p, m->head_wb, m->head_b, m->logits.p, nullptr, rows, 256, d);
+    if (tc) return gemm_tc<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->v.x_b, m->head_wb, m->head_b, m->v.logits, nullptr, rows, 256, d);
     if (m->precision == BOA_PREC_TF32X3)
-        return gemm_t3<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_hi, m->head_lo, m->head_b, m->logits.p, rows, 256, d);
+        return gemm_t3<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->v.x, m->head_hi, m->head_lo, m->head_b, m->v.logits, rows, 256, d);
     if (m->precision == BOA_PREC_FP8)
-        return gemm_f8<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_w8, m->head_s, m->head_b, m->logits.p, rows, 256, d);
-    return gemm<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->x.p, m->head_wt, m->head_b, m->logits.p, rows, 256, d);
+        return gemm_f8<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->v.x, m->head_w8, m->head_s, m->head_b, m->v.logits, rows, 256, d);
+    return gemm<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->v.x, m->head_wt, m->head_b, m->v.logits, rows, 256, d);
 }
 
-// Tensor-core waits that timed out leave a nonzero code in m->err.
+// Bounded waits that timed out (tensor-core pipelines, the bulk-copy scan)
+// leave a nonzero code in m->err.
 static boa_status check_tc_error(boa_model* m) {
-    if (m->precision == BOA_PREC_FP32) return BOA_OK;
+    if (!m->err.p) return BOA_OK;
     int h = 0;
     CU(cudaMemcpyAsync(&h, m->err.p, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     if (h) {
         cudaMemsetAsync(m->err.p, 0, sizeof(int), m->stream);
-        return fail(BOA_ERR_CUDA, "tensor-core GEMM pipeline wait timed out (code %d)", h);
+        return fail(BOA_ERR_CUDA, "a pipeline wait on the device timed out (code %d: %s)", h,
+                    h == 3 ? "decode scan bulk copy" : "tensor-core GEMM");
     }
     return BOA_OK;
 }
@@ -950,7 +1020,7 @@ static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
     TRY(m->yg.ensure(rows * E));
     TRY(m->logits.ensure(rows * 256));
     if (m->F) TRY(m->hid.ensure(rows * m->F));
-    if (m->precision != BOA_PREC_FP32 && !m->err.p) {
+    if (!m->err.p) {
         TRY(m->err.ensure(1));
         CU(cudaMemset(m->err.p, 0, sizeof(int)));
     }
@@ -960,10 +1030,12 @@ static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
         TRY(m->yg_b.ensure(rows * E));
         TRY(m->x_b.ensure(rows * d));
         if (m->F) TRY(m->hid_b.ensure(rows * m->F));
-        if (!m->err.p) {
-            TRY(m->err.ensure(1));
-            CU(cudaMemset(m->err.p, 0, sizeof(int)));
-        }
+    }
+    if (m->precision == BOA_PREC_FP8) {
+        // E4M3 copies of a GEMM's activation rows, K padded to 128
+        m->kp8 = (std::max<size_t>({d, E, (size_t)m->F}) + 127) / 128 * 128;
+        TRY(m->a8.ensure(rows * m->kp8));
+        TRY(m->a8s.ensure(rows));
     }
     TRY(m->h.ensure((size_t)m->nl * S * m->N * E));
     TRY(m->conv.ensure((size_t)m->nl * S * (m->K - 1) * E));
@@ -971,6 +1043,59 @@ static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
     TRY(m->slots.ensure(S));
     TRY(m->slot_beg.ensure(S + 1));
     return BOA_OK;
+}
+
+// Point the launchers at slots [s0, ...) of an S_all-slot batch with Tc rows
+// per slot, launching on stream st.
+static void bind_view(boa_model* m, size_t s0, size_t Tc, size_t S_all, cudaStream_t st) {
+    View& v = m->v;
+    const size_t r0 = s0 * Tc;
+    auto at = [r0](auto* p, size_t per) { return p ? p + r0 * per : p; };
+    v.x = at(m->x.p, m->d);
+    v.xn = at(m->xn.p, m->d);
+    v.xz = at(m->xz.p, 2 * (size_t)m->E);
+    v.u = at(m->u.p, m->E);
+    v.dbc = at(m->dbc.p, m->R2);
+    v.yg = at(m->yg.p, m->E);
+    v.logits = at(m->logits.p, 256);
+    v.hid = at(m->hid.p, m->F);
+    v.xn_b = at(m->xn_b.p, m->d);
+    v.u_b = at(m->u_b.p, m->E);
+    v.yg_b = at(m->yg_b.p, m->E);
+    v.x_b = at(m->x_b.p, m->d);
+    v.hid_b = at(m->hid_b.p, m->F);
+    v.a8 = at(m->a8.p, m->kp8);
+    v.a8s = at(m->a8s.p, 1);
+    v.h = m->h.p ? m->h.p + s0 * m->N * m->E : nullptr;
+    v.conv = m->conv.p ? m->conv.p + s0 * (m->K - 1) * m->E : nullptr;
+    v.slots = m->slots.p ? m->slots.p + s0 : nullptr;
+    v.st = m->st.p ? m->st.p + s0 : nullptr;
+    v.slot_beg = m->slot_beg.p ? m->slot_beg.p + s0 : nullptr;
+    v.S_all = S_all;
+    v.stream = st;
+}
+
+// Streams and events for P decode lanes (created once, outside any capture).
+static boa_status ensure_lanes(boa_model* m, int P) {
+    while ((int)m->lane_streams.size() < P) {
+        cudaStream_t ls;
+        CU(cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking));
+        m->lane_streams.push_back(ls);
+    }
+    while ((int)m->lane_events.size() < P + 1) {
+        cudaEvent_t e;
+        CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        m->lane_events.push_back(e);
+    }
+    return BOA_OK;
+}
+
+// Decode lanes: the slots split into P contiguous groups whose step loops
+// are independent (a slot's rows, state and coder touch no other slot), so
+// each group's launches can go to its own stream and overlap the others'.
+static int decode_lanes(const boa_model* m, int S) {
+    const int P = m->decode_lanes > 0 ? m->decode_lanes : (S >= 2048 ? 2 : 1);
+    return std::max(1, std::min(P, S));
 }
 
 static boa_status ensure_streams(boa_model* m, size_t n) {
@@ -1087,12 +1212,13 @@ static StreamTable stream_table(boa_model* m, bool decoding) {
     return tb;
 }
 
-static SlotMem slot_mem(boa_model* m, int S) {
+// The bound view's per-slot model state, for kernels that reset a slot.
+static SlotMem slot_mem(const boa_model* m) {
     SlotMem sm;
-    sm.h = m->h.p;
-    sm.conv = m->conv.p;
+    sm.h = m->v.h;
+    sm.conv = m->v.conv;
     sm.layers = m->nl;
-    sm.S = S;
+    sm.S = (int)m->v.S_all;
     sm.h_per = m->N * m->E;
     sm.conv_per = (m->K - 1) * m->E;
     return sm;
@@ -1130,8 +1256,9 @@ static boa_status compress_impl(boa_model* m, size_t n, const uint8_t* d_in, con
     TRY(upload_index(m, n, in_off, out_off, lens.data()));
     TRY(upload_schedule(m, sc));
     TRY(zero_state(m, S));
+    bind_view(m, 0, Tc, S, m->stream);
     StreamTable tb = stream_table(m, false);
-    SlotMem mem = slot_mem(m, S);
+    SlotMem mem = slot_mem(m);
     const int tb128 = 128;
     k_enc_trivial<<<(unsigned)((n + tb128 - 1) / tb128), tb128, 0, m->stream>>>((int)n, d_in, tb, d_out);
     TRY(check_launch(m, "enc_trivial"));
@@ -1142,6 +1269,8 @@ static boa_status compress_impl(boa_model* m, size_t n, const uint8_t* d_in, con
         TRY(check_launch(m, "enc_slots"));
         TokenSrc ts{d_in, m->in_off.p, m->lens.p, m->slots.p};
         for (uint64_t c = 0; c < chunks; c++) {
+            m->prof_steps[0][0] += m->prof_on ? 1 : 0;
+            m->prof_steps[0][1]++;
             TRY(forward(m, ts, S, Tc));
             {
                 ProfScope ps(m, BOA_KC_ENCODE, (double)S * Tc * 256 * 8, (double)S * Tc * (256 * 4 + 2));
@@ -1168,15 +1297,15 @@ static boa_status compress_impl(boa_model* m, size_t n, const uint8_t* d_in, con
 template <int VPT>
 static void launch_dec_init(boa_model* m, int S, const uint8_t* cin, const StreamTable& tb, uint8_t* out,
                             const NextEmbed& ne) {
-    k_dec_slots_init<VPT><<<(unsigned)((S + 3) / 4), 128, 0, m->stream>>>(S, m->sched.p, m->slot_beg.p, m->slots.p,
-                                                                         m->st.p, cin, tb, out, ne);
+    k_dec_slots_init<VPT><<<(unsigned)((S + 3) / 4), 128, 0, m->v.stream>>>(S, m->sched.p, m->v.slot_beg, m->v.slots,
+                                                                           m->v.st, cin, tb, out, ne);
 }
 
 template <int VPT>
 static void launch_decode(boa_model* m, int S, const uint8_t* cin, const StreamTable& tb, uint8_t* out,
                           const NextEmbed& ne, const SlotMem& mem) {
-    k_decode<VPT><<<(unsigned)((S + 3) / 4), 128, 0, m->stream>>>(m->logits.p, S, m->sched.p, m->slot_beg.p,
-                                                                 m->slots.p, m->st.p, cin, tb, out, ne, mem);
+    k_decode<VPT><<<(unsigned)((S + 3) / 4), 128, 0, m->v.stream>>>(m->v.logits, S, m->sched.p, m->v.slot_beg,
+                                                                   m->v.slots, m->v.st, cin, tb, out, ne, mem);
 }
 
 static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, const uint64_t* in_off,
@@ -1208,51 +1337,88 @@ static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, c
     TRY(upload_index(m, n, in_off, out_off, lens, csz.data()));
     TRY(upload_schedule(m, sc));
     TRY(zero_state(m, S));
+    const int P = decode_lanes(m, S);
+    TRY(ensure_lanes(m, P));
+    bind_view(m, 0, 1, S, m->stream);
     StreamTable tb = stream_table(m, true);
-    SlotMem mem = slot_mem(m, S);
     const DevLayer& L0 = m->layers[0];
-    NextEmbed ne{m->embed, L0.ln_a_w, L0.ln_a_b, m->x.p, m->xn.p,
-                 m->precision == BOA_PREC_BF16 ? m->xn_b.p : nullptr};
+    // the next step's input rows of the bound view's slots
+    auto next_embed = [&] {
+        return NextEmbed{m->embed, L0.ln_a_w, L0.ln_a_b, m->v.x, m->v.xn,
+                         m->precision == BOA_PREC_BF16 ? m->v.xn_b : nullptr};
+    };
     const int tb128 = 128;
     k_dec_trivial<<<(unsigned)((n + tb128 - 1) / tb128), tb128, 0, m->stream>>>((int)n, d_in, tb, d_out);
     TRY(check_launch(m, "dec_trivial"));
     if (sc.S > 0) {
+        const NextEmbed ne0 = next_embed();
         switch (m->d) {
-            case 64: launch_dec_init<2>(m, S, d_in, tb, d_out, ne); break;
-            case 128: launch_dec_init<4>(m, S, d_in, tb, d_out, ne); break;
-            default: launch_dec_init<8>(m, S, d_in, tb, d_out, ne); break;
+            case 64: launch_dec_init<2>(m, S, d_in, tb, d_out, ne0); break;
+            case 128: launch_dec_init<4>(m, S, d_in, tb, d_out, ne0); break;
+            default: launch_dec_init<8>(m, S, d_in, tb, d_out, ne0); break;
         }
         TRY(check_launch(m, "dec_init"));
-        TokenSrc ts{nullptr, m->in_off.p, m->lens.p, m->slots.p};
-        // One decode step: every argument is fixed for the whole call (slot
-        // positions live in device memory), so without kernel profiling the
-        // step loop runs as a CUDA graph of kGraphSteps steps.
-        auto step = [&](uint64_t t) -> boa_status {
-            m->prof_step = (t % (uint64_t)m->prof_stride) == 0;
-            TRY(forward(m, ts, S, 1, /*embedded=*/true));
+        // One decode step of lane p (slots [S p / P, S (p + 1) / P)) on stream ls.
+        auto lane_step = [&](int p, cudaStream_t ls) -> boa_status {
+            const int s0 = (int)((long long)S * p / P), n_p = (int)((long long)S * (p + 1) / P) - s0;
+            bind_view(m, s0, 1, S, ls);
+            TokenSrc ts{nullptr, m->in_off.p, m->lens.p, m->v.slots};
+            TRY(forward(m, ts, n_p, 1, /*embedded=*/true));
+            const NextEmbed ne = next_embed();
+            const SlotMem mem = slot_mem(m);
             {
-                ProfScope ps(m, BOA_KC_DECODE, (double)S * 256 * 8, (double)S * (256 * 4 + 2 + 8.0 * m->d));
+                ProfScope ps(m, BOA_KC_DECODE, (double)n_p * 256 * 8, (double)n_p * (256 * 4 + 2 + 8.0 * m->d));
                 switch (m->d) {
-                    case 64: launch_decode<2>(m, S, d_in, tb, d_out, ne, mem); break;
-                    case 128: launch_decode<4>(m, S, d_in, tb, d_out, ne, mem); break;
-                    default: launch_decode<8>(m, S, d_in, tb, d_out, ne, mem); break;
+                    case 64: launch_decode<2>(m, n_p, d_in, tb, d_out, ne, mem); break;
+                    case 128: launch_decode<4>(m, n_p, d_in, tb, d_out, ne, mem); break;
+                    default: launch_decode<8>(m, n_p, d_in, tb, d_out, ne, mem); break;
                 }
             }
             return check_launch(m, "decode");
         };
-        uint64_t t = 0;
+        // `count` steps.  Timed steps run the lanes one after another on the
+        // model's stream (one event pair per launch); otherwise each lane's
+        // steps go to its own stream between a fork and a join, so one lane's
+        // memory-bound scan overlaps another's projections.
+        auto steps_block = [&](uint64_t count, bool timed) -> boa_status {
+            m->prof_step = timed;
+            m->prof_steps[1][0] += timed ? count : 0;
+            m->prof_steps[1][1] += count;
+            if (P == 1 || timed) {
+                for (uint64_t k = 0; k < count; k++)
+                    for (int p = 0; p < P; p++) TRY(lane_step(p, m->stream));
+                return BOA_OK;
+            }
+            CU(cudaEventRecord(m->lane_events[0], m->stream));
+            for (int p = 0; p < P; p++) {
+                CU(cudaStreamWaitEvent(m->lane_streams[p], m->lane_events[0], 0));
+                for (uint64_t k = 0; k < count; k++) TRY(lane_step(p, m->lane_streams[p]));
+                CU(cudaEventRecord(m->lane_events[1 + p], m->lane_streams[p]));
+                CU(cudaStreamWaitEvent(m->stream, m->lane_events[1 + p], 0));
+            }
+            return BOA_OK;
+        };
+        // Without profiling every step is eager or in a CUDA graph of
+        // kGraphSteps steps (all its arguments are fixed for the call: slot
+        // positions live in device memory).  With profiling, graphs still
+        // run and one eager timed step precedes each graph launch; without
+        // graphs every prof_stride-th step is timed.
         const uint64_t kGraphSteps = 32;
-        if (!m->prof_on && m->use_graphs && steps >= 2 * kGraphSteps) {
+        uint64_t t = 0;
+        if (m->use_graphs && steps >= 2 * kGraphSteps) {
             // one eager step first: lazily created resources (workspace
-            // growth, kernel attributes) must not be created under capture
-            TRY(step(t++));
+            // growth, kernel attributes, tensor maps) must not be created
+            // under capture
+            TRY(steps_block(1, m->prof_on));
+            t++;
             cudaGraph_t g = nullptr;
             cudaGraphExec_t ge = nullptr;
             const uint64_t before = m->launches;
+            const uint64_t all_before = m->prof_steps[1][1];
             CU(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-            boa_status cs = BOA_OK;
-            for (uint64_t k = 0; k < kGraphSteps && cs == BOA_OK; k++) cs = step(k);
+            boa_status cs = steps_block(kGraphSteps, false);
             cudaError_t ce = cudaStreamEndCapture(m->stream, &g);
+            bind_view(m, 0, 1, S, m->stream);
             if (cs != BOA_OK) { if (g) cudaGraphDestroy(g); return cs; }
             if (ce != cudaSuccess) return fail(BOA_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
             ce = cudaGraphInstantiate(&ge, g, 0);
@@ -1260,17 +1426,26 @@ static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, c
             if (ce != cudaSuccess) return fail(BOA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
             const uint64_t per_graph = m->launches - before;
             m->launches = before;
-            for (; t + kGraphSteps <= steps; t += kGraphSteps) {
+            m->prof_steps[1][1] = all_before;
+            while (t + kGraphSteps <= steps) {
+                if (m->prof_on) {
+                    boa_status st = steps_block(1, true);
+                    if (st != BOA_OK) { cudaGraphExecDestroy(ge); return st; }
+                    if (++t + kGraphSteps > steps) break;
+                }
                 ce = cudaGraphLaunch(ge, m->stream);
                 if (ce != cudaSuccess) { cudaGraphExecDestroy(ge); return fail(BOA_ERR_CUDA, "graph launch: %s", cudaGetErrorString(ce)); }
                 m->launches += per_graph;
+                m->prof_steps[1][1] += kGraphSteps;
+                t += kGraphSteps;
             }
             CU(cudaStreamSynchronize(m->stream));
             cudaGraphExecDestroy(ge);
         }
-        for (; t < steps; t++) TRY(step(t));
+        for (; t < steps; t++) TRY(steps_block(1, m->prof_on && (t % (uint64_t)m->prof_stride) == 0));
         m->prof_step = true;
     }
+    bind_view(m, 0, 1, S, m->stream);
     TRY(m->h_u32.ensure(n));
     CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, n * 4, cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
@@ -1384,6 +1559,14 @@ extern "C" boa_status boa_profile_reset(boa_model* m) {
             m->prof_launches[ph][i] = 0;
             m->prof_ms[ph][i] = m->prof_flops[ph][i] = m->prof_bytes[ph][i] = 0.0;
         }
+    for (int ph = 0; ph < 2; ph++) m->prof_steps[ph][0] = m->prof_steps[ph][1] = 0;
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_profile_steps(const boa_model* m, int phase, uint64_t* timed, uint64_t* total) {
+    if (!m || phase < 0 || phase > 1) return fail(BOA_ERR_ARG, "bad argument");
+    if (timed) *timed = m->prof_steps[phase][0];
+    if (total) *total = m->prof_steps[phase][1];
     return BOA_OK;
 }
 
@@ -1431,6 +1614,23 @@ extern "C" boa_status boa_scan_train_bwd(size_t Bsz, size_t T, size_t E, size_t 
 
 // ------------------------------------------------------------ autotuner
 
+extern "C" boa_status boa_set_tuning(boa_model* m, const boa_tuning* t) {
+    if (!m || !t) return fail(BOA_ERR_ARG, "null argument");
+    if (t->max_rows < 1 || t->max_rows > (1u << 24)) return fail(BOA_ERR_ARG, "max_rows %zu out of range", t->max_rows);
+    if (t->scan_variant < 0 || t->scan_variant > 3) return fail(BOA_ERR_ARG, "scan_variant %d out of range", t->scan_variant);
+    if (t->decode_lanes < 0 || t->decode_lanes > 16) return fail(BOA_ERR_ARG, "decode_lanes %d out of range", t->decode_lanes);
+    m->max_rows = t->max_rows;
+    m->scan_variant = t->scan_variant;
+    m->decode_lanes = t->decode_lanes;
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_get_tuning(const boa_model* m, boa_tuning* out) {
+    if (!m || !out) return fail(BOA_ERR_ARG, "null argument");
+    *out = boa_tuning{m->max_rows, m->scan_variant, m->decode_lanes, 0.0, 0.0};
+    return BOA_OK;
+}
+
 extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream_len, boa_tuning* out) {
     if (!m || n_streams == 0 || stream_len < 2) return fail(BOA_ERR_ARG, "bad argument");
     CU(cudaSetDevice(m->device));
@@ -1468,7 +1668,7 @@ extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream
         return BOA_OK;
     };
     boa_status st = BOA_OK;
-    boa_tuning best{m->max_rows, m->scan_group, 1e30, 1e30};
+    boa_tuning best{m->max_rows, m->scan_variant, m->decode_lanes, 1e30, 1e30};
     const size_t rows_cand[] = {1u << 16, 1u << 17, 1u << 18, 1u << 19};
     for (size_t r : rows_cand) {
         if (st != BOA_OK) break;
@@ -1478,16 +1678,27 @@ extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream
         if (st == BOA_OK && ms < best.compress_ms) { best.compress_ms = ms; best.max_rows = r; }
     }
     m->max_rows = best.max_rows;
-    const int g_cand[] = {0, 1, 2, 4, 8, 16};
-    for (int g : g_cand) {
+    auto time_decode = [&](double& ms) {
+        return timed([&] { return decompress_impl(m, n, dout.p, out_off.data(), sizes.data(), lens.data(), ddec.p,
+                                                  in_off.data()); }, ms);
+    };
+    m->decode_lanes = 1;
+    for (int g = 0; g < 4; g++) {
         if (st != BOA_OK) break;
-        m->scan_group = g;
+        m->scan_variant = g;
         double ms = 0;
-        st = timed([&] { return decompress_impl(m, n, dout.p, out_off.data(), sizes.data(), lens.data(), ddec.p,
-                                                in_off.data()); }, ms);
-        if (st == BOA_OK && ms < best.decompress_ms) { best.decompress_ms = ms; best.scan_group = g; }
+        st = time_decode(ms);
+        if (st == BOA_OK && ms < best.decompress_ms) { best.decompress_ms = ms; best.scan_variant = g; best.decode_lanes = 1; }
     }
-    m->scan_group = best.scan_group;
+    m->scan_variant = best.scan_variant;
+    for (int p : {2, 4}) {
+        if (st != BOA_OK || (size_t)p > n) break;
+        m->decode_lanes = p;
+        double ms = 0;
+        st = time_decode(ms);
+        if (st == BOA_OK && ms < best.decompress_ms) { best.decompress_ms = ms; best.decode_lanes = p; }
+    }
+    m->decode_lanes = best.decode_lanes;
     m->prof_on = prof;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -1620,6 +1831,7 @@ extern "C" boa_status boa_debug_logprobs(boa_model* m, const uint8_t* stream, si
     uint64_t off[2] = {0, len}, lens1[1] = {len};
     TRY(upload_index(m, 1, off, off, lens1));
     TRY(zero_state(m, 1));
+    bind_view(m, 0, Tc, 1, m->stream);
     boa_status st = BOA_OK;
     cudaError_t e = cudaMemcpyAsync(m->d_in.p, stream, len, cudaMemcpyHostToDevice, m->stream);
     if (e != cudaSuccess) st = fail(BOA_ERR_CUDA, "%s", cudaGetErrorString(e));

@@ -52,22 +52,57 @@ def test_autotune_keeps_bytes(api, tiny_model_path):
     m = api.Model(tiny_model_path)
     before = m.compress(streams)
     t = m.autotune(len(streams), 1024)
-    assert t["max_rows"] in (1 << 16, 1 << 17, 1 << 18, 1 << 19) and t["scan_group"] in (0, 1, 2, 4, 8, 16)
+    assert t["max_rows"] in (1 << 16, 1 << 17, 1 << 18, 1 << 19) and t["scan_variant"] in (0, 1, 2, 3)
     after = m.compress(streams)
     assert after == before
     assert m.decompress(after, [len(s) for s in streams]) == streams
 
 
 def test_graph_and_eager_decode_agree(api, tiny_model_path):
-    """The decode step loop runs as CUDA graphs unless kernel profiling is on;
-    both give the same bytes."""
+    """The decode step loop runs as CUDA graphs of 32 steps; with kernel
+    profiling on, a timed eager step (lanes one after another) precedes each
+    graph launch.  Lanes on separate streams or not, the bytes agree, and
+    the step counts add up."""
     streams = [synth.records_stream(90 + i, 3000 + 11 * i) for i in range(5)]
     m = api.Model(tiny_model_path)
     comp = m.compress(streams)
     lens = [len(s) for s in streams]
     assert m.decompress(comp, lens) == streams        # graphs
-    m.profile(True, 1)
-    try:
-        assert m.decompress(comp, lens) == streams    # eager, profiled
-    finally:
-        m.profile(False)
+    for lanes in (1, 2):
+        m.set_tuning(1 << 18, 0, lanes)
+        m.profile(True, 1)
+        m.profile_reset()
+        try:
+            assert m.decompress(comp, lens) == streams
+            timed, total = m.profile_steps()["decompress"]
+            assert total == max(lens) - 1 and 0 < timed < total
+            assert m.profile_read()["decompress"]["scan"]["launches"] == timed * lanes * 2
+        finally:
+            m.profile(False)
+
+
+@pytest.mark.parametrize("d_model,expand,prec", [(64, 2, 0), (256, 2, 2), (64, 3, 1), (128, 4, 0)])
+def test_decode_scan_variants_agree(api, tmp_path, d_model, expand, prec):
+    """Every decode-step scan kernel (persistent bulk-copy fed, four channels
+    per thread, one or eight streams per CTA), with the slots split into one
+    to four lanes on separate streams, decodes the same bytes.  Many
+    short streams: more slots than the persistent grid, so its CTAs walk
+    several streams, with a ragged last round; model widths cover one to
+    eight CTAs per SM and two to four ring stages."""
+    shape = synth.ModelShape(d_model=d_model, n_layer=2, expand=expand)
+    path = synth.make_model_file(str(tmp_path / "v.boaw"), shape, seed=7)
+    g = np.random.default_rng(d_model + expand)
+    lens = g.integers(2, 90, size=2500)
+    buf = synth.atlas_table(int(lens.sum()), seed=11)
+    off = np.concatenate([[0], np.cumsum(lens)])
+    streams = [buf[off[i]:off[i + 1]] for i in range(len(lens))]
+    m = api.Model(path, precision=prec)
+    comp = m.compress(streams)
+    for v, lanes in ((0, 1), (0, 3), (1, 2), (2, 1), (3, 4)):
+        m.set_tuning(1 << 18, v, lanes)
+        assert m.tuning() == {"max_rows": 1 << 18, "scan_variant": v, "decode_lanes": lanes}
+        assert m.decompress(comp, [len(s) for s in streams]) == streams, (v, lanes)
+    with pytest.raises(api.BoaError):
+        m.set_tuning(1 << 18, 4)
+    with pytest.raises(api.BoaError):
+        m.set_tuning(1 << 18, 0, 17)
