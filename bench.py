@@ -213,11 +213,14 @@ def form_accuracy(streams, forms, path, n_lp=4, lp_len=256, n_gap=16, gap_len=20
     return out
 
 
-def form_speed(form, path, d_in, in_off, d_out, out_off, d_dec, lens, stream):
-    """One warm-up and one timed step of another precision form."""
+def form_speed(form, path, d_in, in_off, d_out, out_off, d_dec, lens, stream, autotune=True):
+    """One warm-up and one timed step of another precision form (autotuned
+    like the headline form)."""
     import torch
     from paper_2511_11337_b300 import api
     m = api.Model(path, cuda_stream=stream.cuda_stream, precision=PREC[form])
+    if autotune:
+        m.autotune(len(lens), int(max(lens)))
     total = int(in_off[-1])
     res = {}
     for k in range(2):
@@ -308,9 +311,11 @@ def run_boa(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
-    def step():
+    def step(mid=None):
         sizes = model.compress_device(d_in.data_ptr(), in_off, d_out.data_ptr(), out_off)
         n1 = model.last_launch_count
+        if mid is not None:
+            mid.record(stream)
         model.decompress_device(d_out.data_ptr(), out_off, lens, d_dec.data_ptr(), in_off, in_sizes=sizes)
         return sizes, n1 + model.last_launch_count
 
@@ -338,17 +343,22 @@ def run_boa(args):
                 flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
+            mid = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            sizes, n = step()
+            sizes, n = step(mid)
             b.record(stream)
-            evs.append((a, b))
+            evs.append((a, mid, b))
             launches += n
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     model.profile(False)
     prof = model.profile_read()
     prof_steps = model.profile_steps()
-    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    ms = statistics.mean(a.elapsed_time(b) for a, _, b in evs)
+    # the phases as they ran (decode lanes overlap, so the per-class kernel
+    # times below add up to more than the decompression phase)
+    phase_ms = {"compress": round(statistics.mean(a.elapsed_time(c) for a, c, _ in evs), 1),
+                "decompress": round(statistics.mean(c.elapsed_time(b) for _, c, b in evs), 1)}
     if dist:
         ms = reduce_max(ms, dist, "cuda")
         dist.barrier()
@@ -418,8 +428,8 @@ def run_boa(args):
     breakdown = {f"{ph}:{k}": {"launches_timed": v["launches"], "ms_per_step": round(v["ms_step"], 2),
                                "share": round(v["ms_step"] / step_est, 4) if step_est else None}
                  for (ph, k), v in sorted(est.items(), key=lambda kv: -kv[1]["ms_step"])}
-    phase_ms = {ph: round(sum(v["ms_step"] for (p2, _), v in est.items() if p2 == ph), 1)
-                for ph in ("compress", "decompress")}
+    kernel_ms = {ph: round(sum(v["ms_step"] for (p2, _), v in est.items() if p2 == ph), 1)
+                 for ph in ("compress", "decompress")}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -437,7 +447,8 @@ def run_boa(args):
                                      decompress_MBps=total / 1e6 / (phase_ms["decompress"] / 1e3))
         model.close()
         for f in names:
-            forms[f] = dict(acc[f], **form_speed(f, path, d_in, in_off, d_out, out_off, d_dec, lens, stream))
+            forms[f] = dict(acc[f], **form_speed(f, path, d_in, in_off, d_out, out_off, d_dec, lens, stream,
+                                                 args.autotune))
 
     clocks = clk.summary()
     out = {
@@ -456,6 +467,7 @@ def run_boa(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "phase_ms_per_step": phase_ms,
+        "kernel_ms_sum_per_step": kernel_ms,
         "compress_MBps": total / 1e6 / (phase_ms["compress"] / 1e3) if phase_ms["compress"] else None,
         "decompress_MBps": total / 1e6 / (phase_ms["decompress"] / 1e3) if phase_ms["decompress"] else None,
         "roofline": roof,

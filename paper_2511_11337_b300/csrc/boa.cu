@@ -18,6 +18,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -202,6 +203,7 @@ struct boa_model {
     bool use_graphs = true;         // decode step loop as CUDA graphs (when not profiling)
     int scan_variant = 0;           // decode-step scan kernel (see scan())
     int decode_lanes = 0;           // independent slot groups per decode step (0 = automatic)
+    bool pdl = true;                // chain kernels with programmatic dependent launch
     size_t kp8 = 0;                 // row stride of the FP8 activation scratch
 
     View v;                         // what the launchers work on
@@ -595,6 +597,37 @@ static boa_status check_launch(boa_model* m, const char* what) {
     return BOA_OK;
 }
 
+// Launch a kernel of the predictor / coder chain on the view's stream with
+// programmatic stream serialization (the kernel overlaps its set-up with
+// its predecessor and waits in pdl_wait_prev); splits > 1 launches clusters
+// of (1, 1, splits) along z.
+template <typename... P, typename... A>
+static void launch_k(boa_model* m, void (*kern)(P...), dim3 grid, dim3 block, size_t smem, int splits, A&&... args) {
+    cudaLaunchConfig_t cfg{};
+    if (splits > 1) grid.z = (unsigned)splits;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = m->v.stream;
+    cudaLaunchAttribute at[2];
+    unsigned na = 0;
+    if (splits > 1) {
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = 1;
+        at[na].val.clusterDim.y = 1;
+        at[na].val.clusterDim.z = (unsigned)splits;
+        na++;
+    }
+    if (m->pdl) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        na++;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = na;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+
 template <int EPI>
 static boa_status gemm(boa_model* m, int cls, const float* A, const float* Wt, const float* bias, float* C, long long M,
                        int N, int K) {
@@ -607,13 +640,13 @@ static boa_status gemm(boa_model* m, int cls, const float* A, const float* Wt, c
     const long long waves = 2LL * m->num_sms;
     if (N >= 128 && t128 >= waves) {
         dim3 grid((N + 127) / 128, (unsigned)((M + 127) / 128));
-        k_gemm_fp32<128, 128, EPI><<<grid, kGemmThreads, 0, m->v.stream>>>(A, Wt, bias, C, (int)M, N, K);
+        launch_k(m, k_gemm_fp32<128, 128, EPI>, grid, kGemmThreads, 0, 1, A, Wt, bias, C, (int)M, N, K);
     } else if (t12864 >= waves) {
         dim3 grid((N + 63) / 64, (unsigned)((M + 127) / 128));
-        k_gemm_fp32<128, 64, EPI><<<grid, kGemmThreads, 0, m->v.stream>>>(A, Wt, bias, C, (int)M, N, K);
+        launch_k(m, k_gemm_fp32<128, 64, EPI>, grid, kGemmThreads, 0, 1, A, Wt, bias, C, (int)M, N, K);
     } else {
         dim3 grid((N + 63) / 64, (unsigned)((M + 63) / 64));
-        k_gemm_fp32<64, 64, EPI><<<grid, kGemmThreads, 0, m->v.stream>>>(A, Wt, bias, C, (int)M, N, K);
+        launch_k(m, k_gemm_fp32<64, 64, EPI>, grid, kGemmThreads, 0, 1, A, Wt, bias, C, (int)M, N, K);
     }
     return check_launch(m, "gemm");
 }
@@ -668,17 +701,30 @@ static boa_status tmap_2d(boa_model* m, const void* ptr, uint64_t rows, uint64_t
 // same MMA shape in compression and decompression.
 static int tc_bn(int N) { return N >= 512 ? 128 : N > 48 ? 64 : 48; }
 
+// Split K across a cluster of CTAs (deterministic reduction in the
+// epilogue) for x_proj (N <= 64), whose grid is otherwise a few dozen long
+// K loops at decode sizes.  Chosen by (N, K) only, like the tile width, each
+// CTA keeping at least two K blocks of k_elems.  (Splitting out_proj and the
+// head as well cost compression more than it saved decompression.)
+static int tc_splits(int N, int K, int k_elems) {
+    int s = N <= 64 ? 4 : 1;
+    while (s > 1 && (K % (s * k_elems) != 0 || K / (s * k_elems) < 2)) s /= 2;
+    return s;
+}
+
+
 template <int BN, int EPI, int KIND, bool DEEP>
-static void launch_tc_cfg(boa_model* m, dim3 grid, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias,
-                          float* C, __nv_bfloat16* outb, long long M, int N, int K, const float* rs, const float* cs) {
+static void launch_tc_cfg(boa_model* m, dim3 grid, int splits, const CUtensorMap& ta, const CUtensorMap& tb,
+                          const float* bias, float* C, __nv_bfloat16* outb, long long M, int N, int K, const float* rs,
+                          const float* cs) {
     using L = TcSmem<BN, DEEP>;
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L::kBytes);
     });
-    k_gemm_tc_bf16<BN, EPI, KIND, DEEP><<<grid, kTcThreads, L::kBytes, m->v.stream>>>(ta, tb, bias, C, outb, (int)M, N,
-                                                                                    K, m->err.p, rs, cs);
+    launch_k(m, k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, grid, kTcThreads, L::kBytes, splits, ta, tb, bias, C, outb,
+             (int)M, N, K, m->err.p, rs, cs);
 }
 
 // Grids smaller than the SM count take the deep-pipeline variant.
@@ -686,10 +732,11 @@ template <int BN, int EPI, int KIND>
 static void launch_tc(boa_model* m, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, float* C,
                       __nv_bfloat16* outb, long long M, int N, int K, const float* rs, const float* cs) {
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
-    if ((long long)grid.x * grid.y < m->num_sms)
-        launch_tc_cfg<BN, EPI, KIND, true>(m, grid, ta, tb, bias, C, outb, M, N, K, rs, cs);
+    const int splits = tc_splits(N, K, KIND == kKindE4M3 ? 128 : kTcBK);
+    if ((long long)grid.x * grid.y * splits < m->num_sms)
+        launch_tc_cfg<BN, EPI, KIND, true>(m, grid, splits, ta, tb, bias, C, outb, M, N, K, rs, cs);
     else
-        launch_tc_cfg<BN, EPI, KIND, false>(m, grid, ta, tb, bias, C, outb, M, N, K, rs, cs);
+        launch_tc_cfg<BN, EPI, KIND, false>(m, grid, splits, ta, tb, bias, C, outb, M, N, K, rs, cs);
 }
 
 template <int EPI>
@@ -723,8 +770,8 @@ static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_
     if (!m->v.a8 || (size_t)Kp > m->kp8) return fail(BOA_ERR_ARG, "FP8 activation scratch not sized for K=%d", K);
     {
         ProfScope pq(m, BOA_KC_OTHER, 3.0 * M * K, 5.0 * M * K + 4.0 * M);
-        k_quant_rows_e4m3<<<(unsigned)((M + 7) / 8), 256, 0, m->v.stream>>>(
-            A, reinterpret_cast<__nv_fp8_e4m3*>(m->v.a8), m->v.a8s, M, K, Kp);
+        launch_k(m, k_quant_rows_e4m3, dim3((unsigned)((M + 7) / 8)), 256, 0, 1, A,
+                 reinterpret_cast<__nv_fp8_e4m3*>(m->v.a8), m->v.a8s, M, K, Kp);
     }
     TRY(check_launch(m, "quant_rows"));
     const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
@@ -742,26 +789,27 @@ static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_
 }
 
 template <int BN, int EPI, bool DEEP>
-static void launch_t3_cfg(boa_model* m, dim3 grid, const CUtensorMap& ta, const CUtensorMap& th, const CUtensorMap& tl,
-                          const float* bias, float* C, long long M, int N, int K) {
+static void launch_t3_cfg(boa_model* m, dim3 grid, int splits, const CUtensorMap& ta, const CUtensorMap& th,
+                          const CUtensorMap& tl, const float* bias, float* C, long long M, int N, int K) {
     using L = T3Smem<BN, DEEP>;
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_gemm_tc_tf32x3<BN, EPI, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L::kBytes);
     });
-    k_gemm_tc_tf32x3<BN, EPI, DEEP><<<grid, kT3Threads, L::kBytes, m->v.stream>>>(ta, th, tl, bias, C, (int)M, N, K,
-                                                                                m->err.p);
+    launch_k(m, k_gemm_tc_tf32x3<BN, EPI, DEEP>, grid, kT3Threads, L::kBytes, splits, ta, th, tl, bias, C, (int)M,
+             N, K, m->err.p);
 }
 
 template <int BN, int EPI>
 static void launch_t3(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th, const CUtensorMap& tl,
                       const float* bias, float* C, long long M, int N, int K) {
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
-    if ((long long)grid.x * grid.y < m->num_sms)
-        launch_t3_cfg<BN, EPI, true>(m, grid, ta, th, tl, bias, C, M, N, K);
+    const int splits = tc_splits(N, K, kT3BK);
+    if ((long long)grid.x * grid.y * splits < m->num_sms)
+        launch_t3_cfg<BN, EPI, true>(m, grid, splits, ta, th, tl, bias, C, M, N, K);
     else
-        launch_t3_cfg<BN, EPI, false>(m, grid, ta, th, tl, bias, C, M, N, K);
+        launch_t3_cfg<BN, EPI, false>(m, grid, splits, ta, th, tl, bias, C, M, N, K);
 }
 
 // FP32-accurate tensor-core GEMM (3xTF32); A is FP32, W pre-split.
@@ -787,8 +835,8 @@ template <int VPT>
 static void launch_embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc, const DevLayer& L0) {
     const long long rows = (long long)S * Tc;
     const bool tc = m->precision == BOA_PREC_BF16;
-    k_embed_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->v.stream>>>(ts, S, Tc, m->embed, L0.ln_a_w, L0.ln_a_b,
-                                                                        m->v.x, m->v.xn, tc ? m->v.xn_b : nullptr);
+    launch_k(m, k_embed_ln<VPT>, dim3((unsigned)((rows + 7) / 8)), 256, 0, 1, ts, S, Tc, m->embed, L0.ln_a_w,
+             L0.ln_a_b, m->v.x, m->v.xn, tc ? m->v.xn_b : nullptr);
 }
 
 template <int VPT>
@@ -796,9 +844,8 @@ static void launch_ln_ln(boa_model* m, long long rows, const DevLayer& L, const 
     const bool tc = m->precision == BOA_PREC_BF16;
     // the BF16 copy of x feeds the head (last block) or the next block's FFN
     __nv_bfloat16* xb = (tc && (!next || m->F)) ? m->v.x_b : nullptr;
-    k_ln_ln<VPT><<<(unsigned)((rows + 7) / 8), 256, 0, m->v.stream>>>(
-        rows, m->v.x, L.ln_b_w, L.ln_b_b, next ? next->ln_a_w : nullptr, next ? next->ln_a_b : nullptr, m->v.xn, xb,
-        tc ? m->v.xn_b : nullptr);
+    launch_k(m, k_ln_ln<VPT>, dim3((unsigned)((rows + 7) / 8)), 256, 0, 1, rows, m->v.x, L.ln_b_w, L.ln_b_b,
+             next ? next->ln_a_w : nullptr, next ? next->ln_a_b : nullptr, m->v.xn, xb, tc ? m->v.xn_b : nullptr);
 }
 
 static boa_status embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc) {
@@ -833,7 +880,7 @@ static boa_status conv(boa_model* m, int l, int S, int Tc) {
     ProfScope ps(m, BOA_KC_CONV, rows * m->E * (2.0 * m->K + 4), 4.0 * (2 * rows * m->E + 2.0 * S * (m->K - 1) * m->E));
     __nv_bfloat16* ub = m->precision == BOA_PREC_BF16 ? m->v.u_b : nullptr;
 #define CONV_CASE(KK, GG) \
-    k_conv_silu<KK, GG><<<grid, 128, 0, m->v.stream>>>(m->v.xz, m->E, L.conv_w, L.conv_b, win, m->v.u, ub, S, Tc)
+    launch_k(m, k_conv_silu<KK, GG>, grid, 128, 0, 1, m->v.xz, m->E, L.conv_w, L.conv_b, win, m->v.u, ub, S, Tc)
     if (G == 8) {
         switch (m->K) { case 2: CONV_CASE(2, 8); break; case 3: CONV_CASE(3, 8); break; default: CONV_CASE(4, 8); break; }
     } else {
@@ -883,8 +930,8 @@ static boa_status launch_step_bulk(boa_model* m, const DevLayer& L, float* hs, _
     });
     if (attr_err != cudaSuccess) return fail(BOA_ERR_CUDA, "decode scan set-up: %s", cudaGetErrorString(attr_err));
     const int grid = (int)std::min<long long>(S, (long long)m->num_sms * cps);
-    k_scan_step_bulk<16, RR><<<grid, m->E / 2, smem, m->v.stream>>>(m->v.u, m->v.xz, m->v.dbc, L.dt_w, L.dt_b, L.A2,
-                                                                   L.D, hs, m->v.yg, ygb, m->E, S, stages, m->err.p);
+    launch_k(m, k_scan_step_bulk<16, RR>, dim3((unsigned)grid), dim3((unsigned)(m->E / 2)), smem, 1, m->v.u, m->v.xz,
+             m->v.dbc, L.dt_w, L.dt_b, L.A2, L.D, hs, m->v.yg, ygb, m->E, S, stages, m->err.p);
     return BOA_OK;
 }
 
@@ -907,8 +954,8 @@ static boa_status scan(boa_model* m, int l, int S, int Tc) {
     if (v == 1) {
         dim3 g4((m->E + 4 * kScanThreads - 1) / (4 * kScanThreads), S);
 #define STEP4_CASE(RR)                                                                                       \
-    k_scan_step4<16, RR><<<g4, kScanThreads, 0, m->v.stream>>>(m->v.u, m->v.xz, m->v.dbc, L.dt_w, L.dt_b, L.A2, \
-                                                               L.D, hs, m->v.yg, ygb, m->E)
+    launch_k(m, k_scan_step4<16, RR>, g4, kScanThreads, 0, 1, m->v.u, m->v.xz, m->v.dbc, L.dt_w, L.dt_b, L.A2, L.D, \
+             hs, m->v.yg, ygb, m->E)
         switch (m->r) { case 4: STEP4_CASE(4); break; case 8: STEP4_CASE(8); break; default: STEP4_CASE(16); break; }
 #undef STEP4_CASE
         return check_launch(m, "scan_step4");
@@ -916,8 +963,8 @@ static boa_status scan(boa_model* m, int l, int S, int Tc) {
     const int G = v == 3 ? 8 : 1;
     dim3 grid((m->E + kScanThreads - 1) / kScanThreads, (S + G - 1) / G);
 #define SCAN_CASE(RR, GG)                                                                                         \
-    k_scan<16, RR, GG><<<grid, kScanThreads, 0, m->v.stream>>>(m->v.u, m->v.xz, m->v.dbc, L.dt_w, L.dt_b, L.A2, L.D, \
-                                                               hs, m->v.yg, ygb, m->E, S, Tc)
+    launch_k(m, k_scan<16, RR, GG>, grid, kScanThreads, 0, 1, m->v.u, m->v.xz, m->v.dbc, L.dt_w, L.dt_b, L.A2, L.D, \
+             hs, m->v.yg, ygb, m->E, S, Tc)
 #define SCAN_R(GG)                      \
     switch (m->r) {                     \
         case 4: SCAN_CASE(4, GG); break; \
@@ -1264,8 +1311,8 @@ static boa_status compress_impl(boa_model* m, size_t n, const uint8_t* d_in, con
     TRY(check_launch(m, "enc_trivial"));
     if (sc.S > 0) {
         const unsigned wgrid = (unsigned)((S + 3) / 4);
-        k_enc_slots<<<wgrid, 128, 0, m->stream>>>(S, 1, 0, m->sched.p, m->slot_beg.p, m->slots.p, m->st.p, d_in, tb,
-                                                 d_out, mem);
+        launch_k(m, k_enc_slots, dim3(wgrid), 128, 0, 1, S, 1, 0LL, (const int*)m->sched.p, (const int*)m->slot_beg.p,
+                 m->slots.p, m->st.p, d_in, tb, d_out, mem);
         TRY(check_launch(m, "enc_slots"));
         TokenSrc ts{d_in, m->in_off.p, m->lens.p, m->slots.p};
         for (uint64_t c = 0; c < chunks; c++) {
@@ -1274,11 +1321,12 @@ static boa_status compress_impl(boa_model* m, size_t n, const uint8_t* d_in, con
             TRY(forward(m, ts, S, Tc));
             {
                 ProfScope ps(m, BOA_KC_ENCODE, (double)S * Tc * 256 * 8, (double)S * Tc * (256 * 4 + 2));
-                k_encode<<<wgrid, 128, 0, m->stream>>>(m->logits.p, S, Tc, m->slots.p, m->st.p, d_in, tb, d_out);
+                launch_k(m, k_encode, dim3(wgrid), 128, 0, 1, (const float*)m->v.logits, S, Tc,
+                         (const SlotState*)m->v.slots, m->v.st, d_in, tb, d_out);
             }
             TRY(check_launch(m, "encode"));
-            k_enc_slots<<<wgrid, 128, 0, m->stream>>>(S, 0, Tc, m->sched.p, m->slot_beg.p, m->slots.p, m->st.p, d_in,
-                                                     tb, d_out, mem);
+            launch_k(m, k_enc_slots, dim3(wgrid), 128, 0, 1, S, 0, (long long)Tc, (const int*)m->sched.p,
+                     (const int*)m->slot_beg.p, m->slots.p, m->st.p, d_in, tb, d_out, mem);
             TRY(check_launch(m, "enc_slots"));
         }
     }
@@ -1297,15 +1345,15 @@ static boa_status compress_impl(boa_model* m, size_t n, const uint8_t* d_in, con
 template <int VPT>
 static void launch_dec_init(boa_model* m, int S, const uint8_t* cin, const StreamTable& tb, uint8_t* out,
                             const NextEmbed& ne) {
-    k_dec_slots_init<VPT><<<(unsigned)((S + 3) / 4), 128, 0, m->v.stream>>>(S, m->sched.p, m->v.slot_beg, m->v.slots,
-                                                                           m->v.st, cin, tb, out, ne);
+    launch_k(m, k_dec_slots_init<VPT>, dim3((unsigned)((S + 3) / 4)), 128, 0, 1, S, (const int*)m->sched.p,
+             m->v.slot_beg, m->v.slots, m->v.st, cin, tb, out, ne);
 }
 
 template <int VPT>
 static void launch_decode(boa_model* m, int S, const uint8_t* cin, const StreamTable& tb, uint8_t* out,
                           const NextEmbed& ne, const SlotMem& mem) {
-    k_decode<VPT><<<(unsigned)((S + 3) / 4), 128, 0, m->v.stream>>>(m->v.logits, S, m->sched.p, m->v.slot_beg,
-                                                                   m->v.slots, m->v.st, cin, tb, out, ne, mem);
+    launch_k(m, k_decode<VPT>, dim3((unsigned)((S + 3) / 4)), 128, 0, 1, (const float*)m->v.logits, S,
+             (const int*)m->sched.p, m->v.slot_beg, m->v.slots, m->v.st, cin, tb, out, ne, mem);
 }
 
 static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, const uint64_t* in_off,
@@ -1913,6 +1961,11 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
             CU(cudaMemcpy(dq.p, q.data(), N * Kp, cudaMemcpyHostToDevice));
             CU(cudaMemcpy(ds.p, sc.data(), N * 4, cudaMemcpyHostToDevice));
             const __nv_fp8_e4m3* w8 = reinterpret_cast<const __nv_fp8_e4m3*>(dq.p);
+            t.kp8 = Kp;
+            TRY(t.a8.ensure(M * Kp));
+            TRY(t.a8s.ensure(M));
+            t.v.a8 = t.a8.p;
+            t.v.a8s = t.a8s.p;
             boa_status r = BOA_OK;
             switch (epilogue) {
                 case kEpiStore: r = gemm_f8<kEpiStore>(&t, BOA_KC_OTHER, dA.p, w8, ds.p, dB.p, dC.p, M, N, K); break;

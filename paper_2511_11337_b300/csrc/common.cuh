@@ -46,6 +46,17 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     return v;
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream is still
+// running: pdl_launch_next lets this kernel's successor start early (it runs
+// once every CTA here has issued it), and pdl_wait_prev blocks until the
+// predecessor has finished and its writes are visible.  Every kernel that
+// the library launches that way calls pdl_wait_prev before it reads any
+// input or writes any output.  Without that launch attribute both return
+// at once.
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // 2^x on the MUFU unit (ex2.approx); used for exp(Delta * A) with A
 // pre-scaled by log2(e).
 __device__ __forceinline__ float ex2_approx(float x) {

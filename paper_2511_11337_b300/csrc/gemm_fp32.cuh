@@ -33,6 +33,8 @@ template <int BM, int BN, int EPI>
 __global__ void __launch_bounds__(kGemmThreads)
 k_gemm_fp32(const float* __restrict__ A, const float* __restrict__ Wt, const float* __restrict__ bias,
             float* __restrict__ Cm, int M, int N, int K) {
+    pdl_launch_next();
+    pdl_wait_prev();
     constexpr int TM = BM / 16, TN = BN / 16;
     constexpr int GM = TM / 4, GN = TN / 4;           // groups of 4
     constexpr int A_F4 = BM * kGemmBK / 4;            // float4 per A tile

@@ -155,49 +155,94 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Epilogue shared by the tensor-core kernels.  Warp q owns accumulator rows
-// (TMEM lanes) 32q .. 32q+31.  Phase 1: it copies them, 16 columns per
-// tcgen05.ld, into its own slice of the (now idle) pipeline shared memory,
-// 16-byte chunks XOR-swizzled by row so the writes are conflict-free.
-// Phase 2: it walks its rows, each lane taking one 16-byte chunk, so every
-// global store of the warp covers whole contiguous row segments; the
-// epilogue arithmetic (scales, bias, GELU, residual) happens here.
+// (TMEM lanes) 32q .. 32q+31.  Phase 1 (tc_stage_tile): it copies them, 16
+// columns per tcgen05.ld, into its own slice of the (now idle) pipeline
+// shared memory, 16-byte chunks XOR-swizzled by row so the writes are
+// conflict-free.  Phase 2 (tc_store_rows): a warp walks a range of rows,
+// each lane taking one 16-byte chunk, so every global store of the warp
+// covers whole contiguous row segments; the epilogue arithmetic (scales,
+// bias, GELU, residual) happens here.  With split K (a cluster of `peers`
+// CTAs along z, each with the partial sum of its share of the K blocks) the
+// chunk is the sum of the peers' staged tiles, read through distributed
+// shared memory in rank order 0, 1, ..., so every element sees the same
+// additions wherever its tile runs.
 // row_scale / col_scale (FP8 operands): acc * row_scale[m] * col_scale[n].
-template <int BN, int EPI>
-__device__ __forceinline__ void tc_epilogue(uint32_t tmem, int q, int lane, int m0, int n0, int M, int N,
-                                            const float* __restrict__ bias, float* __restrict__ Cm,
-                                            __nv_bfloat16* __restrict__ out_bf16, float* stage,
-                                            const float* __restrict__ row_scale = nullptr,
-                                            const float* __restrict__ col_scale = nullptr) {
-    constexpr int kChunks = BN / 16;
-    constexpr int kSlots = BN / 4;                       // float4 per row
-    constexpr int kMask = kSlots >= 16 ? 7 : 3;          // swizzle stays inside the row
-    constexpr int kRowsPerIter = 32 / kSlots;            // rows one warp store covers
-    constexpr int kIters = 32 / kRowsPerIter;
-    float4* st = reinterpret_cast<float4*>(stage) + (size_t)q * 32 * kSlots;
-    // phase 1: TMEM -> registers -> shared (row = lane)
+template <int BN>
+struct TileLayout {
+    static constexpr int kChunks = BN / 16;
+    static constexpr int kSlots = BN / 4;                       // float4 per row
+    static constexpr int kMask = kSlots >= 16 ? 7 : 3;          // swizzle stays inside the row
+    static constexpr int kRowsPerIter = 32 / kSlots;            // rows one warp store covers
+};
+
+template <int BN>
+__device__ __forceinline__ void tc_stage_tile(uint32_t tmem, int q, int lane, float* stage) {
+    using T = TileLayout<BN>;
+    float4* st = reinterpret_cast<float4*>(stage) + (size_t)q * 32 * T::kSlots;
 #pragma unroll
-    for (int g0 = 0; g0 < kChunks; g0 += 4) {
+    for (int g0 = 0; g0 < T::kChunks; g0 += 4) {
         uint32_t r[4][16];
 #pragma unroll
         for (int c = 0; c < 4; c++)
-            if (g0 + c < kChunks) tmem_ld16_nowait(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * (g0 + c)), r[c]);
+            if (g0 + c < T::kChunks)
+                tmem_ld16_nowait(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * (g0 + c)), r[c]);
         tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < 4; c++) {
-            if (g0 + c >= kChunks) break;
+            if (g0 + c >= T::kChunks) break;
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const int f = (g0 + c) * 4 + j;
-                st[lane * kSlots + (f ^ (lane & kMask))] =
+                st[lane * T::kSlots + (f ^ (lane & T::kMask))] =
                     make_float4(__uint_as_float(r[c][4 * j]), __uint_as_float(r[c][4 * j + 1]),
                                 __uint_as_float(r[c][4 * j + 2]), __uint_as_float(r[c][4 * j + 3]));
             }
         }
     }
-    __syncwarp();
-    // phase 2: shared -> global, whole row segments per warp store
-    const int f = lane % kSlots;
-    const bool active = lane < kRowsPerIter * kSlots;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t dsmem_addr(const void* local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ float4 dsmem_ld4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int dsmem_ld_s32(uint32_t addr) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// Rows r_beg .. r_beg + n_rows - 1 of the staged tile (n_rows a multiple of
+// the rows one warp store covers) to global memory.
+template <int BN, int EPI>
+__device__ __forceinline__ void tc_store_rows(int r_beg, int n_rows, int lane, int m0, int n0, int M, int N,
+                                              const float* __restrict__ bias, float* __restrict__ Cm,
+                                              __nv_bfloat16* __restrict__ out_bf16, const float* stage, int peers,
+                                              const float* __restrict__ row_scale,
+                                              const float* __restrict__ col_scale) {
+    using T = TileLayout<BN>;
+    const float4* st = reinterpret_cast<const float4*>(stage);
+    const int kIters = n_rows / T::kRowsPerIter;
+    const int f = lane % T::kSlots;
+    const bool active = lane < T::kRowsPerIter * T::kSlots;
     const int n = n0 + 4 * f;
     const bool col_ok = active && n < N;                 // N % 4 == 0
     float4 bv = make_float4(0.f, 0.f, 0.f, 0.f), cs = make_float4(1.f, 1.f, 1.f, 1.f);
@@ -212,8 +257,8 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, int q, int lane, int 
         float rsv[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; u++) {
-            const int rl = (it0 + u) * kRowsPerIter + lane / kSlots;
-            const int row = m0 + q * 32 + rl;
+            const int rl = r_beg + (it0 + u) * T::kRowsPerIter + lane / T::kSlots;
+            const int row = m0 + rl;
             old[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             rsv[u] = 1.f;
             if (it0 + u < kIters && col_ok && row < M) {
@@ -224,10 +269,23 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, int q, int lane, int 
 #pragma unroll
         for (int u = 0; u < kBatch; u++) {
             if (it0 + u >= kIters) break;
-            const int rl = (it0 + u) * kRowsPerIter + lane / kSlots;
-            const int row = m0 + q * 32 + rl;
+            const int rl = r_beg + (it0 + u) * T::kRowsPerIter + lane / T::kSlots;
+            const int row = m0 + rl;
             if (!col_ok || row >= M) continue;
-            const float4 a = st[rl * kSlots + (f ^ (rl & kMask))];
+            const float4* src = st + rl * T::kSlots + (f ^ (rl & T::kMask));
+            float4 a;
+            if (peers == 1) {
+                a = *src;
+            } else {
+                a = dsmem_ld4(dsmem_addr(src, 0));
+                for (int p = 1; p < peers; p++) {
+                    const float4 b = dsmem_ld4(dsmem_addr(src, (uint32_t)p));
+                    a.x = __fadd_rn(a.x, b.x);
+                    a.y = __fadd_rn(a.y, b.y);
+                    a.z = __fadd_rn(a.z, b.z);
+                    a.w = __fadd_rn(a.w, b.w);
+                }
+            }
             float o[4] = {a.x, a.y, a.z, a.w};
             const float* bp = reinterpret_cast<const float*>(&bv);
             const float* cp = reinterpret_cast<const float*>(&cs);
@@ -249,6 +307,41 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, int q, int lane, int 
             }
         }
     }
+}
+
+// The whole epilogue of one CTA.  Every thread of the CTA calls it (the
+// cluster barriers of split K count every thread); `epi` marks the four
+// epilogue warps and q their TMEM quadrant.  bad: this CTA's pipeline gave
+// up; with split K no CTA of the cluster then stores anything.
+template <int BN, int EPI>
+__device__ __forceinline__ void tc_epilogue(bool epi, bool bad, int* bad_flag, uint32_t tmem, int q, int lane, int m0,
+                                            int n0, int M, int N, const float* __restrict__ bias,
+                                            float* __restrict__ Cm, __nv_bfloat16* __restrict__ out_bf16,
+                                            float* stage, const float* __restrict__ row_scale = nullptr,
+                                            const float* __restrict__ col_scale = nullptr) {
+    const int peers = (int)gridDim.z;
+    if (peers == 1) {
+        if (epi && !bad) {
+            tc_stage_tile<BN>(tmem, q, lane, stage);
+            __syncwarp();
+            tc_store_rows<BN, EPI>(32 * q, 32, lane, m0, n0, M, N, bias, Cm, out_bf16, stage, 1, row_scale,
+                                   col_scale);
+        }
+        return;
+    }
+    if (epi && !bad) tc_stage_tile<BN>(tmem, q, lane, stage);
+    if (threadIdx.x == 0) *bad_flag = bad ? 1 : 0;
+    __syncwarp();
+    cluster_sync_all();                                  // every peer's tile and flag are in place
+    bool any_bad = false;
+    for (int p = 0; p < peers; p++) any_bad |= dsmem_ld_s32(dsmem_addr(bad_flag, (uint32_t)p)) != 0;
+    if (epi && !any_bad) {
+        const int rows = kTcBM / peers;                  // this CTA's share of the tile
+        const int per_warp = rows / 4;
+        tc_store_rows<BN, EPI>((int)cluster_rank() * rows + q * per_warp, per_warp, lane, m0, n0, M, N, bias, Cm,
+                               out_bf16, stage, peers, row_scale, col_scale);
+    }
+    cluster_sync_all();                                  // peers are done reading this CTA's tile
 }
 
 // DEEP = false: about 110 KB of stages so that two CTAs share an SM (one's
@@ -290,9 +383,12 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::kBars);
     __shared__ int abort_flag;
 
+    __shared__ int bad_flag;
+
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
-    const int nk = K / kElemK;
+    const int nk = K / kElemK / (int)gridDim.z;          // split K: this CTA's K blocks
+    const int kb0 = (int)blockIdx.z * nk;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -309,6 +405,9 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    // the set-up above overlaps the previous kernel; inputs are read below
+    pdl_launch_next();
+    pdl_wait_prev();
 
     int armed_last = -1;   // producer: last K-block whose loads were issued
     if (threadIdx.x == 0) {
@@ -321,8 +420,8 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
             uint8_t* sa = smem + (size_t)s * L::kStage;
             mbar_expect_tx(&full[s], L::kStage);
-            tma_load_2d(&tmA, &full[s], sa, kb * kElemK, m0);
-            tma_load_2d(&tmB, &full[s], sa + L::kA, kb * kElemK, n0);
+            tma_load_2d(&tmA, &full[s], sa, (kb0 + kb) * kElemK, m0);
+            tma_load_2d(&tmB, &full[s], sa + L::kA, (kb0 + kb) * kElemK, n0);
             armed_last = kb;
         }
     } else if (threadIdx.x == 32) {
@@ -354,19 +453,17 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const bool finished = mbar_wait(&done[0], 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
-    if (!finished || abort_flag) {
-        if (threadIdx.x == 0) {
-            atomicExch(err, 1);
-            // let copies and MMAs still in flight land before TMEM and shared
-            // memory are released (each wait again bounded)
-            for (int kb = armed_last; kb >= 0 && kb > armed_last - L::kStages; kb--)
-                mbar_wait(&full[kb % L::kStages], (kb / L::kStages) & 1);
-            if (!finished) mbar_wait(&done[0], 0);
-        }
-    } else {
-        tc_epilogue<BN, EPI>(tmem, warp, lane, m0, n0, M, N, bias, Cm, out_bf16, reinterpret_cast<float*>(smem),
-                             row_scale, col_scale);
+    const bool bad = !finished || abort_flag;
+    if (bad && threadIdx.x == 0) {
+        atomicExch(err, 1);
+        // let copies and MMAs still in flight land before TMEM and shared
+        // memory are released (each wait again bounded)
+        for (int kb = armed_last; kb >= 0 && kb > armed_last - L::kStages; kb--)
+            mbar_wait(&full[kb % L::kStages], (kb / L::kStages) & 1);
+        if (!finished) mbar_wait(&done[0], 0);
     }
+    tc_epilogue<BN, EPI>(true, bad, &bad_flag, tmem, warp, lane, m0, n0, M, N, bias, Cm, out_bf16,
+                         reinterpret_cast<float*>(smem), row_scale, col_scale);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -437,9 +534,12 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::kBars);
     __shared__ int abort_flag;
 
+    __shared__ int bad_flag;
+
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
-    const int nk = K / kT3BK;
+    const int nk = K / kT3BK / (int)gridDim.z;           // split K: this CTA's K blocks
+    const int kb0 = (int)blockIdx.z * nk;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -461,6 +561,9 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    // the set-up above overlaps the previous kernel; inputs are read below
+    pdl_launch_next();
+    pdl_wait_prev();
 
     int armed_last = -1;
     if (threadIdx.x == 0) {
@@ -472,9 +575,9 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             }
             uint8_t* st = smem + (size_t)s * L::kStage;
             mbar_expect_tx(&full[s], L::kA + 2 * L::kB);
-            tma_load_2d(&tmA, &full[s], st, kb * kT3BK, m0);
-            tma_load_2d(&tmBhi, &full[s], st + 2 * L::kA, kb * kT3BK, n0);
-            tma_load_2d(&tmBlo, &full[s], st + 2 * L::kA + L::kB, kb * kT3BK, n0);
+            tma_load_2d(&tmA, &full[s], st, (kb0 + kb) * kT3BK, m0);
+            tma_load_2d(&tmBhi, &full[s], st + 2 * L::kA, (kb0 + kb) * kT3BK, n0);
+            tma_load_2d(&tmBlo, &full[s], st + 2 * L::kA + L::kB, (kb0 + kb) * kT3BK, n0);
             armed_last = kb;
         }
     } else if (threadIdx.x == 32) {
@@ -527,16 +630,15 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     const bool finished = mbar_wait(&done[0], 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
-    if (!finished || abort_flag) {
-        if (threadIdx.x == 0) {
-            atomicExch(err, 1);
-            for (int kb = armed_last; kb >= 0 && kb > armed_last - L::kStages; kb--)
-                mbar_wait(&full[kb % L::kStages], (kb / L::kStages) & 1);
-            if (!finished) mbar_wait(&done[0], 0);
-        }
-    } else if (warp >= 2) {
-        tc_epilogue<BN, EPI>(tmem, warp % 4, lane, m0, n0, M, N, bias, Cm, nullptr, reinterpret_cast<float*>(smem));
+    const bool bad = !finished || abort_flag;
+    if (bad && threadIdx.x == 0) {
+        atomicExch(err, 1);
+        for (int kb = armed_last; kb >= 0 && kb > armed_last - L::kStages; kb--)
+            mbar_wait(&full[kb % L::kStages], (kb / L::kStages) & 1);
+        if (!finished) mbar_wait(&done[0], 0);
     }
+    tc_epilogue<BN, EPI>(warp >= 2, bad, &bad_flag, tmem, warp % 4, lane, m0, n0, M, N, bias, Cm, nullptr,
+                         reinterpret_cast<float*>(smem));
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)

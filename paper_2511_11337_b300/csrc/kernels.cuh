@@ -70,6 +70,8 @@ template <int VPT>
 __global__ void k_embed_ln(TokenSrc ts, int S, int Tc, const float* __restrict__ embed,
                            const float* __restrict__ g, const float* __restrict__ b,
                            float* __restrict__ x, float* __restrict__ xn, __nv_bfloat16* __restrict__ xn_b) {
+    pdl_launch_next();
+    pdl_wait_prev();
     constexpr int d = VPT * 32;
     const int lane = threadIdx.x & 31;
     const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -96,6 +98,8 @@ __global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __re
                         const float* __restrict__ bb, const float* __restrict__ ga,
                         const float* __restrict__ ba, float* __restrict__ xn,
                         __nv_bfloat16* __restrict__ x_b, __nv_bfloat16* __restrict__ xn_b) {
+    pdl_launch_next();
+    pdl_wait_prev();
     constexpr int d = VPT * 32;
     const int lane = threadIdx.x & 31;
     const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -131,6 +135,8 @@ __global__ void __launch_bounds__(128)
 k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ wt,
             const float* __restrict__ bconv, float* __restrict__ win,
             float* __restrict__ u, __nv_bfloat16* __restrict__ u_b, int S, int Tc) {
+    pdl_launch_next();
+    pdl_wait_prev();
     const int c = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= E) return;
     float4 wv[K];
@@ -194,6 +200,8 @@ k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* _
        const float* __restrict__ dtwt, const float* __restrict__ dt_b, const float* __restrict__ A2t,
        const float* __restrict__ Dv, float* __restrict__ hstate, float* __restrict__ yg,
        __nv_bfloat16* __restrict__ yg_b, int E, int S, int Tc) {
+    pdl_launch_next();
+    pdl_wait_prev();
     constexpr int W = R + 2 * NS;   // dbc row width
     static_assert(R % 4 == 0 && NS % 4 == 0, "rows are read as float4");
     __shared__ __align__(16) float sm[kScanRowsSmem][W];
@@ -316,6 +324,8 @@ k_scan_step4(const float* __restrict__ u, const float* __restrict__ xz, const fl
              const float* __restrict__ dtwt, const float* __restrict__ dt_b, const float* __restrict__ A2t,
              const float* __restrict__ Dv, float* __restrict__ hstate, float* __restrict__ yg,
              __nv_bfloat16* __restrict__ yg_b, int E) {
+    pdl_launch_next();
+    pdl_wait_prev();
     constexpr int W = R + 2 * NS;
     __shared__ float sm[W];
     const int s = blockIdx.y;
@@ -616,6 +626,8 @@ __global__ void k_enc_trivial(int n, const uint8_t* __restrict__ data, StreamTab
 __global__ void k_enc_slots(int S, int init, long long tc, const int* __restrict__ sched,
                             const int* __restrict__ slot_beg, SlotState* slots, CoderState* st,
                             const uint8_t* __restrict__ data, StreamTable tb, uint8_t* __restrict__ out, SlotMem mem) {
+    pdl_launch_next();
+    pdl_wait_prev();
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (s >= S) return;
@@ -659,6 +671,8 @@ __global__ void k_enc_slots(int S, int init, long long tc, const int* __restrict
 // encode the true next byte of the slot's current stream (paper "Encoder").
 __global__ void k_encode(const float* __restrict__ logits, int S, int Tc, const SlotState* __restrict__ slots,
                          CoderState* st, const uint8_t* __restrict__ data, StreamTable tb, uint8_t* __restrict__ out) {
+    pdl_launch_next();
+    pdl_wait_prev();
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (s >= S) return;
@@ -753,6 +767,8 @@ template <int VPT>
 __global__ void k_dec_slots_init(int S, const int* __restrict__ sched, const int* __restrict__ slot_beg,
                                  SlotState* slots, CoderState* st, const uint8_t* __restrict__ cin, StreamTable tb,
                                  uint8_t* __restrict__ out, NextEmbed ne) {
+    pdl_launch_next();
+    pdl_wait_prev();
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (s >= S) return;
@@ -774,6 +790,8 @@ __global__ void k_decode(const float* __restrict__ logits, int S, const int* __r
                          const int* __restrict__ slot_beg, SlotState* slots, CoderState* st,
                          const uint8_t* __restrict__ cin, StreamTable tb, uint8_t* __restrict__ out, NextEmbed ne,
                          SlotMem mem) {
+    pdl_launch_next();
+    pdl_wait_prev();
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (s >= S) return;
@@ -832,6 +850,8 @@ __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restric
 // zero (the GEMM's K blocks are 128 wide).  One warp per row, K <= 1024.
 __global__ void k_quant_rows_e4m3(const float* __restrict__ A, __nv_fp8_e4m3* __restrict__ q,
                                   float* __restrict__ scale, long long M, int K, int Kp) {
+    pdl_launch_next();
+    pdl_wait_prev();
     const int lane = threadIdx.x & 31;
     const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (row >= M) return;

@@ -66,12 +66,14 @@ k_scan_step_bulk(const float* __restrict__ u, const float* __restrict__ xz, cons
     };
 
     int issued = 0;
+    pdl_launch_next();
     if (tid == 0) {
         for (int i = 0; i < stages; i++) mbar_init(&full[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    pdl_wait_prev();                             // u, z, dbc and the state come from earlier kernels
     if (tid == 0)
         for (; issued < min(stages, mine); issued++) issue(issued);
 

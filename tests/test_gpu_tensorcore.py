@@ -73,10 +73,15 @@ def test_gemm_kernels(api, shape, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
-def test_gemm_rows_independent_of_batch(api, precision):
+@pytest.mark.parametrize("NK", [(1024, 256), (48, 512), (256, 512)])
+def test_gemm_rows_independent_of_batch(api, precision, NK):
+    """Also under split K (N = 48: four CTAs per cluster reduce their partial
+    tiles through distributed shared memory), whose reduction order is fixed
+    by (N, K) alone."""
+    N, K = NK
     g = np.random.default_rng(5)
-    A = g.normal(0, 1, (1000, 256)).astype(np.float32)
-    W = g.normal(0, 0.05, (1024, 256)).astype(np.float32)
+    A = g.normal(0, 1, (1000, K)).astype(np.float32)
+    W = g.normal(0, 0.05, (N, K)).astype(np.float32)
     full = api.gemm(A, W, precision=precision)
     for lo, hi in ((0, 1), (5, 133), (999, 1000), (300, 428)):
         part = api.gemm(A[lo:hi], W, precision=precision)
