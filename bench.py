@@ -320,6 +320,11 @@ def run_boa(args):
         return sizes, n1 + model.last_launch_count
 
     tuning = model.autotune(len(streams), args.stream_len) if args.autotune else None
+    if args.decode_lanes is not None or args.scan_variant is not None:
+        t = model.tuning()
+        model.set_tuning(t["max_rows"], t["scan_variant"] if args.scan_variant is None else args.scan_variant,
+                         t["decode_lanes"] if args.decode_lanes is None else args.decode_lanes)
+        tuning = dict(tuning or {}, **model.tuning(), overridden=True)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -496,6 +501,8 @@ def main():
     ap.add_argument("--forms", default="fp32,bf16,fp8", help="other precision forms to report ('' for none)")
     ap.add_argument("--report", default="", choices=["", "precision"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--decode-lanes", type=int, default=None, help="override the tuned decode lane count")
+    ap.add_argument("--scan-variant", type=int, default=None, help="override the tuned decode scan kernel")
     ap.add_argument("--cpu-prefix", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

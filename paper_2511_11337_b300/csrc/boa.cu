@@ -138,6 +138,7 @@ struct boa_model {
     int precision = BOA_PREC_FP32;
     int d = 0, nl = 0, N = 0, K = 0, E = 0, r = 0, ffn_mult = 0, F = 0, R2 = 0;
     uint64_t fingerprint = 0;
+    size_t n_params = 0;            // floats in the weight file's tensor array
     int num_sms = 148;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -319,50 +320,16 @@ static void transpose(const float* src, int rows, int cols, float* dst) {
         for (int j = 0; j < cols; j++) dst[(size_t)j * rows + i] = src[(size_t)i * cols + j];
 }
 
-extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa_model** out) {
-    if (!path || !out) return fail(BOA_ERR_ARG, "boa_load_model: null argument");
-    FILE* fp = fopen(path, "rb");
-    if (!fp) return fail(BOA_ERR_IO, "cannot open weight file %s", path);
-    std::vector<uint8_t> buf;
-    {
-        fseek(fp, 0, SEEK_END);
-        long sz = ftell(fp);
-        fseek(fp, 0, SEEK_SET);
-        if (sz < 40) { fclose(fp); return fail(BOA_ERR_FORMAT, "weight file too short"); }
-        buf.resize((size_t)sz);
-        size_t got = fread(buf.data(), 1, buf.size(), fp);
-        fclose(fp);
-        if (got != buf.size()) return fail(BOA_ERR_IO, "short read on %s", path);
-    }
-    if (memcmp(buf.data(), "BOAW", 4) != 0) return fail(BOA_ERR_FORMAT, "bad magic");
-    uint32_t hdr[9];
-    memcpy(hdr, buf.data() + 4, sizeof hdr);
-    if (hdr[0] != 1) return fail(BOA_ERR_FORMAT, "unsupported version %u", hdr[0]);
-    const int vocab = (int)hdr[1], d = (int)hdr[2], nl = (int)hdr[3], N = (int)hdr[4], K = (int)hdr[5];
-    const int expand = (int)hdr[6], r = (int)hdr[7], ffn = (int)hdr[8];
-    const int E = expand * d, F = ffn * d, R2 = r + 2 * N;
-    if (vocab != 256 || nl < 1 || nl > 64 || expand < 1 || expand > 4 || r != (d + 15) / 16)
-        return fail(BOA_ERR_FORMAT, "unsupported header (vocab %d, layers %d, expand %d, dt_rank %d)", vocab, nl, expand, r);
-    if (!supported_d(d) || !supported_scan(N, r) || K < 2 || K > 4 || (ffn != 0 && ffn != 2 && ffn != 4))
-        return fail(BOA_ERR_FORMAT, "unsupported shape d=%d N=%d r=%d K=%d ffn=%d", d, N, r, K, ffn);
-
-    const size_t per_layer = 2 * (size_t)d + 2 * (size_t)E * d + (size_t)E * K + E + (size_t)R2 * E +
-                             (size_t)E * r + E + (size_t)E * N + E + (size_t)d * E +
-                             (F ? (size_t)F * d + F + (size_t)d * F + d : 0) + 2 * (size_t)d;
-    const size_t total = 256 * (size_t)d + nl * per_layer + 256 * (size_t)d + 256;
-    if (buf.size() != 40 + total * 4) return fail(BOA_ERR_FORMAT, "weight file size %zu, expected %zu", buf.size(), 40 + total * 4);
-
-    boa_opts o = {0, BOA_PREC_FP32, nullptr, 0, 0};
-    if (opts) o = *opts;
-    if (o.precision < BOA_PREC_FP32 || o.precision > BOA_PREC_FP8)
-        return fail(BOA_ERR_ARG, "precision %d not supported", o.precision);
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(BOA_ERR_CUDA, "no CUDA device available");
-    if (o.device < 0 || o.device >= ndev) return fail(BOA_ERR_ARG, "bad device %d", o.device);
-    CU(cudaSetDevice(o.device));
-
+// (Re)build every device copy of the weights from the file-layout array src:
+// the FP32 arrays (projection matrices K-major, A scaled by log2(e)) and the
+// precision form's copies.  Allocations happen on the first call and are
+// reused afterwards (training refreshes the copies after each step).
+static boa_status upload_weights(boa_model* m, const float* src) {
+    const int d = m->d, nl = m->nl, N = m->N, K = m->K, E = m->E, r = m->r, F = m->F, R2 = m->R2;
+    const size_t total = m->n_params;
+    if (d <= 0 || nl <= 0 || N <= 0 || K <= 0 || E <= 0 || r <= 0 || F < 0 || R2 <= 0)
+        return fail(BOA_ERR_ARG, "model shapes not set");
     // Host-side rearrangement: weight matrices K-major, A pre-scaled by log2(e).
-    const float* src = reinterpret_cast<const float*>(buf.data() + 40);
     std::vector<float> dev(total);
     size_t so = 0, dof = 0;
     auto copy = [&](size_t n) { size_t at = dof; memcpy(&dev[dof], src + so, n * 4); so += n; dof += n; return at; };
@@ -406,28 +373,8 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
     size_t head_o = copy_t(256, d);
     size_t head_b_o = copy(256);
 
-    boa_model* m = new boa_model();
-    m->device = o.device;
-    m->precision = o.precision;
-    if (o.max_rows) m->max_rows = std::max<size_t>(o.max_rows, 1);
-    if (o.max_slots) m->max_slots = std::max<size_t>(o.max_slots, 1);
-    m->d = d; m->nl = nl; m->N = N; m->K = K; m->E = E; m->r = r; m->ffn_mult = ffn; m->F = F; m->R2 = R2;
-    m->fingerprint = fnv1a64(buf.data(), buf.size());
-    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, o.device);
-    if (o.cuda_stream) {
-        m->stream = (cudaStream_t)o.cuda_stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            delete m;
-            return fail(BOA_ERR_CUDA, "cudaStreamCreate failed");
-        }
-        m->own_stream = true;
-    }
-    if (cudaMalloc(&m->weights, total * 4) != cudaSuccess ||
-        cudaMemcpy(m->weights, dev.data(), total * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
-        boa_free_model(m);
-        return fail(BOA_ERR_OOM, "weight upload failed");
-    }
+    if (!m->weights) CU(cudaMalloc(&m->weights, total * 4));
+    CU(cudaMemcpy(m->weights, dev.data(), total * 4, cudaMemcpyHostToDevice));
     float* w = m->weights;
     m->embed = w + embed_o;
     m->head_wt = w + head_o;
@@ -460,11 +407,8 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
         std::vector<__nv_bfloat16> hb(tot, __float2bfloat16_rn(0.f));
         for (size_t i = 0; i < mats.size(); i++)
             for (size_t j = 0; j < mats[i].second; j++) hb[at[i] + j] = __float2bfloat16_rn(src[mats[i].first + j]);
-        if (cudaMalloc(&m->wb, tot * 2) != cudaSuccess ||
-            cudaMemcpy(m->wb, hb.data(), tot * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
-            boa_free_model(m);
-            return fail(BOA_ERR_OOM, "bf16 weight upload failed");
-        }
+        if (!m->wb) CU(cudaMalloc(&m->wb, tot * 2));
+        CU(cudaMemcpy(m->wb, hb.data(), tot * 2, cudaMemcpyHostToDevice));
         size_t k = 0;
         m->blayers.resize(nl);
         for (int l = 0; l < nl; l++) {
@@ -504,11 +448,8 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
                 hb[at[i] + half + j] = x - hi;
             }
         }
-        if (cudaMalloc(&m->w3, tot * 4) != cudaSuccess ||
-            cudaMemcpy(m->w3, hb.data(), tot * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
-            boa_free_model(m);
-            return fail(BOA_ERR_OOM, "tf32 weight upload failed");
-        }
+        if (!m->w3) CU(cudaMalloc(&m->w3, tot * 4));
+        CU(cudaMemcpy(m->w3, hb.data(), tot * 4, cudaMemcpyHostToDevice));
         size_t k = 0;
         auto pair = [&](float*& hi, float*& lo) {
             const size_t half = (mats[k].second + 31) / 32 * 32;
@@ -560,12 +501,10 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
                     hq[atb[i] + rr * kpad(Cc) + k] = (uint8_t)__nv_cvt_float_to_fp8(w[k] * inv, __NV_SATFINITE, __NV_E4M3);
             }
         }
-        if (cudaMalloc(&m->w8, tb) != cudaSuccess || cudaMalloc(&m->w8s, ts * 4) != cudaSuccess ||
-            cudaMemcpy(m->w8, hq.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(m->w8s, hs.data(), ts * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
-            boa_free_model(m);
-            return fail(BOA_ERR_OOM, "fp8 weight upload failed");
-        }
+        if (!m->w8) CU(cudaMalloc(&m->w8, tb));
+        if (!m->w8s) CU(cudaMalloc(&m->w8s, ts * 4));
+        CU(cudaMemcpy(m->w8, hq.data(), tb, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(m->w8s, hs.data(), ts * 4, cudaMemcpyHostToDevice));
         size_t k = 0;
         auto q = [&](const __nv_fp8_e4m3*& w, const float*& sc) {
             w = reinterpret_cast<const __nv_fp8_e4m3*>(m->w8 + atb[k]);
@@ -583,6 +522,75 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
             if (F) { q(Q.w1, Q.w1_s); q(Q.w2, Q.w2_s); }
         }
         q(m->head_w8, m->head_s);
+    }
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa_model** out) {
+    if (!path || !out) return fail(BOA_ERR_ARG, "boa_load_model: null argument");
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(BOA_ERR_IO, "cannot open weight file %s", path);
+    std::vector<uint8_t> buf;
+    {
+        fseek(fp, 0, SEEK_END);
+        long sz = ftell(fp);
+        fseek(fp, 0, SEEK_SET);
+        if (sz < 40) { fclose(fp); return fail(BOA_ERR_FORMAT, "weight file too short"); }
+        buf.resize((size_t)sz);
+        size_t got = fread(buf.data(), 1, buf.size(), fp);
+        fclose(fp);
+        if (got != buf.size()) return fail(BOA_ERR_IO, "short read on %s", path);
+    }
+    if (memcmp(buf.data(), "BOAW", 4) != 0) return fail(BOA_ERR_FORMAT, "bad magic");
+    uint32_t hdr[9];
+    memcpy(hdr, buf.data() + 4, sizeof hdr);
+    if (hdr[0] != 1) return fail(BOA_ERR_FORMAT, "unsupported version %u", hdr[0]);
+    const int vocab = (int)hdr[1], d = (int)hdr[2], nl = (int)hdr[3], N = (int)hdr[4], K = (int)hdr[5];
+    const int expand = (int)hdr[6], r = (int)hdr[7], ffn = (int)hdr[8];
+    const int E = expand * d, F = ffn * d, R2 = r + 2 * N;
+    if (vocab != 256 || nl < 1 || nl > 64 || expand < 1 || expand > 4 || r != (d + 15) / 16)
+        return fail(BOA_ERR_FORMAT, "unsupported header (vocab %d, layers %d, expand %d, dt_rank %d)", vocab, nl, expand, r);
+    if (!supported_d(d) || !supported_scan(N, r) || K < 2 || K > 4 || (ffn != 0 && ffn != 2 && ffn != 4))
+        return fail(BOA_ERR_FORMAT, "unsupported shape d=%d N=%d r=%d K=%d ffn=%d", d, N, r, K, ffn);
+
+    const size_t per_layer = 2 * (size_t)d + 2 * (size_t)E * d + (size_t)E * K + E + (size_t)R2 * E +
+                             (size_t)E * r + E + (size_t)E * N + E + (size_t)d * E +
+                             (F ? (size_t)F * d + F + (size_t)d * F + d : 0) + 2 * (size_t)d;
+    const size_t total = 256 * (size_t)d + nl * per_layer + 256 * (size_t)d + 256;
+    if (buf.size() != 40 + total * 4) return fail(BOA_ERR_FORMAT, "weight file size %zu, expected %zu", buf.size(), 40 + total * 4);
+
+    boa_opts o = {0, BOA_PREC_FP32, nullptr, 0, 0};
+    if (opts) o = *opts;
+    if (o.precision < BOA_PREC_FP32 || o.precision > BOA_PREC_FP8)
+        return fail(BOA_ERR_ARG, "precision %d not supported", o.precision);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(BOA_ERR_CUDA, "no CUDA device available");
+    if (o.device < 0 || o.device >= ndev) return fail(BOA_ERR_ARG, "bad device %d", o.device);
+    CU(cudaSetDevice(o.device));
+
+    boa_model* m = new boa_model();
+    m->device = o.device;
+    m->precision = o.precision;
+    if (o.max_rows) m->max_rows = std::max<size_t>(o.max_rows, 1);
+    if (o.max_slots) m->max_slots = std::max<size_t>(o.max_slots, 1);
+    m->d = d; m->nl = nl; m->N = N; m->K = K; m->E = E; m->r = r; m->ffn_mult = ffn; m->F = F; m->R2 = R2;
+    m->fingerprint = fnv1a64(buf.data(), buf.size());
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, o.device);
+    if (o.cuda_stream) {
+        m->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete m;
+            return fail(BOA_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        m->own_stream = true;
+    }
+    const float* src = reinterpret_cast<const float*>(buf.data() + 40);
+    m->n_params = total;
+    const boa_status ws = upload_weights(m, src);
+    if (ws != BOA_OK) {
+        boa_free_model(m);
+        return ws;
     }
     *out = m;
     return BOA_OK;
@@ -821,13 +829,16 @@ static boa_status gemm_t3(boa_model* m, int cls, const float* A, const float* Wh
     const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
     ProfScope ps(m, cls, 2.0 * M * N * K,
                  4.0 * ((double)M * K + 2.0 * K * N) + 4.0 * (double)M * N * (resid ? 2 : 1));
-    const int BN = N > 48 ? 64 : 48;
+    const int BN = tc_bn(N);
     CUtensorMap ta, th, tl;
     TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, 4, &ta));
     TRY(tmap_2d(m, Whi, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 4, &th));
     TRY(tmap_2d(m, Wlo, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 4, &tl));
-    if (BN == 48) launch_t3<48, EPI>(m, ta, th, tl, bias, C, M, N, K);
-    else launch_t3<64, EPI>(m, ta, th, tl, bias, C, M, N, K);
+    switch (BN) {
+        case 48: launch_t3<48, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
+        case 64: launch_t3<64, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
+        default: launch_t3<128, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
+    }
     return check_launch(m, "gemm_t3");
 }
 

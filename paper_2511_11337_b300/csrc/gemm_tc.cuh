@@ -512,7 +512,10 @@ struct T3Smem {
     static constexpr int kA = kTcBM * kT3BK * 4;     // 16 KB (fp32 -> hi in place)
     static constexpr int kB = BN * kT3BK * 4;
     static constexpr int kStage = 2 * kA + 2 * kB;   // A_hi, A_lo, B_hi, B_lo
-    static constexpr int kStages = DEEP ? (200 * 1024) / kStage : 2;
+    // two CTAs per SM with two stages each where they fit (BN <= 64);
+    // otherwise (deep grids, or BN = 128) one CTA with up to ~200 KB of stages
+    static constexpr bool kOnePerSm = DEEP || 2 * kStage > 110 * 1024;
+    static constexpr int kStages = kOnePerSm ? ((200 * 1024) / kStage > 8 ? 8 : (200 * 1024) / kStage) : 2;
     static constexpr int kTmemCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     static constexpr int kBars = 3 * kStages + 1;    // full, converted, empty, done
     static constexpr size_t kBytes = 1024 + (size_t)kStages * kStage + 8 * kBars + 16;
