@@ -262,11 +262,46 @@ boa_status boa_scan_train_bwd(size_t Bsz, size_t T, size_t E, size_t N, size_t c
                               float* du, float* ddelta, float* dA_part, float* dD_part, float* dB_part,
                               float* dC_part, void* cuda_stream);
 
+/* One training step of the predictor (paper, "Entropy-Based Compression and
+ * Cross-Entropy Loss": minimising the base-256 cross-entropy minimises the
+ * code length), entirely in the library's kernels: the forward over
+ * n_seq x (seqlen - 1) rows, the reverse-mode gradient of the mean
+ * cross-entropy in bytes per byte, -log_256 Q(y_t | y_<t) averaged over
+ * every predicted position, and one AdamW step (betas 0.9 / 0.999, eps 1e-8,
+ * decoupled weight decay 0.01 on every tensor, bias-corrected) of the weight
+ * file's tensor array with learning rate lr.  The model then uses the
+ * updated weights (its device copies in every precision form are rebuilt)
+ * and its fingerprint becomes that of the file boa_save_model would write.
+ * FP32 throughout, sums in a fixed order (the same batch gives the same
+ * update bit for bit); the Adam moments live in the model.
+ * batch: host, n_seq x seqlen bytes, row-major; sequence b predicts its
+ * bytes 1..seqlen-1 from their prefixes.  loss_out (host, may be NULL): the
+ * loss before the update.  Blocks with an FFN (ffn_mult > 0) are not
+ * supported; at most 2^22 predicted positions per batch.  Memory: about
+ * 80 bytes x E per predicted position on the device.
+ * Errors: BOA_ERR_ARG, BOA_ERR_CUDA, BOA_ERR_OOM. */
+boa_status boa_train_step(boa_model* model, const uint8_t* batch, size_t n_seq, size_t seqlen, float lr,
+                          float* loss_out);
+
+/* Write the model's current weights as a weight file (header of the file it
+ * was loaded from, then its tensor array).  Errors: BOA_ERR_ARG, BOA_ERR_IO. */
+boa_status boa_save_model(const boa_model* model, const char* path);
+
+/* Number of floats in the model's tensor array (the weight file's layout). */
+size_t boa_model_param_count(const boa_model* model);
+
 /* Thread-local message describing the last error on this thread. */
 const char* boa_last_error(void);
 
 /* ----------------------------------------------------------- test hooks
  * Exposed for parity tests; not part of the compression API. */
+
+/* The loss and gradient boa_train_step would use for this batch, without
+ * updating anything: grad_out (host, boa_model_param_count floats, may be
+ * NULL) in the weight file's layout, the gradient of the mean base-256
+ * cross-entropy; loss_out (host, may be NULL).  Errors as boa_train_step. */
+boa_status boa_debug_train_grad(boa_model* model, const uint8_t* batch, size_t n_seq, size_t seqlen,
+                                float* grad_out, float* loss_out);
 
 /* Range-code given integer CDFs on the GPU (section "Range coding",
  * paragraphs "Encoder" and "Decoder").  n_seq independent sequences; sequence

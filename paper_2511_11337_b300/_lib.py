@@ -24,6 +24,10 @@ SIGNATURES = {
     "boa_decompress_device": (i32, [vp, sz, vp, vp, vp, vp, vp, vp]),
     "boa_last_launch_count": (u64, [vp]),
     "boa_last_error": (C.c_char_p, []),
+    "boa_train_step": (i32, [vp, vp, sz, sz, C.c_float, vp]),
+    "boa_save_model": (i32, [vp, C.c_char_p]),
+    "boa_model_param_count": (sz, [vp]),
+    "boa_debug_train_grad": (i32, [vp, vp, sz, sz, vp, vp]),
     "boa_autotune": (i32, [vp, sz, sz, vp]),
     "boa_set_tuning": (i32, [vp, vp]),
     "boa_get_tuning": (i32, [vp, vp]),

@@ -147,6 +147,31 @@ class Model:
                 "decode_lanes": int(t.decode_lanes), "compress_ms_est": t.compress_ms,
                 "decompress_ms_est": t.decompress_ms}
 
+    # ----------------------------------------------------------- training
+    @property
+    def param_count(self) -> int:
+        return int(load().boa_model_param_count(self._h))
+
+    def train_step(self, batch: np.ndarray, lr: float) -> float:
+        """boa_train_step on a [n_seq, seqlen] uint8 batch; returns the loss
+        (bytes per byte) before the update."""
+        b = np.ascontiguousarray(batch, np.uint8)
+        loss = C.c_float()
+        check(load().boa_train_step(self._h, _p(b), b.shape[0], b.shape[1], C.c_float(lr), C.byref(loss)))
+        return float(loss.value)
+
+    def train_grad(self, batch: np.ndarray) -> tuple[float, np.ndarray]:
+        """boa_debug_train_grad: (loss, gradient in the weight file's layout)."""
+        b = np.ascontiguousarray(batch, np.uint8)
+        g = np.zeros(self.param_count, np.float32)
+        loss = C.c_float()
+        check(load().boa_debug_train_grad(self._h, _p(b), b.shape[0], b.shape[1], _p(g), C.byref(loss)))
+        return float(loss.value), g
+
+    def save(self, path: str) -> None:
+        """boa_save_model: write the current weights as a weight file."""
+        check(load().boa_save_model(self._h, os.fsencode(path)))
+
     def set_tuning(self, max_rows: int, scan_variant: int, decode_lanes: int = 0) -> None:
         """boa_set_tuning: apply a launch configuration (results do not depend on it)."""
         t = _Tuning(max_rows, scan_variant, decode_lanes, 0.0, 0.0)

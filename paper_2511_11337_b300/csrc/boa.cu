@@ -31,6 +31,7 @@
 #include "kernels.cuh"
 #include "scan_step.cuh"
 #include "scan_train.cuh"
+#include "train_step.cuh"
 
 using namespace boa;
 
@@ -133,6 +134,8 @@ struct View {
     cudaStream_t stream = nullptr;
 };
 
+struct TrainState;                 // native training step (boa_train_step)
+
 struct boa_model {
     int device = 0;
     int precision = BOA_PREC_FP32;
@@ -210,17 +213,21 @@ struct boa_model {
     View v;                         // what the launchers work on
     std::vector<cudaStream_t> lane_streams;
     std::vector<cudaEvent_t> lane_events;   // [0] fork, [1 + p] lane p done
+    uint32_t header[9] = {};        // the weight file's header words after the magic
+    std::vector<float> params;      // the weight file's tensor array (host copy)
+    TrainState* tr = nullptr;
     uint64_t prof_steps[2][2] = {};         // [phase][timed, all] steps of the step loops
 };
 
-static uint64_t fnv1a64(const uint8_t* p, size_t n) {
-    uint64_t h = 1469598103934665603ull;
+static uint64_t fnv1a64_update(uint64_t h, const uint8_t* p, size_t n) {
     for (size_t i = 0; i < n; i++) {
         h ^= p[i];
         h *= 1099511628211ull;
     }
     return h;
 }
+
+static uint64_t fnv1a64(const uint8_t* p, size_t n) { return fnv1a64_update(1469598103934665603ull, p, n); }
 
 // ---- kernel-class profiling: an event pair around each timed launch.
 static const size_t kMaxProfEvents = 1u << 17;
@@ -286,6 +293,8 @@ extern "C" uint64_t boa_model_fingerprint(const boa_model* m) { return m ? m->fi
 
 extern "C" uint64_t boa_last_launch_count(const boa_model* m) { return m ? m->launches : 0; }
 
+static void free_train_state(boa_model* m);
+
 static void free_workspace(boa_model* m) {
     m->x.release(); m->xn.release(); m->xz.release(); m->u.release(); m->dbc.release();
     m->yg.release(); m->logits.release(); m->hid.release(); m->h.release(); m->conv.release();
@@ -310,6 +319,7 @@ extern "C" void boa_free_model(boa_model* m) {
     if (m->w3) cudaFree(m->w3);
     if (m->w8) cudaFree(m->w8);
     if (m->w8s) cudaFree(m->w8s);
+    free_train_state(m);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -575,6 +585,7 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
     if (o.max_slots) m->max_slots = std::max<size_t>(o.max_slots, 1);
     m->d = d; m->nl = nl; m->N = N; m->K = K; m->E = E; m->r = r; m->ffn_mult = ffn; m->F = F; m->R2 = R2;
     m->fingerprint = fnv1a64(buf.data(), buf.size());
+    memcpy(m->header, hdr, sizeof hdr);
     cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, o.device);
     if (o.cuda_stream) {
         m->stream = (cudaStream_t)o.cuda_stream;
@@ -587,6 +598,7 @@ extern "C" boa_status boa_load_model(const char* path, const boa_opts* opts, boa
     }
     const float* src = reinterpret_cast<const float*>(buf.data() + 40);
     m->n_params = total;
+    m->params.assign(src, src + total);
     const boa_status ws = upload_weights(m, src);
     if (ws != BOA_OK) {
         boa_free_model(m);
@@ -2287,5 +2299,329 @@ extern "C" boa_status boa_unpack(boa_model* m, const uint8_t* c, size_t size, ui
     }
     if (n) TRY(boa_decompress(m, n, ptrs.data(), sizes.data(), lens.data(), outs.data()));
     *out_len = total;
+    return BOA_OK;
+}
+
+// ------------------------------------------------------------ training step
+//
+// boa_train_step: the predictor's forward over n_seq x (seqlen - 1) rows
+// keeping its intermediates, the gradient of the mean base-256
+// cross-entropy, and one AdamW step of the weight file's tensor array; the
+// device copies of the weights are then rebuilt from the updated array.
+// FP32 throughout, fixed reduction order (kernels in train_step.cuh).
+
+// Offsets of every tensor in the weight file's array.
+struct FileOffsets {
+    struct Layer { size_t ln_a_w, ln_a_b, in_w, conv_w, conv_b, x_w, dt_w, dt_b, A_log, D, out_w, ln_b_w, ln_b_b; };
+    size_t embed = 0, head_w = 0, head_b = 0;
+    std::vector<Layer> layers;
+};
+
+static FileOffsets file_offsets(const boa_model* m) {
+    const size_t d = m->d, E = m->E, N = m->N, K = m->K, r = m->r, R2 = m->R2, F = m->F;
+    FileOffsets fo;
+    size_t o = 0;
+    auto take = [&](size_t n) { size_t at = o; o += n; return at; };
+    fo.embed = take(256 * d);
+    fo.layers.resize(m->nl);
+    for (auto& L : fo.layers) {
+        L.ln_a_w = take(d); L.ln_a_b = take(d);
+        L.in_w = take(2 * E * d);
+        L.conv_w = take(E * K); L.conv_b = take(E);
+        L.x_w = take(R2 * E);
+        L.dt_w = take(E * r); L.dt_b = take(E);
+        L.A_log = take(E * N); L.D = take(E);
+        L.out_w = take(d * E);
+        if (F) take(F * d + F + d * F + d);
+        L.ln_b_w = take(d); L.ln_b_b = take(d);
+    }
+    fo.head_w = take(256 * d);
+    fo.head_b = take(256);
+    return fo;
+}
+
+struct TrainState {
+    size_t rows = 0;                 // capacity of the row buffers
+    int bsz = 0, T = 0;
+    DevBuf<float> master, grad, m1, m2;
+    DevBuf<uint8_t> tok;
+    // per layer
+    std::vector<DevBuf<float>> X, XN, mA, rA, XZ, CPRE, U, DBC, DPRE, DELTA, AN, BM, CM, YS, HIN, YG, URES, mB, rB;
+    // shared by the backward
+    DevBuf<float> logits, dlogits, loss_rows, loss, dX, dXin, dU, dCPRE, dXZ, dYG, dYS, dDELTA, dDPRE, dDBC, dDL,
+        dXN, dyxh, dURES, hs, dA_part, dD_part, dB_part, dC_part, part;
+    uint64_t step = 0;
+};
+
+static void free_train_state(boa_model* m) {
+    delete m->tr;
+    m->tr = nullptr;
+}
+
+static const int kTrainChunk = 256;        // scan backward recomputation chunk
+static const long long kTrRowsPerPart = 4096;
+
+// Train on n_seq sequences of seqlen bytes (device copy of the batch in
+// tr->tok); fills tr->grad and tr->loss.
+static boa_status train_forward_backward(boa_model* m, int bsz, int T, int seqlen) {
+    TrainState& t = *m->tr;
+    const long long rows = (long long)bsz * T;
+    const int d = m->d, E = m->E, N = m->N, K = m->K, r = m->r, R2 = m->R2, nl = m->nl;
+    const FileOffsets fo = file_offsets(m);
+    const float* P = t.master.p;
+    float* G = t.grad.p;
+    cudaStream_t st = m->stream;
+    const uint8_t* tok = t.tok.p;
+    auto blocks = [](long long n, int b) { return (unsigned)((n + b - 1) / b); };
+    auto nn = [&](int M, int Nn, int Kk, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                  const float* bias, int acc) {
+        dim3 g(blocks(Nn, kTrTile), blocks(M, kTrTile));
+        k_tr_gemm_nn<<<g, 256, 0, st>>>(M, Nn, Kk, A, lda, B, ldb, C, ldc, bias, acc);
+    };
+    const int nparts = (int)((rows + kTrRowsPerPart - 1) / kTrRowsPerPart);
+    // out[Nn][Kk] = A^T B over all rows (A rows x Nn, B rows x Kk)
+    auto tn = [&](int Nn, int Kk, const float* A, int lda, const float* B, int ldb, float* out) {
+        dim3 g(blocks(Kk, kTrTile), blocks(Nn, kTrTile), nparts);
+        k_tr_gemm_tn<<<g, 256, 0, st>>>(rows, Nn, Kk, A, lda, B, ldb, t.part.p, kTrRowsPerPart);
+        const size_t cnt = (size_t)Nn * Kk;
+        k_tr_reduce<<<blocks((long long)cnt, 256), 256, 0, st>>>(t.part.p, nparts, cnt, out, 0, nullptr);
+    };
+    auto colsum = [&](const float* A, int n, int lda, float* out) {
+        dim3 g(blocks(n, 128), nparts);
+        k_tr_colsum<<<g, 128, 0, st>>>(A, rows, n, lda, t.part.p, kTrRowsPerPart);
+        k_tr_reduce<<<blocks(n, 256), 256, 0, st>>>(t.part.p, nparts, (size_t)n, out, 0, nullptr);
+    };
+    const unsigned warps_grid = blocks(rows, 8);   // one warp per row, 8 per CTA
+
+    // ---- forward
+    k_tr_embed<<<blocks(rows * d, 256), 256, 0, st>>>(tok, T, seqlen, P + fo.embed, t.X[0].p, rows, d);
+    for (int l = 0; l < nl; l++) {
+        const auto& o = fo.layers[l];
+        const DevLayer& L = m->layers[l];
+        k_tr_ln_fwd<<<warps_grid, 256, 0, st>>>(t.X[l].p, P + o.ln_a_w, P + o.ln_a_b, t.XN[l].p, t.mA[l].p, t.rA[l].p,
+                                                rows, d);
+        nn((int)rows, 2 * E, d, t.XN[l].p, d, L.in_wt, 2 * E, t.XZ[l].p, 2 * E, nullptr, 0);
+        k_tr_conv_fwd<<<dim3(blocks(E, 128), bsz), 128, 0, st>>>(t.XZ[l].p, E, P + o.conv_w, P + o.conv_b,
+                                                                  t.CPRE[l].p, t.U[l].p, T, K);
+        nn((int)rows, R2, E, t.U[l].p, E, L.x_wt, R2, t.DBC[l].p, R2, nullptr, 0);
+        nn((int)rows, E, r, t.DBC[l].p, R2, L.dt_w, E, t.DPRE[l].p, E, P + o.dt_b, 0);
+        k_tr_softplus<<<blocks(rows * E, 256), 256, 0, st>>>(t.DPRE[l].p, t.DELTA[l].p, (size_t)rows * E);
+        k_tr_neg_exp<<<blocks((long long)E * N, 256), 256, 0, st>>>(P + o.A_log, t.AN[l].p, (size_t)E * N);
+        k_tr_split_bc<<<blocks(rows * N, 256), 256, 0, st>>>(t.DBC[l].p, r, N, t.BM[l].p, t.CM[l].p, rows);
+        k_scan_train_fwd<16><<<dim3(blocks(E, kTrainThreads), bsz), kTrainThreads, 0, st>>>(
+            T, E, kTrainChunk, t.U[l].p, t.DELTA[l].p, t.AN[l].p, t.BM[l].p, t.CM[l].p, P + o.D, t.YS[l].p, t.HIN[l].p);
+        k_tr_gate_fwd<<<blocks(rows * E, 256), 256, 0, st>>>(t.YS[l].p, t.XZ[l].p, E, t.YG[l].p, rows);
+        CU(cudaMemcpyAsync(t.URES[l].p, t.X[l].p, (size_t)rows * d * 4, cudaMemcpyDeviceToDevice, st));
+        nn((int)rows, d, E, t.YG[l].p, E, L.out_wt, d, t.URES[l].p, d, nullptr, 1);
+        k_tr_ln_fwd<<<warps_grid, 256, 0, st>>>(t.URES[l].p, P + o.ln_b_w, P + o.ln_b_b, t.X[l + 1].p, t.mB[l].p,
+                                                t.rB[l].p, rows, d);
+    }
+    nn((int)rows, 256, d, t.X[nl].p, d, m->head_wt, 256, t.logits.p, 256, P + fo.head_b, 0);
+    const float scale = (float)(1.0 / ((double)rows * std::log(256.0)));
+    k_tr_xent<<<warps_grid, 256, 0, st>>>(t.logits.p, tok, T, seqlen, t.dlogits.p, t.loss_rows.p, rows, scale);
+    k_tr_sum<<<1, kTrBlock, 0, st>>>(t.loss_rows.p, rows, t.loss.p);
+
+    // ---- backward
+    tn(256, d, t.dlogits.p, 256, t.X[nl].p, d, G + fo.head_w);
+    colsum(t.dlogits.p, 256, 256, G + fo.head_b);
+    nn((int)rows, d, 256, t.dlogits.p, 256, P + fo.head_w, d, t.dX.p, d, nullptr, 0);
+    const int nblk = (E + kTrainThreads - 1) / kTrainThreads;
+    for (int l = nl - 1; l >= 0; l--) {
+        const auto& o = fo.layers[l];
+        // LN_b
+        k_tr_ln_bwd<<<warps_grid, 256, 0, st>>>(t.dX.p, t.URES[l].p, t.mB[l].p, t.rB[l].p, P + o.ln_b_w, t.dURES.p,
+                                                t.dyxh.p, rows, d, 0);
+        colsum(t.dyxh.p, d, d, G + o.ln_b_w);
+        colsum(t.dX.p, d, d, G + o.ln_b_b);
+        // residual: the block input receives dURES directly
+        CU(cudaMemcpyAsync(t.dXin.p, t.dURES.p, (size_t)rows * d * 4, cudaMemcpyDeviceToDevice, st));
+        // out_proj
+        tn(d, E, t.dURES.p, d, t.YG[l].p, E, G + o.out_w);
+        nn((int)rows, E, d, t.dURES.p, d, P + o.out_w, E, t.dYG.p, E, nullptr, 0);
+        // gate
+        k_tr_gate_bwd<<<blocks(rows * E, 256), 256, 0, st>>>(t.dYG.p, t.YS[l].p, t.XZ[l].p, E, t.dYS.p, t.dXZ.p, rows);
+        // scan
+        k_scan_train_bwd<16><<<dim3(blocks(E, kTrainThreads), bsz), kTrainThreads, 0, st>>>(
+            T, E, kTrainChunk, t.U[l].p, t.DELTA[l].p, t.AN[l].p, t.BM[l].p, t.CM[l].p, P + o.D, t.dYS.p, t.HIN[l].p,
+            t.hs.p, t.dU.p, t.dDELTA.p, t.dA_part.p, t.dD_part.p, t.dB_part.p, t.dC_part.p);
+        k_tr_reduce<<<blocks(E, 256), 256, 0, st>>>(t.dD_part.p, bsz, (size_t)E, G + o.D, 0, nullptr);
+        k_tr_reduce<<<blocks((long long)E * N, 256), 256, 0, st>>>(t.dA_part.p, bsz, (size_t)E * N, G + o.A_log, 0,
+                                                                    t.AN[l].p);   // dA/dA_log = A
+        // softplus, dt_proj
+        k_tr_softplus_bwd<<<blocks(rows * E, 256), 256, 0, st>>>(t.dDELTA.p, t.DPRE[l].p, t.dDPRE.p, (size_t)rows * E);
+        tn(E, r, t.dDPRE.p, E, t.DBC[l].p, R2, G + o.dt_w);
+        colsum(t.dDPRE.p, E, E, G + o.dt_b);
+        nn((int)rows, r, E, t.dDPRE.p, E, P + o.dt_w, r, t.dDL.p, r, nullptr, 0);
+        // x_proj
+        k_tr_assemble_ddbc<<<blocks(rows * R2, 256), 256, 0, st>>>(t.dDL.p, t.dB_part.p, t.dC_part.p, nblk, r, N,
+                                                                    t.dDBC.p, rows);
+        tn(R2, E, t.dDBC.p, R2, t.U[l].p, E, G + o.x_w);
+        nn((int)rows, E, R2, t.dDBC.p, R2, P + o.x_w, E, t.dU.p, E, nullptr, 1);
+        // SiLU, conv
+        k_tr_silu_bwd<<<blocks(rows * E, 256), 256, 0, st>>>(t.dU.p, t.CPRE[l].p, t.dCPRE.p, (size_t)rows * E);
+        k_tr_conv_bwd<<<dim3(blocks(E, 128), bsz), 128, 0, st>>>(t.dCPRE.p, P + o.conv_w, t.dXZ.p, T, E, K);
+        {
+            dim3 g(blocks(E, 128), nparts);
+            k_tr_conv_wgrad<<<g, 128, 0, st>>>(t.dCPRE.p, t.XZ[l].p, t.part.p, T, E, K, rows, kTrRowsPerPart);
+            // parts are [z][c][K+1]: weights [c][k] and bias c
+            const size_t cnt = (size_t)E * (K + 1);
+            k_tr_reduce<<<blocks((long long)cnt, 256), 256, 0, st>>>(t.part.p, nparts, cnt, t.dDL.p, 0, nullptr);
+            // scatter: weight grads [E][K] and bias [E] from the [E][K+1] sums
+            CU(cudaMemcpy2DAsync(G + o.conv_w, (size_t)K * 4, t.dDL.p, (size_t)(K + 1) * 4, (size_t)K * 4, E,
+                                 cudaMemcpyDeviceToDevice, st));
+            CU(cudaMemcpy2DAsync(G + o.conv_b, 4, t.dDL.p + K, (size_t)(K + 1) * 4, 4, E, cudaMemcpyDeviceToDevice, st));
+        }
+        // in_proj
+        tn(2 * E, d, t.dXZ.p, 2 * E, t.XN[l].p, d, G + o.in_w);
+        nn((int)rows, d, 2 * E, t.dXZ.p, 2 * E, P + o.in_w, d, t.dXN.p, d, nullptr, 0);
+        // LN_a (adds into the residual gradient of the block input)
+        k_tr_ln_bwd<<<warps_grid, 256, 0, st>>>(t.dXN.p, t.X[l].p, t.mA[l].p, t.rA[l].p, P + o.ln_a_w, t.dXin.p,
+                                                t.dyxh.p, rows, d, 1);
+        colsum(t.dyxh.p, d, d, G + o.ln_a_w);
+        colsum(t.dXN.p, d, d, G + o.ln_a_b);
+        std::swap(t.dX.p, t.dXin.p);
+        std::swap(t.dX.n, t.dXin.n);
+    }
+    k_tr_embed_bwd<<<256, d, 0, st>>>(t.dX.p, tok, T, seqlen, rows, d, G + fo.embed);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(BOA_ERR_CUDA, "training kernels: %s", cudaGetErrorString(e));
+    return BOA_OK;
+}
+
+// Buffers for bsz x T rows (kept and grown across calls).
+static boa_status ensure_train_state(boa_model* m, int bsz, int T, int seqlen) {
+    if (m->F) return fail(BOA_ERR_ARG, "boa_train_step supports blocks without FFN (ffn_mult 0)");
+    if (!m->tr) m->tr = new TrainState();
+    TrainState& t = *m->tr;
+    const size_t rows = (size_t)bsz * T;
+    const size_t d = m->d, E = m->E, N = m->N, R2 = m->R2, nl = m->nl, r = m->r, K = m->K;
+    if (!t.master.p) {
+        TRY(t.master.ensure(m->n_params));
+        TRY(t.grad.ensure(m->n_params));
+        TRY(t.m1.ensure(m->n_params));
+        TRY(t.m2.ensure(m->n_params));
+        CU(cudaMemcpy(t.master.p, m->params.data(), m->n_params * 4, cudaMemcpyHostToDevice));
+        CU(cudaMemset(t.m1.p, 0, m->n_params * 4));
+        CU(cudaMemset(t.m2.p, 0, m->n_params * 4));
+    }
+    TRY(t.tok.ensure((size_t)bsz * seqlen));
+    auto per_layer = [&](std::vector<DevBuf<float>>& v, size_t count, size_t layers) -> boa_status {
+        if (v.size() < layers) v.resize(layers);
+        for (size_t i = 0; i < layers; i++) TRY(v[i].ensure(std::max<size_t>(count, 1)));
+        return BOA_OK;
+    };
+    const size_t nck = (T + kTrainChunk - 1) / kTrainChunk, nblk = (E + kTrainThreads - 1) / kTrainThreads;
+    TRY(per_layer(t.X, rows * d, nl + 1));
+    TRY(per_layer(t.XN, rows * d, nl));
+    TRY(per_layer(t.mA, rows, nl));
+    TRY(per_layer(t.rA, rows, nl));
+    TRY(per_layer(t.XZ, rows * 2 * E, nl));
+    TRY(per_layer(t.CPRE, rows * E, nl));
+    TRY(per_layer(t.U, rows * E, nl));
+    TRY(per_layer(t.DBC, rows * R2, nl));
+    TRY(per_layer(t.DPRE, rows * E, nl));
+    TRY(per_layer(t.DELTA, rows * E, nl));
+    TRY(per_layer(t.AN, E * N, nl));
+    TRY(per_layer(t.BM, rows * N, nl));
+    TRY(per_layer(t.CM, rows * N, nl));
+    TRY(per_layer(t.YS, rows * E, nl));
+    TRY(per_layer(t.HIN, (size_t)bsz * nck * N * E, nl));
+    TRY(per_layer(t.YG, rows * E, nl));
+    TRY(per_layer(t.URES, rows * d, nl));
+    TRY(per_layer(t.mB, rows, nl));
+    TRY(per_layer(t.rB, rows, nl));
+    TRY(t.logits.ensure(rows * 256));
+    TRY(t.dlogits.ensure(rows * 256));
+    TRY(t.loss_rows.ensure(rows));
+    TRY(t.loss.ensure(1));
+    TRY(t.dX.ensure(rows * d));
+    TRY(t.dXin.ensure(rows * d));
+    TRY(t.dU.ensure(rows * E));
+    TRY(t.dCPRE.ensure(rows * E));
+    TRY(t.dXZ.ensure(rows * 2 * E));
+    TRY(t.dYG.ensure(rows * E));
+    TRY(t.dYS.ensure(rows * E));
+    TRY(t.dDELTA.ensure(rows * E));
+    TRY(t.dDPRE.ensure(rows * E));
+    TRY(t.dDBC.ensure(rows * R2));
+    TRY(t.dDL.ensure(std::max(rows * r, E * (K + 1))));
+    TRY(t.dXN.ensure(rows * d));
+    TRY(t.dyxh.ensure(rows * d));
+    TRY(t.dURES.ensure(rows * d));
+    TRY(t.hs.ensure((size_t)bsz * kTrainChunk * N * E));
+    TRY(t.dA_part.ensure((size_t)bsz * E * N));
+    TRY(t.dD_part.ensure((size_t)bsz * E));
+    TRY(t.dB_part.ensure(rows * nblk * N));
+    TRY(t.dC_part.ensure(rows * nblk * N));
+    const size_t nparts = (rows + kTrRowsPerPart - 1) / kTrRowsPerPart;
+    const size_t widest = std::max({2 * E * d, d * E, R2 * E, E * r, (size_t)256 * d, E * (K + 1), 2 * E, (size_t)256});
+    TRY(t.part.ensure(nparts * widest));
+    t.rows = std::max(t.rows, rows);
+    return BOA_OK;
+}
+
+static boa_status train_batch(boa_model* m, const uint8_t* batch, size_t n_seq, size_t seqlen) {
+    if (!m || !batch || n_seq == 0 || seqlen < 2) return fail(BOA_ERR_ARG, "bad argument");
+    if (n_seq > 65535 || seqlen > (1u << 24) || n_seq * (seqlen - 1) > (1ull << 22))
+        return fail(BOA_ERR_ARG, "batch too large (at most 2^22 predicted positions)");
+    CU(cudaSetDevice(m->device));
+    const int bsz = (int)n_seq, T = (int)seqlen - 1;
+    TRY(ensure_train_state(m, bsz, T, (int)seqlen));
+    CU(cudaMemcpyAsync(m->tr->tok.p, batch, n_seq * seqlen, cudaMemcpyHostToDevice, m->stream));
+    return train_forward_backward(m, bsz, T, (int)seqlen);
+}
+
+static boa_status read_loss(boa_model* m, size_t rows, float* loss_out) {
+    float s = 0.f;
+    CU(cudaMemcpyAsync(&s, m->tr->loss.p, 4, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    if (loss_out) *loss_out = (float)(s / (rows * std::log(256.0)));
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_train_step(boa_model* m, const uint8_t* batch, size_t n_seq, size_t seqlen, float lr,
+                                     float* loss_out) {
+    TRY(train_batch(m, batch, n_seq, seqlen));
+    TrainState& t = *m->tr;
+    t.step++;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f, wd = 0.01f;
+    const float bc1 = (float)(1.0 - std::pow((double)b1, (double)t.step));
+    const float bc2 = (float)(1.0 - std::pow((double)b2, (double)t.step));
+    k_tr_adamw<<<(unsigned)((m->n_params + 255) / 256), 256, 0, m->stream>>>(t.master.p, t.grad.p, t.m1.p, t.m2.p,
+                                                                           m->n_params, lr, b1, b2, eps, wd, bc1, bc2);
+    CU(cudaGetLastError());
+    TRY(read_loss(m, n_seq * (seqlen - 1), loss_out));
+    // the updated array becomes the model: host copy, device copies, fingerprint
+    CU(cudaMemcpyAsync(m->params.data(), t.master.p, m->n_params * 4, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    TRY(upload_weights(m, m->params.data()));
+    // FNV-1a of the file boa_save_model would write, as boa_load_model takes it
+    uint64_t h = fnv1a64_update(1469598103934665603ull, reinterpret_cast<const uint8_t*>("BOAW"), 4);
+    h = fnv1a64_update(h, reinterpret_cast<const uint8_t*>(m->header), sizeof m->header);
+    m->fingerprint = fnv1a64_update(h, reinterpret_cast<const uint8_t*>(m->params.data()), m->n_params * 4);
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_debug_train_grad(boa_model* m, const uint8_t* batch, size_t n_seq, size_t seqlen,
+                                           float* grad_out, float* loss_out) {
+    TRY(train_batch(m, batch, n_seq, seqlen));
+    TRY(read_loss(m, n_seq * (seqlen - 1), loss_out));
+    if (grad_out) {
+        CU(cudaMemcpyAsync(grad_out, m->tr->grad.p, m->n_params * 4, cudaMemcpyDeviceToHost, m->stream));
+        CU(cudaStreamSynchronize(m->stream));
+    }
+    return BOA_OK;
+}
+
+extern "C" size_t boa_model_param_count(const boa_model* m) { return m ? m->n_params : 0; }
+
+extern "C" boa_status boa_save_model(const boa_model* m, const char* path) {
+    if (!m || !path) return fail(BOA_ERR_ARG, "null argument");
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return fail(BOA_ERR_IO, "cannot open %s for writing", path);
+    bool ok = fwrite("BOAW", 1, 4, fp) == 4 && fwrite(m->header, 4, 9, fp) == 9 &&
+              fwrite(m->params.data(), 4, m->n_params, fp) == m->n_params;
+    ok = (fclose(fp) == 0) && ok;
+    if (!ok) return fail(BOA_ERR_IO, "short write on %s", path);
     return BOA_OK;
 }
