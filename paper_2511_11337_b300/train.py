@@ -2,13 +2,16 @@
 Compression and Cross-Entropy Loss": minimising the base-256 cross-entropy
 minimises the code length).
 
-The selective scan, forward and backward, runs in the library's hand-written
-kernels (boa_scan_train_fwd / boa_scan_train_bwd) behind a
-torch.autograd.Function; states are recomputed per chunk of 256 steps instead
-of being stored.  The rest of the block (norms, projections, depthwise conv,
-activations) is expressed with torch operations, the projections in BF16
-under autocast with FP32 master weights.  Parameters mirror the weight-file
-layout, so a trained model exports to a file that boa_load_model reads.
+Two routes.  train_native drives the library's own training step
+(boa_train_step: forward, backward and AdamW in its kernels, FP32).  The
+autograd route (TorchPredictor, train) runs the selective scan, forward and
+backward, in the library's hand-written kernels (boa_scan_train_fwd /
+boa_scan_train_bwd) behind a torch.autograd.Function, with states recomputed
+per chunk of 256 steps instead of stored, and the rest of the block
+(norms, projections, depthwise conv, activations) as torch operations, the
+projections in BF16 under autocast with FP32 master weights.  Parameters
+mirror the weight-file layout, so either route's model exports to a file
+that boa_load_model reads.
 """
 from __future__ import annotations
 
@@ -161,6 +164,24 @@ def train(model: TorchPredictor, data: bytes, steps: int, batch: int = 64, seqle
     return hist
 
 
+def train_native(path: str, data: bytes, steps: int, batch: int, seqlen: int, lr: float, seed: int = 0,
+                 log_every: int = 10):
+    """The same loop through the library's own training step (boa_train_step:
+    forward, backward and AdamW all in its kernels); returns the model and
+    [(step, loss), ...]."""
+    from . import api
+    m = api.Model(path)
+    buf = np.frombuffer(data, np.uint8)
+    g = np.random.Generator(np.random.PCG64(seed))
+    hist = []
+    for step in range(steps):
+        starts = g.integers(0, len(buf) - seqlen, batch)
+        loss = m.train_step(np.stack([buf[s:s + seqlen] for s in starts]), lr)
+        if step % log_every == 0 or step == steps - 1:
+            hist.append((step, loss))
+    return m, hist
+
+
 def main():
     import argparse
     import json
@@ -170,6 +191,8 @@ def main():
 
     from . import api
     ap = argparse.ArgumentParser(description="Train the predictor on CMS-like records, then compress held-out data.")
+    ap.add_argument("--route", choices=["native", "torch"], default="native",
+                    help="native: boa_train_step; torch: autograd with the library's scan kernels")
     ap.add_argument("--train-mb", type=float, default=256.0)
     ap.add_argument("--heldout-mb", type=float, default=64.0)
     ap.add_argument("--steps", type=int, default=300)
@@ -179,15 +202,23 @@ def main():
     ap.add_argument("--out", default="")
     args = ap.parse_args()
     shape = synth.PAPER_SCALE
-    train_data = synth.cms_records(int(args.train_mb * 1e6), seed=5000)
-    held = synth.cms_records(int(args.heldout_mb * 1e6), seed=5001)
-    model = TorchPredictor(shape, synth.init_weights(shape, seed=2)).cuda()
+    n_train = int(args.train_mb * 1e6)
+    stream = synth.cms_records(n_train + int(args.heldout_mb * 1e6), seed=5000)
+    train_data, held = stream[:n_train], stream[n_train:]
+    path = args.out or os.path.join(tempfile.mkdtemp(), "trained.boaw")
+    init = os.path.join(tempfile.mkdtemp(), "init.boaw")
+    synth.make_model_file(init, shape, seed=2)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = train(model, train_data, args.steps, args.batch, args.seqlen, args.lr)
+    if args.route == "native":
+        nm, hist = train_native(init, train_data, args.steps, args.batch, args.seqlen, args.lr)
+        nm.save(path)
+    else:
+        model = TorchPredictor(shape, synth.init_weights(shape, seed=2)).cuda()
+        hist = train(model, train_data, args.steps, args.batch, args.seqlen, args.lr)
+        model.save(path)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    path = args.out or os.path.join(tempfile.mkdtemp(), "trained.boaw")
-    model.save(path)
     m = api.Model(path)
     streams = synth.split_equal(held, max(1, len(held) // 16384))
     flat, in_off = api.pack(streams)
@@ -205,7 +236,9 @@ def main():
     t_d = time.perf_counter() - t0
     ok = bool(torch.equal(d_dec, d_in))
     total = int(len(flat))
-    print(json.dumps({"train_steps": args.steps, "train_s": t_train, "loss_bytes_per_byte": hist,
+    tokens = args.steps * args.batch * (args.seqlen - 1)
+    print(json.dumps({"route": args.route, "train_steps": args.steps, "train_s": t_train,
+                      "train_tokens_per_s": tokens / t_train, "loss_bytes_per_byte": hist,
                       "heldout_bytes": total, "compressed_bytes": int(sizes.sum()),
                       "compression_ratio": total / int(sizes.sum()), "compress_MBps": total / 1e6 / t_c,
                       "decompress_MBps": total / 1e6 / t_d, "lossless": ok}))
