@@ -397,9 +397,9 @@ def run_boa(args):
     # launch is timed, so scale by all steps / timed steps.
     est = {}
     for phase, d in prof.items():
-        timed, total = prof_steps[phase]
+        n_timed, n_all = prof_steps[phase]
         for k, v in d.items():
-            scale = (total / timed if timed else 0.0) / args.steps
+            scale = (n_all / n_timed if n_timed else 0.0) / args.steps
             est[(phase, k)] = dict(v, ms_step=v["ms"] * scale)
     step_est = sum(v["ms_step"] for v in est.values())
     dom = max(est, key=lambda k: est[k]["ms_step"]) if est else None
