@@ -295,8 +295,14 @@ def run_boa(args):
     # The job is world x 64 MiB of independent streams; each rank compresses
     # its contiguous share (weak scaling, no data-path collective).
     lo, hi = shard_range(world * args.streams, rank, world)
-    buf = synth.atlas_workload(args.streams, args.stream_len, seed=2000 + lo // args.streams)
-    streams = synth.split_equal(buf, args.streams)[: hi - lo]
+    if args.workload == "mixed":
+        # SURVEY configuration 3's uneven mix, each stream cut into 16 KB
+        # chunks as the container stores it (a chunk is a coder stream)
+        src = synth.mixed_workload(args.streams, seed=3000 + lo)
+        streams = [s[i:i + args.stream_len] for s in src for i in range(0, len(s), args.stream_len)]
+    else:
+        buf = synth.atlas_workload(args.streams, args.stream_len, seed=2000 + lo // args.streams)
+        streams = synth.split_equal(buf, args.streams)[: hi - lo]
     total = sum(map(len, streams))
 
     stream = torch.cuda.Stream()
@@ -319,7 +325,7 @@ def run_boa(args):
         model.decompress_device(d_out.data_ptr(), out_off, lens, d_dec.data_ptr(), in_off, in_sizes=sizes)
         return sizes, n1 + model.last_launch_count
 
-    tuning = model.autotune(len(streams), args.stream_len) if args.autotune else None
+    tuning = model.autotune(len(streams), int(np.median(lens))) if args.autotune else None
     if args.decode_lanes is not None or args.scan_variant is not None:
         t = model.tuning()
         model.set_tuning(t["max_rows"], t["scan_variant"] if args.scan_variant is None else args.scan_variant,
@@ -461,13 +467,18 @@ def run_boa(args):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "f32 (projections as 3xTF32 on tensor cores)",
                   "bf16": "bf16 projections, f32 elsewhere", "fp8": "e4m3 projections, f32 elsewhere"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if (args.streams, args.stream_len) == (N_STREAMS, STREAM_LEN) else
+        "config": {"workload": (f"SURVEY cfg 3 mix: {args.streams} streams of log-uniform 1 KB-1 MB, ATLAS-like or "
+                                f"CMS-like at random, cut into {len(streams)} chunks of at most {args.stream_len} B; "
+                                "same model") if args.workload == "mixed" else
+                   WORKLOAD if (args.streams, args.stream_len) == (N_STREAMS, STREAM_LEN) else
                    f"reduced: {args.streams} x {args.stream_len} B of the jet table, same model",
                    "streams": args.streams, "stream_len": args.stream_len, "bytes_per_gpu": total,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed (256 MiB write) before every timed step", "autotuned": tuning},
         "compression_ratio": total / comp_total,
         "compressed_bytes": comp_total,
+        # the paper's space-saving rate (original - compressed) / time, here per round trip
+        "sigma_ssr_MBps": world * (total - comp_total) / 1e6 / (ms / 1e3),
         "wall_s_timed": t_wall,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -496,6 +507,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--streams", type=int, default=N_STREAMS)
     ap.add_argument("--stream-len", type=int, default=STREAM_LEN)
+    ap.add_argument("--workload", default="jet", choices=["jet", "mixed"],
+                    help="jet: the benchmark's 64 MiB jet table; mixed: configuration 3's uneven mix (--streams sources)")
     ap.add_argument("--max-rows", type=int, default=0)
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "bf16", "tf32x3", "fp8"])
     ap.add_argument("--forms", default="fp32,bf16,fp8", help="other precision forms to report ('' for none)")

@@ -139,6 +139,15 @@ boa_status boa_decompress_device(boa_model* model, size_t n_streams, const uint8
  * (counted by the host as it enqueues them). */
 uint64_t boa_last_launch_count(const boa_model* model);
 
+/* Per-stream status of the last compress / decompress call on this model
+ * (host out, its first n streams): 0 for a stream that was coded cleanly,
+ * else bits 1 = encoder output capacity exceeded, 2 = the decoder met an
+ * impossible state or its stream's coded length did not match (corrupt or
+ * truncated input), 4 = renormalisation exceeded its proven bound.  A call
+ * that failed with BOA_ERR_CORRUPT names the first such stream; this lists
+ * all of them.  Errors: BOA_ERR_ARG (n above the last call's stream count). */
+boa_status boa_last_stream_status(const boa_model* model, size_t n, uint32_t* status);
+
 /* Kernel classes for boa_profile_read. */
 typedef enum {
     BOA_KC_EMBED_LN = 0,    /* byte embedding + first LayerNorm */

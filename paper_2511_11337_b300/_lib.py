@@ -23,6 +23,7 @@ SIGNATURES = {
     "boa_compress_device": (i32, [vp, sz, vp, vp, vp, vp, vp]),
     "boa_decompress_device": (i32, [vp, sz, vp, vp, vp, vp, vp, vp]),
     "boa_last_launch_count": (u64, [vp]),
+    "boa_last_stream_status": (i32, [vp, sz, vp]),
     "boa_last_error": (C.c_char_p, []),
     "boa_train_step": (i32, [vp, vp, sz, sz, C.c_float, vp]),
     "boa_save_model": (i32, [vp, C.c_char_p]),

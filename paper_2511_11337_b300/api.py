@@ -61,6 +61,12 @@ class Model:
     def fingerprint(self) -> int:
         return int(load().boa_model_fingerprint(self._h))
 
+    def last_stream_status(self, n: int) -> np.ndarray:
+        """boa_last_stream_status: per-stream flags of the last call (0 = clean)."""
+        out = np.zeros(max(n, 1), np.uint32)
+        check(load().boa_last_stream_status(self._h, n, _p(out)))
+        return out[:n]
+
     @property
     def last_launch_count(self) -> int:
         return int(load().boa_last_launch_count(self._h))

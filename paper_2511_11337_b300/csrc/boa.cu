@@ -216,6 +216,7 @@ struct boa_model {
     uint32_t header[9] = {};        // the weight file's header words after the magic
     std::vector<float> params;      // the weight file's tensor array (host copy)
     TrainState* tr = nullptr;
+    std::vector<uint32_t> last_status;   // per-stream flags of the last compress / decompress call
     uint64_t prof_steps[2][2] = {};         // [phase][timed, all] steps of the step loops
 };
 
@@ -292,6 +293,13 @@ extern "C" const char* boa_last_error(void) { return g_err.c_str(); }
 extern "C" uint64_t boa_model_fingerprint(const boa_model* m) { return m ? m->fingerprint : 0; }
 
 extern "C" uint64_t boa_last_launch_count(const boa_model* m) { return m ? m->launches : 0; }
+
+extern "C" boa_status boa_last_stream_status(const boa_model* m, size_t n, uint32_t* status) {
+    if (!m || (n && !status)) return fail(BOA_ERR_ARG, "null argument");
+    if (n > m->last_status.size()) return fail(BOA_ERR_ARG, "the last call had %zu streams", m->last_status.size());
+    if (n) memcpy(status, m->last_status.data(), n * 4);
+    return BOA_OK;
+}
 
 static void free_train_state(boa_model* m);
 
@@ -1358,6 +1366,9 @@ static boa_status compress_impl(boa_model* m, size_t n, const uint8_t* d_in, con
     CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, n * 4, cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     prof_collect(m);
+    m->last_status.assign(m->h_u32.p, m->h_u32.p + n);
+    for (size_t i = 0; i < n; i++)
+        if (lens[i] < 2) m->last_status[i] = 0;
     TRY(check_tc_error(m));
     for (size_t i = 0; i < n; i++)
         if (lens[i] >= 2 && m->h_u32.p[i])
@@ -1521,6 +1532,7 @@ static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, c
     CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, n * 4, cudaMemcpyDeviceToHost, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     prof_collect(m);
+    m->last_status.assign(m->h_u32.p, m->h_u32.p + n);
     TRY(check_tc_error(m));
     for (size_t i = 0; i < n; i++)
         if (m->h_u32.p[i]) return fail(BOA_ERR_CORRUPT, "stream %zu did not decode cleanly (flags %u)", i, m->h_u32.p[i]);

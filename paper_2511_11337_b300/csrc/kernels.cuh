@@ -190,12 +190,13 @@ k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ wt,
 // A2t = (A * log2 e) stored [N][E] and dtwt = W_dt stored [R][E] (channel
 // innermost, so the per-channel loads coalesce); exp(Delta A) = 2^(Delta A2).
 // A CTA covers 128 channels of G consecutive streams and loads the weights
-// once; the rows it visits (stream-major) are staged 32 at a time.
+// once; the rows it visits (stream-major) are staged 32 at a time.  Six CTAs
+// per SM (80 registers): measured 3 % faster than five at compression sizes.
 constexpr int kScanThreads = 128;
 constexpr int kScanRowsSmem = 32;
 
 template <int NS, int R, int G>
-__global__ void __launch_bounds__(kScanThreads)
+__global__ void __launch_bounds__(kScanThreads, 6)
 k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* __restrict__ dbc,
        const float* __restrict__ dtwt, const float* __restrict__ dt_b, const float* __restrict__ A2t,
        const float* __restrict__ Dv, float* __restrict__ hstate, float* __restrict__ yg,

@@ -179,6 +179,12 @@ def test_corrupt_stream_is_reported(tiny):
     with pytest.raises(Exception) as e:
         tiny.decompress(bad, [2000, 2000])
     assert getattr(e.value, "code", None) == 7
+    st = tiny.last_stream_status(2)
+    assert st[0] & 2 and st[1] == 0          # only the truncated stream is flagged
+    tiny.decompress(comp, [2000, 2000])
+    assert not tiny.last_stream_status(2).any()
+    with pytest.raises(Exception):
+        tiny.last_stream_status(3)
     flipped = bytearray(comp[1]); flipped[len(flipped) // 2] ^= 0xFF
     try:
         out = tiny.decompress([comp[0], bytes(flipped)], [2000, 2000])
