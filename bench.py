@@ -177,10 +177,11 @@ def run_reference(args):
     v = nb / 1e6 / (ms / 1e3)
     sample = f"first {prefix} B of {len(streams)} of the 4096 streams ({nb} B), compress + decompress"
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "config": {"workload": WORKLOAD, "streams": N_STREAMS, "stream_len": STREAM_LEN,
+                   "parallelism": "host cores, one OpenMP thread per stream", "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
