@@ -725,9 +725,19 @@ static boa_status tmap_2d(boa_model* m, const void* ptr, uint64_t rows, uint64_t
     return BOA_OK;
 }
 
-// Tile width by output width only, so a given projection always runs the
-// same MMA shape in compression and decompression.
-static int tc_bn(int N) { return N >= 512 ? 128 : N > 48 ? 64 : 48; }
+// Tile width.  An output element's value does not depend on the MMA's N
+// (its K sums run through the same instructions whatever the tile width:
+// tested bit for bit across widths), so the width may follow the batch.
+// Decode-size batches keep several CTAs per output column block (128 for
+// N >= 512, 64, or 48 for x_proj); compression-size batches (more than
+// kWideRows rows) take the widest tile N fills, up to 256, which does more
+// work per tensor instruction.  x_proj (N <= 64) keeps its 48-wide tile,
+// since its split K depends on N alone.
+static const long long kWideRows = 8192;
+static int tc_bn(int N, long long M) {
+    if (M > kWideRows && N > 64) return N >= 256 ? 256 : 128;
+    return N >= 512 ? 128 : N > 48 ? 64 : 48;
+}
 
 // Split K across a cluster of CTAs (deterministic reduction in the
 // epilogue) for x_proj (N <= 64), whose grid is otherwise a few dozen long
@@ -775,14 +785,15 @@ static boa_status gemm_tc(boa_model* m, int cls, const __nv_bfloat16* A, const _
     const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
     ProfScope ps(m, cls, 2.0 * M * N * K,
                  2.0 * ((double)M * K + (double)K * N) + 4.0 * (double)M * N * (resid ? 2 : 1) + (outb ? 2.0 * M * N : 0));
-    const int BN = tc_bn(N);
+    const int BN = tc_bn(N, M);
     CUtensorMap ta, tb;
     TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, 2, &ta));
     TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 2, &tb));
     switch (BN) {
         case 48: launch_tc<48, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
         case 64: launch_tc<64, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
-        default: launch_tc<128, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
+        case 128: launch_tc<128, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
+        default: launch_tc<256, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
     }
     return check_launch(m, "gemm_tc");
 }
@@ -804,14 +815,15 @@ static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_
     TRY(check_launch(m, "quant_rows"));
     const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
     ProfScope ps(m, cls, 2.0 * M * N * K, ((double)M * K + (double)K * N) + 4.0 * (double)M * N * (resid ? 2 : 1));
-    const int BN = tc_bn(N);
+    const int BN = tc_bn(N, M);
     CUtensorMap ta, tb;
     TRY(tmap_2d(m, m->v.a8, (uint64_t)M, (uint64_t)Kp, kTcBM, 1, &ta));
     TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)Kp, (uint32_t)BN, 1, &tb));
     switch (BN) {
         case 48: launch_tc<48, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
         case 64: launch_tc<64, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
-        default: launch_tc<128, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
+        case 128: launch_tc<128, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
+        default: launch_tc<256, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
     }
     return check_launch(m, "gemm_f8");
 }
@@ -849,7 +861,7 @@ static boa_status gemm_t3(boa_model* m, int cls, const float* A, const float* Wh
     const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
     ProfScope ps(m, cls, 2.0 * M * N * K,
                  4.0 * ((double)M * K + 2.0 * K * N) + 4.0 * (double)M * N * (resid ? 2 : 1));
-    const int BN = tc_bn(N);
+    const int BN = tc_bn(N, M);
     CUtensorMap ta, th, tl;
     TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, 4, &ta));
     TRY(tmap_2d(m, Whi, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 4, &th));
@@ -857,7 +869,8 @@ static boa_status gemm_t3(boa_model* m, int cls, const float* A, const float* Wh
     switch (BN) {
         case 48: launch_t3<48, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
         case 64: launch_t3<64, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
-        default: launch_t3<128, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
+        case 128: launch_t3<128, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
+        default: launch_t3<256, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
     }
     return check_launch(m, "gemm_t3");
 }

@@ -172,7 +172,9 @@ struct TileLayout {
     static constexpr int kChunks = BN / 16;
     static constexpr int kSlots = BN / 4;                       // float4 per row
     static constexpr int kMask = kSlots >= 16 ? 7 : 3;          // swizzle stays inside the row
-    static constexpr int kRowsPerIter = 32 / kSlots;            // rows one warp store covers
+    static constexpr int kLaneSlots = kSlots < 32 ? kSlots : 32;   // float4 columns one pass covers
+    static constexpr int kPasses = kSlots / kLaneSlots;         // column passes per row (2 for BN = 256)
+    static constexpr int kRowsPerIter = 32 / kLaneSlots;        // rows one warp store covers
 };
 
 template <int BN>
@@ -241,8 +243,10 @@ __device__ __forceinline__ void tc_store_rows(int r_beg, int n_rows, int lane, i
     using T = TileLayout<BN>;
     const float4* st = reinterpret_cast<const float4*>(stage);
     const int kIters = n_rows / T::kRowsPerIter;
-    const int f = lane % T::kSlots;
-    const bool active = lane < T::kRowsPerIter * T::kSlots;
+#pragma unroll 1
+    for (int pass = 0; pass < T::kPasses; pass++) {
+    const int f = lane % T::kLaneSlots + pass * T::kLaneSlots;
+    const bool active = lane < T::kRowsPerIter * T::kLaneSlots;
     const int n = n0 + 4 * f;
     const bool col_ok = active && n < N;                 // N % 4 == 0
     float4 bv = make_float4(0.f, 0.f, 0.f, 0.f), cs = make_float4(1.f, 1.f, 1.f, 1.f);
@@ -257,7 +261,7 @@ __device__ __forceinline__ void tc_store_rows(int r_beg, int n_rows, int lane, i
         float rsv[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; u++) {
-            const int rl = r_beg + (it0 + u) * T::kRowsPerIter + lane / T::kSlots;
+            const int rl = r_beg + (it0 + u) * T::kRowsPerIter + lane / T::kLaneSlots;
             const int row = m0 + rl;
             old[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             rsv[u] = 1.f;
@@ -269,7 +273,7 @@ __device__ __forceinline__ void tc_store_rows(int r_beg, int n_rows, int lane, i
 #pragma unroll
         for (int u = 0; u < kBatch; u++) {
             if (it0 + u >= kIters) break;
-            const int rl = r_beg + (it0 + u) * T::kRowsPerIter + lane / T::kSlots;
+            const int rl = r_beg + (it0 + u) * T::kRowsPerIter + lane / T::kLaneSlots;
             const int row = m0 + rl;
             if (!col_ok || row >= M) continue;
             const float4* src = st + rl * T::kSlots + (f ^ (rl & T::kMask));
@@ -306,6 +310,7 @@ __device__ __forceinline__ void tc_store_rows(int r_beg, int n_rows, int lane, i
                 bo[1] = __floats2bfloat162_rn(o[2], o[3]);
             }
         }
+    }
     }
 }
 
@@ -355,7 +360,10 @@ struct TcSmem {
     static constexpr int kB = BN * kTcBK * 2;
     static constexpr int kStage = kA + kB;
     static constexpr int kStagesRaw = ((DEEP ? 200 : 110) * 1024) / kStage;
-    static constexpr int kStages = kStagesRaw < 2 ? 2 : (kStagesRaw > 8 ? 8 : kStagesRaw);
+    // the epilogue stages the 128 x BN FP32 tile in the same memory
+    static constexpr int kStagesTile = (kTcBM * BN * 4 + kStage - 1) / kStage;
+    static constexpr int kStagesMin = kStagesTile > 2 ? kStagesTile : 2;
+    static constexpr int kStages = kStagesRaw < kStagesMin ? kStagesMin : (kStagesRaw > 8 ? 8 : kStagesRaw);
     static constexpr int kTmemCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     // stages, then barriers (full, empty, done) and the TMEM address slot
     static constexpr int kBars = 2 * kStages + 1;
