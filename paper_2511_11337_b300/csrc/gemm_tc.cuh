@@ -203,6 +203,8 @@ __device__ __forceinline__ void tc_stage_tile(uint32_t tmem, int q, int lane, fl
     }
 }
 
+constexpr int kMaxPeers = 4;                      // split-K factors are 1, 2 or 4
+
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -254,7 +256,8 @@ __device__ __forceinline__ void tc_store_rows(int r_beg, int n_rows, int lane, i
         bv = *reinterpret_cast<const float4*>(bias + n);
     if (col_ok && col_scale) cs = *reinterpret_cast<const float4*>(col_scale + n);
     constexpr bool kResid = EPI == kEpiResid || EPI == kEpiBiasResid;
-    constexpr int kBatch = 8;
+    // rows whose residual loads are in flight together
+    constexpr int kBatch = kResid && T::kRowsPerIter == 2 ? 16 : 8;
 #pragma unroll 1
     for (int it0 = 0; it0 < kIters; it0 += kBatch) {
         float4 old[kBatch];
@@ -281,14 +284,20 @@ __device__ __forceinline__ void tc_store_rows(int r_beg, int n_rows, int lane, i
             if (peers == 1) {
                 a = *src;
             } else {
-                a = dsmem_ld4(dsmem_addr(src, 0));
-                for (int p = 1; p < peers; p++) {
-                    const float4 b = dsmem_ld4(dsmem_addr(src, (uint32_t)p));
-                    a.x = __fadd_rn(a.x, b.x);
-                    a.y = __fadd_rn(a.y, b.y);
-                    a.z = __fadd_rn(a.z, b.z);
-                    a.w = __fadd_rn(a.w, b.w);
-                }
+                // all peers' chunks requested at once, then added in rank order
+                float4 pv[kMaxPeers];
+#pragma unroll
+                for (int p = 0; p < kMaxPeers; p++)
+                    if (p < peers) pv[p] = dsmem_ld4(dsmem_addr(src, (uint32_t)p));
+                a = pv[0];
+#pragma unroll
+                for (int p = 1; p < kMaxPeers; p++)
+                    if (p < peers) {
+                        a.x = __fadd_rn(a.x, pv[p].x);
+                        a.y = __fadd_rn(a.y, pv[p].y);
+                        a.z = __fadd_rn(a.z, pv[p].z);
+                        a.w = __fadd_rn(a.w, pv[p].w);
+                    }
             }
             float o[4] = {a.x, a.y, a.z, a.w};
             const float* bp = reinterpret_cast<const float*>(&bv);
