@@ -921,10 +921,12 @@ static boa_status conv(boa_model* m, int l, int S, int Tc) {
     dim3 grid((m->E + 511) / 512, (S + G - 1) / G);   // 4 channels per thread
     float* win = m->v.conv + (size_t)l * m->v.S_all * (m->K - 1) * m->E;
     const double rows = (double)S * Tc;
-    ProfScope ps(m, BOA_KC_CONV, rows * m->E * (2.0 * m->K + 4), 4.0 * (2 * rows * m->E + 2.0 * S * (m->K - 1) * m->E));
+    ProfScope ps(m, BOA_KC_CONV, rows * m->E * (2.0 * m->K + 4),
+                 4.0 * (2 * rows * m->E + (double)S * ((m->K - 1) + std::min(Tc, m->K - 1)) * m->E));
     __nv_bfloat16* ub = m->precision == BOA_PREC_BF16 ? m->v.u_b : nullptr;
 #define CONV_CASE(KK, GG) \
-    launch_k(m, k_conv_silu<KK, GG>, grid, 128, 0, 1, m->v.xz, m->E, L.conv_w, L.conv_b, win, m->v.u, ub, S, Tc)
+    launch_k(m, k_conv_silu<KK, GG>, grid, 128, 0, 1, m->v.xz, m->E, L.conv_w, L.conv_b, win, \
+             (const SlotState*)m->v.slots, m->v.u, ub, S, Tc)
     if (G == 8) {
         switch (m->K) { case 2: CONV_CASE(2, 8); break; case 3: CONV_CASE(3, 8); break; default: CONV_CASE(4, 8); break; }
     } else {

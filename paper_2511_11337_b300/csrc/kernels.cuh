@@ -127,13 +127,17 @@ __global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __re
 // ---------------------------------------------------- causal conv1d + SiLU
 
 // u[s, t, c] = SiLU(b_c + sum_k w[c][k] xi[s, t-K+1+k, c]); the last K-1
-// inputs of every (stream, channel) persist in win[S][K-1][E] across calls.
-// wt is the tap matrix stored [K][E] (channel innermost).  A thread owns four
-// adjacent channels (16-byte loads and stores) of G consecutive streams.
+// inputs of every (stream, channel) persist in win[S][K-1][E] across calls
+// as a ring: the input of stream position t sits in row t mod (K-1), so a
+// decode step rewrites one row (its own input over the oldest) instead of
+// shifting all K-1.  slots[s].t is the position of the slot's first row in
+// this call.  wt is the tap matrix stored [K][E] (channel innermost).  A
+// thread owns four adjacent channels (16-byte loads and stores) of G
+// consecutive streams.
 template <int K, int G>
 __global__ void __launch_bounds__(128)
 k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ wt,
-            const float* __restrict__ bconv, float* __restrict__ win,
+            const float* __restrict__ bconv, float* __restrict__ win, const SlotState* __restrict__ slots,
             float* __restrict__ u, __nv_bfloat16* __restrict__ u_b, int S, int Tc) {
     pdl_launch_next();
     pdl_wait_prev();
@@ -146,9 +150,11 @@ k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ wt,
     for (int g = 0; g < G; g++) {
         const int s = blockIdx.y * G + g;
         if (s >= S) break;
-        float4 h[K];
+        const long long t0 = slots[s].t;
+        float* ring = win + (size_t)s * (K - 1) * E + c;
+        float4 h[K];                             // oldest first: positions t0 - K + 1 .. t0 - 1
 #pragma unroll
-        for (int k = 0; k < K - 1; k++) h[k] = *reinterpret_cast<const float4*>(win + ((size_t)s * (K - 1) + k) * E + c);
+        for (int k = 0; k < K - 1; k++) h[k] = *reinterpret_cast<const float4*>(ring + (size_t)((t0 + k) % (K - 1)) * E);
         size_t row = (size_t)s * Tc;
         float4 xi = *reinterpret_cast<const float4*>(xz + row * 2 * E + c);
         for (int tau = 0; tau < Tc; tau++, row++) {
@@ -175,8 +181,13 @@ k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ wt,
             }
             xi = xnext;
         }
+        // the inputs of this call's rows that are still in the window
+        const long long t1 = t0 + Tc;
 #pragma unroll
-        for (int k = 0; k < K - 1; k++) *reinterpret_cast<float4*>(win + ((size_t)s * (K - 1) + k) * E + c) = h[k];
+        for (int k = 0; k < K - 1; k++) {
+            const long long pos = t1 - (K - 1) + k;
+            if (pos >= t0) *reinterpret_cast<float4*>(ring + (size_t)(pos % (K - 1)) * E) = h[k];
+        }
     }
 }
 
