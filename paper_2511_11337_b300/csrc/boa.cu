@@ -743,7 +743,8 @@ static int tc_bn(int N, long long M) {
 // epilogue) for x_proj (N <= 64), whose grid is otherwise a few dozen long
 // K loops at decode sizes.  Chosen by (N, K) only, like the tile width, each
 // CTA keeping at least two K blocks of k_elems.  (Splitting out_proj and the
-// head as well cost compression more than it saved decompression.)
+// head 2 ways as well, with 128-wide decode tiles, left decompression as
+// fast as before: measured, and dropped.)
 static int tc_splits(int N, int K, int k_elems) {
     int s = N <= 64 ? 4 : 1;
     while (s > 1 && (K % (s * k_elems) != 0 || K / (s * k_elems) < 2)) s /= 2;
@@ -828,9 +829,15 @@ static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_
     return check_launch(m, "gemm_f8");
 }
 
+// 3xTF32 split K follows tc_splits (x_proj: 4).  The partial sums are added
+// in chunk order whether the chunks run on the CTAs of a cluster (small
+// grids: decode steps) or sit in one CTA's TMEM (grids that fill the GPU:
+// compression, where a cluster's epilogue exchange costs more than it
+// hides), so both give the same bits.
 template <int BN, int EPI, bool DEEP>
-static void launch_t3_cfg(boa_model* m, dim3 grid, int splits, const CUtensorMap& ta, const CUtensorMap& th,
-                          const CUtensorMap& tl, const float* bias, float* C, long long M, int N, int K) {
+static void launch_t3_cfg(boa_model* m, dim3 grid, int splits, int chunks, const CUtensorMap& ta,
+                          const CUtensorMap& th, const CUtensorMap& tl, const float* bias, float* C, long long M,
+                          int N, int K) {
     using L = T3Smem<BN, DEEP>;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -838,18 +845,21 @@ static void launch_t3_cfg(boa_model* m, dim3 grid, int splits, const CUtensorMap
                              (int)L::kBytes);
     });
     launch_k(m, k_gemm_tc_tf32x3<BN, EPI, DEEP>, grid, kT3Threads, L::kBytes, splits, ta, th, tl, bias, C, (int)M,
-             N, K, m->err.p);
+             N, K, m->err.p, chunks);
 }
 
 template <int BN, int EPI>
 static void launch_t3(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th, const CUtensorMap& tl,
                       const float* bias, float* C, long long M, int N, int K) {
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
-    const int splits = tc_splits(N, K, kT3BK);
-    if ((long long)grid.x * grid.y * splits < m->num_sms)
-        launch_t3_cfg<BN, EPI, true>(m, grid, splits, ta, th, tl, bias, C, M, N, K);
+    const int split = tc_splits(N, K, kT3BK);
+    const bool in_cta = (long long)grid.x * grid.y >= m->num_sms;
+    const int chunks = in_cta && split * T3Smem<BN>::kTmemCols <= 512 ? split : 1;
+    const int peers = split / chunks;
+    if ((long long)grid.x * grid.y * peers < m->num_sms)
+        launch_t3_cfg<BN, EPI, true>(m, grid, peers, chunks, ta, th, tl, bias, C, M, N, K);
     else
-        launch_t3_cfg<BN, EPI, false>(m, grid, splits, ta, th, tl, bias, C, M, N, K);
+        launch_t3_cfg<BN, EPI, false>(m, grid, peers, chunks, ta, th, tl, bias, C, M, N, K);
 }
 
 // FP32-accurate tensor-core GEMM (3xTF32); A is FP32, W pre-split.

@@ -203,6 +203,46 @@ __device__ __forceinline__ void tc_stage_tile(uint32_t tmem, int q, int lane, fl
     }
 }
 
+// Split K inside one CTA: the K blocks fall into `chunks` consecutive
+// chunks, each accumulated in its own TMEM columns (chunk j at column
+// j * chunk_cols), and the staged tile is their sum in chunk order 0, 1, ...
+// This is the same sum, with the same additions, as a cluster of `chunks`
+// CTAs each holding one chunk (tc_store_rows with peers = chunks).
+template <int BN>
+__device__ __forceinline__ void tc_stage_tile_sum(uint32_t tmem, int q, int lane, float* stage, int chunks,
+                                                  int chunk_cols) {
+    using T = TileLayout<BN>;
+    float4* st = reinterpret_cast<float4*>(stage) + (size_t)q * 32 * T::kSlots;
+    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+    for (int g0 = 0; g0 < T::kChunks; g0 += 2) {
+        float acc[2][16];
+        uint32_t r[2][16];
+#pragma unroll 1
+        for (int j = 0; j < chunks; j++) {
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+                if (g0 + c < T::kChunks) tmem_ld16_nowait(base + (uint32_t)(j * chunk_cols + 16 * (g0 + c)), r[c]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    acc[c][i] = j == 0 ? __uint_as_float(r[c][i]) : __fadd_rn(acc[c][i], __uint_as_float(r[c][i]));
+        }
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            if (g0 + c >= T::kChunks) break;
+#pragma unroll
+            for (int jj = 0; jj < 4; jj++) {
+                const int f = (g0 + c) * 4 + jj;
+                st[lane * T::kSlots + (f ^ (lane & T::kMask))] =
+                    make_float4(acc[c][4 * jj], acc[c][4 * jj + 1], acc[c][4 * jj + 2], acc[c][4 * jj + 3]);
+            }
+        }
+    }
+}
+
 constexpr int kMaxPeers = 4;                      // split-K factors are 1, 2 or 4
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -326,17 +366,21 @@ __device__ __forceinline__ void tc_store_rows(int r_beg, int n_rows, int lane, i
 // The whole epilogue of one CTA.  Every thread of the CTA calls it (the
 // cluster barriers of split K count every thread); `epi` marks the four
 // epilogue warps and q their TMEM quadrant.  bad: this CTA's pipeline gave
-// up; with split K no CTA of the cluster then stores anything.
+// up; with split K no CTA of the cluster then stores anything.  chunks > 1
+// (only without a cluster): split K held in this CTA's TMEM, see
+// tc_stage_tile_sum.
 template <int BN, int EPI>
 __device__ __forceinline__ void tc_epilogue(bool epi, bool bad, int* bad_flag, uint32_t tmem, int q, int lane, int m0,
                                             int n0, int M, int N, const float* __restrict__ bias,
                                             float* __restrict__ Cm, __nv_bfloat16* __restrict__ out_bf16,
                                             float* stage, const float* __restrict__ row_scale = nullptr,
-                                            const float* __restrict__ col_scale = nullptr) {
+                                            const float* __restrict__ col_scale = nullptr, int chunks = 1,
+                                            int chunk_cols = 0) {
     const int peers = (int)gridDim.z;
     if (peers == 1) {
         if (epi && !bad) {
-            tc_stage_tile<BN>(tmem, q, lane, stage);
+            if (chunks > 1) tc_stage_tile_sum<BN>(tmem, q, lane, stage, chunks, chunk_cols);
+            else tc_stage_tile<BN>(tmem, q, lane, stage);
             __syncwarp();
             tc_store_rows<BN, EPI>(32 * q, 32, lane, m0, n0, M, N, bias, Cm, out_bf16, stage, 1, row_scale,
                                    col_scale);
@@ -542,7 +586,7 @@ template <int BN, int EPI, bool DEEP = false>
 __global__ void __launch_bounds__(kT3Threads)
 k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
                  const __grid_constant__ CUtensorMap tmBlo, const float* __restrict__ bias, float* __restrict__ Cm,
-                 int M, int N, int K, int* __restrict__ err) {
+                 int M, int N, int K, int* __restrict__ err, int chunks) {
     using L = T3Smem<BN, DEEP>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -560,6 +604,8 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
     const int nk = K / kT3BK / (int)gridDim.z;           // split K: this CTA's K blocks
     const int kb0 = (int)blockIdx.z * nk;
+    const int nkc = nk / chunks;                         // K blocks per TMEM chunk
+    const uint32_t tmem_cols = (uint32_t)(L::kTmemCols * chunks);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -574,7 +620,7 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(tmem_slot)), "r"(L::kTmemCols));
+                     ::"r"(smem_u32(tmem_slot)), "r"(tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -611,12 +657,14 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             const uint32_t alo = ahi + L::kA;
             const uint32_t bhi = ahi + 2 * L::kA;
             const uint32_t blo = bhi + L::kB;
+            const int kc = kb % nkc;                     // K block within its chunk
+            const uint32_t d = tmem + (uint32_t)((kb / nkc) * L::kTmemCols);
 #pragma unroll
             for (int k = 0; k < kT3BK / 8; k++) {
                 const uint32_t o = 32 * k;
-                umma_tf32(tmem, umma_desc_sw128(ahi + o), umma_desc_sw128(bhi + o), idesc, (kb | k) != 0 ? 1u : 0u);
-                umma_tf32(tmem, umma_desc_sw128(ahi + o), umma_desc_sw128(blo + o), idesc, 1u);
-                umma_tf32(tmem, umma_desc_sw128(alo + o), umma_desc_sw128(bhi + o), idesc, 1u);
+                umma_tf32(d, umma_desc_sw128(ahi + o), umma_desc_sw128(bhi + o), idesc, (kc | k) != 0 ? 1u : 0u);
+                umma_tf32(d, umma_desc_sw128(ahi + o), umma_desc_sw128(blo + o), idesc, 1u);
+                umma_tf32(d, umma_desc_sw128(alo + o), umma_desc_sw128(bhi + o), idesc, 1u);
             }
             umma_commit(&empty[s]);
         }
@@ -658,11 +706,11 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         if (!finished) mbar_wait(&done[0], 0);
     }
     tc_epilogue<BN, EPI>(warp >= 2, bad, &bad_flag, tmem, warp % 4, lane, m0, n0, M, N, bias, Cm, nullptr,
-                         reinterpret_cast<float*>(smem));
+                         reinterpret_cast<float*>(smem), nullptr, nullptr, chunks, L::kTmemCols);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
 }  // namespace boa

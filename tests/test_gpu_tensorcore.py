@@ -48,7 +48,9 @@ def api():
 
 
 SHAPES = [(128, 128, 64), (300, 1024, 256), (4096, 48, 512), (1000, 256, 512), (77, 64, 64), (129, 36, 64),
-          (513, 256, 1024), (8500, 256, 256), (8300, 1024, 128)]   # the last two: compression-size 256-wide tiles
+          (513, 256, 1024), (8500, 256, 256), (8300, 1024, 128),   # these two: compression-size 256-wide tiles
+          (20000, 256, 512), (19000, 48, 512), (19000, 128, 256)]  # grids that fill the GPU (3xTF32 x_proj:
+                                                                   # split K inside one CTA's TMEM)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -73,19 +75,21 @@ def test_gemm_kernels(api, shape, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2, 3])
-@pytest.mark.parametrize("NK", [(1024, 256), (48, 512), (256, 512)])
+@pytest.mark.parametrize("NK", [(1024, 256), (48, 512), (256, 512), (256, 256), (128, 256)])
 def test_gemm_rows_independent_of_batch(api, precision, NK):
     """A row's result does not depend on the batch it sits in: under split K
-    (N = 48: four CTAs per cluster reduce their partial tiles through
-    distributed shared memory, in an order fixed by (N, K) alone), and across
-    tile widths (a batch of 9000 rows runs 256- or 128-wide tiles, its slices
-    the narrower decode-size ones)."""
+    (its partial sums added in an order fixed by (N, K) alone, whether the
+    chunks run on the CTAs of a cluster and meet through distributed shared
+    memory, as in the small slices, or sit in one CTA's TMEM, as in 3xTF32
+    grids that fill the GPU: the 20000-row batch), and across tile widths
+    (batches above 8192 rows run 256- or 128-wide tiles, the slices the
+    narrower decode-size ones)."""
     N, K = NK
     g = np.random.default_rng(5)
-    A = g.normal(0, 1, (9000, K)).astype(np.float32)
+    A = g.normal(0, 1, (20000, K)).astype(np.float32)
     W = g.normal(0, 0.05, (N, K)).astype(np.float32)
     full = api.gemm(A, W, precision=precision)
-    for lo, hi in ((0, 1), (5, 133), (8999, 9000), (300, 428), (4000, 5000)):
+    for lo, hi in ((0, 1), (5, 133), (19999, 20000), (300, 428), (4000, 5000), (7000, 16000)):
         part = api.gemm(A[lo:hi], W, precision=precision)
         assert np.array_equal(part, full[lo:hi])
 
