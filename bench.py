@@ -297,8 +297,9 @@ def run_boa(args):
     # its contiguous share (weak scaling, no data-path collective).
     lo, hi = shard_range(world * args.streams, rank, world)
     if args.workload == "mixed":
-        # SURVEY configuration 3's uneven mix, each stream cut into 16 KB
-        # chunks as the container stores it (a chunk is a coder stream)
+        # an uneven mix of ATLAS-like and CMS-like streams (log-uniform
+        # 1 KB - 1 MB), each cut into 16 KB chunks as the container stores
+        # it (a chunk is a coder stream)
         src = synth.mixed_workload(args.streams, seed=3000 + lo)
         streams = [s[i:i + args.stream_len] for s in src for i in range(0, len(s), args.stream_len)]
     else:
@@ -468,7 +469,7 @@ def run_boa(args):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "f32 (projections as 3xTF32 on tensor cores)",
                   "bf16": "bf16 projections, f32 elsewhere", "fp8": "e4m3 projections, f32 elsewhere"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": (f"SURVEY cfg 3 mix: {args.streams} streams of log-uniform 1 KB-1 MB, ATLAS-like or "
+        "config": {"workload": (f"uneven mix: {args.streams} streams of log-uniform 1 KB-1 MB, ATLAS-like or "
                                 f"CMS-like at random, cut into {len(streams)} chunks of at most {args.stream_len} B; "
                                 "same model") if args.workload == "mixed" else
                    WORKLOAD if (args.streams, args.stream_len) == (N_STREAMS, STREAM_LEN) else
@@ -509,7 +510,7 @@ def main():
     ap.add_argument("--streams", type=int, default=N_STREAMS)
     ap.add_argument("--stream-len", type=int, default=STREAM_LEN)
     ap.add_argument("--workload", default="jet", choices=["jet", "mixed"],
-                    help="jet: the benchmark's 64 MiB jet table; mixed: configuration 3's uneven mix (--streams sources)")
+                    help="jet: the benchmark's 64 MiB jet table; mixed: an uneven ATLAS/CMS mix of log-uniform 1 KB-1 MB streams (--streams sources)")
     ap.add_argument("--max-rows", type=int, default=0)
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "bf16", "tf32x3", "fp8"])
     ap.add_argument("--forms", default="fp32,bf16,fp8", help="other precision forms to report ('' for none)")
