@@ -753,9 +753,9 @@ static int tc_splits(int N, int K, int k_elems) {
 
 
 template <int BN, int EPI, int KIND, bool DEEP>
-static void launch_tc_cfg(boa_model* m, dim3 grid, int splits, const CUtensorMap& ta, const CUtensorMap& tb,
-                          const float* bias, float* C, __nv_bfloat16* outb, long long M, int N, int K, const float* rs,
-                          const float* cs) {
+static void launch_tc_cfg(boa_model* m, dim3 grid, int splits, int chunks, const CUtensorMap& ta,
+                          const CUtensorMap& tb, const float* bias, float* C, __nv_bfloat16* outb, long long M, int N,
+                          int K, const float* rs, const float* cs) {
     using L = TcSmem<BN, DEEP>;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -763,19 +763,24 @@ static void launch_tc_cfg(boa_model* m, dim3 grid, int splits, const CUtensorMap
                              (int)L::kBytes);
     });
     launch_k(m, k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, grid, kTcThreads, L::kBytes, splits, ta, tb, bias, C, outb,
-             (int)M, N, K, m->err.p, rs, cs);
+             (int)M, N, K, m->err.p, rs, cs, chunks);
 }
 
-// Grids smaller than the SM count take the deep-pipeline variant.
+// Grids smaller than the SM count take the deep-pipeline variant.  Split K
+// runs across a cluster on small grids and in one CTA's TMEM on grids that
+// fill the GPU (the same additions in the same order; see launch_t3).
 template <int BN, int EPI, int KIND>
 static void launch_tc(boa_model* m, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, float* C,
                       __nv_bfloat16* outb, long long M, int N, int K, const float* rs, const float* cs) {
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
-    const int splits = tc_splits(N, K, KIND == kKindE4M3 ? 128 : kTcBK);
-    if ((long long)grid.x * grid.y * splits < m->num_sms)
-        launch_tc_cfg<BN, EPI, KIND, true>(m, grid, splits, ta, tb, bias, C, outb, M, N, K, rs, cs);
+    const int split = tc_splits(N, K, KIND == kKindE4M3 ? 128 : kTcBK);
+    const bool in_cta = (long long)grid.x * grid.y >= m->num_sms;
+    const int chunks = in_cta && split * TcSmem<BN>::kTmemCols <= 512 ? split : 1;
+    const int peers = split / chunks;
+    if ((long long)grid.x * grid.y * peers < m->num_sms)
+        launch_tc_cfg<BN, EPI, KIND, true>(m, grid, peers, chunks, ta, tb, bias, C, outb, M, N, K, rs, cs);
     else
-        launch_tc_cfg<BN, EPI, KIND, false>(m, grid, splits, ta, tb, bias, C, outb, M, N, K, rs, cs);
+        launch_tc_cfg<BN, EPI, KIND, false>(m, grid, peers, chunks, ta, tb, bias, C, outb, M, N, K, rs, cs);
 }
 
 template <int EPI>

@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kTcThreads)
 k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const float* __restrict__ bias, float* __restrict__ Cm, __nv_bfloat16* __restrict__ out_bf16,
                int M, int N, int K, int* __restrict__ err, const float* __restrict__ row_scale,
-               const float* __restrict__ col_scale) {
+               const float* __restrict__ col_scale, int chunks) {
     constexpr int kElemK = KIND == kKindE4M3 ? 128 : kTcBK;    // elements per 128-byte stage row
     using L = TcSmem<BN, DEEP>;
     extern __shared__ uint8_t smem_raw[];
@@ -450,6 +450,8 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
     const int nk = K / kElemK / (int)gridDim.z;          // split K: this CTA's K blocks
     const int kb0 = (int)blockIdx.z * nk;
+    const int nkc = nk / chunks;                         // K blocks per TMEM chunk
+    const uint32_t tmem_cols = (uint32_t)(L::kTmemCols * chunks);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -459,7 +461,7 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(tmem_slot)), "r"(L::kTmemCols));
+                     ::"r"(smem_u32(tmem_slot)), "r"(tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -495,14 +497,16 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = smem_u32(smem + (size_t)s * L::kStage);
             const uint32_t sb = sa + L::kA;
+            const int kc = kb % nkc;                     // K block within its chunk
+            const uint32_t d = tmem + (uint32_t)((kb / nkc) * L::kTmemCols);
 #pragma unroll
             for (int k = 0; k < 4; k++) {   // 32 bytes of K per instruction: 16 BF16 or 32 E4M3
                 if (KIND == kKindE4M3)
-                    umma_e4m3(tmem, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
-                              (kb | k) != 0 ? 1u : 0u);
+                    umma_e4m3(d, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
+                              (kc | k) != 0 ? 1u : 0u);
                 else
-                    umma_bf16(tmem, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
-                              (kb | k) != 0 ? 1u : 0u);
+                    umma_bf16(d, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
+                              (kc | k) != 0 ? 1u : 0u);
             }
             umma_commit(&empty[s]);
         }
@@ -524,11 +528,11 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (!finished) mbar_wait(&done[0], 0);
     }
     tc_epilogue<BN, EPI>(true, bad, &bad_flag, tmem, warp, lane, m0, n0, M, N, bias, Cm, out_bf16,
-                         reinterpret_cast<float*>(smem), row_scale, col_scale);
+                         reinterpret_cast<float*>(smem), row_scale, col_scale, chunks, L::kTmemCols);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
 // ------------------------------------------------------------ 3xTF32 form
