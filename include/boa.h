@@ -249,6 +249,63 @@ boa_status boa_unpack(boa_model* model, const uint8_t* container, size_t size, u
 /* CRC-32, IEEE 802.3 polynomial (the container's checksum). */
 uint32_t boa_crc32(const uint8_t* data, size_t n);
 
+/* Decompress a concatenation of containers (the shards boa_stream_* writes,
+ * or any containers written with this model, laid end to end) into out, one
+ * after another; *out_len gets the total length.  All their chunks are
+ * decoded in one batch.  out = NULL with cap = 0 only validates the
+ * containers and returns the total length.  Errors: those of boa_unpack,
+ * for the first container that fails. */
+boa_status boa_unpack_shards(boa_model* model, const uint8_t* data, size_t size, uint8_t* out, size_t cap,
+                             size_t* out_len);
+
+/* ------------------------------------------------------------ streaming
+ * The streaming pipeline of the paper (section "Streaming", Fig. 2): chunks
+ * are buffered while the previous set compresses, and the next set is
+ * pre-loaded.  Bytes the caller pushes are cut into chunks of chunk_len
+ * bytes and gathered, in pinned host memory, into sets of set_chunks
+ * chunks.  A full set is copied to the device on the pipeline's own copy
+ * stream and compressed, as one batch of set_chunks streams, by the
+ * pipeline's worker thread.  Meanwhile the caller fills the other set buffer
+ * and its copy pre-loads the device.  Each set becomes one shard, a complete
+ * container (format above) of that set's bytes, appended to the pipeline's
+ * output in input order; boa_unpack decodes one shard, boa_unpack_shards a
+ * concatenation.  Two set buffers exist, so a push waits while both are in
+ * use.  While a pipeline is open its worker thread owns the model: make no
+ * other call on that model until boa_stream_close.  A worker error (those
+ * of boa_compress, BOA_ERR_CUDA) is returned by the next push or finish;
+ * the pipeline then accepts no more data. */
+typedef struct boa_stream boa_stream;
+
+/* Open a pipeline on model.  Allocates 2 x chunk_len x set_chunks bytes of
+ * pinned host and of device memory.  Errors: BOA_ERR_ARG (zero or oversized
+ * set), BOA_ERR_OOM, BOA_ERR_CUDA. */
+boa_status boa_stream_open(boa_model* model, size_t chunk_len, size_t set_chunks, boa_stream** out);
+
+/* Append len bytes (caller-owned, read before the call returns).  Every set
+ * that fills is handed to the worker.  Errors: BOA_ERR_ARG (after finish),
+ * a worker error. */
+boa_status boa_stream_push(boa_stream* stream, const uint8_t* data, size_t len);
+
+/* Hand over the partial last set, if any, and wait until every shard is
+ * written.  Later pushes fail; reads continue. */
+boa_status boa_stream_finish(boa_stream* stream);
+
+/* Bytes of finished shards not yet read. */
+size_t boa_stream_available(const boa_stream* stream);
+
+/* Copy up to cap bytes of finished shards, in order, into out (host);
+ * *out_size gets the count. */
+boa_status boa_stream_read(boa_stream* stream, uint8_t* out, size_t cap, size_t* out_size);
+
+/* Bytes handed to the worker, shards written, and how many of those sets
+ * were already on the device when the worker took them (pre-loaded while the
+ * previous set compressed).  Any pointer may be NULL. */
+boa_status boa_stream_stats(const boa_stream* stream, uint64_t* bytes_in, uint64_t* sets, uint64_t* preloaded);
+
+/* Stop the pipeline (sets already handed over are still compressed) and free
+ * it.  NULL is ignored. */
+void boa_stream_close(boa_stream* stream);
+
 /* ------------------------------------------------------------ training
  * The selective scan for training the predictor (paper App. A recurrence
  * h_t = exp(delta_t A) h_{t-1} + delta_t B_t u_t, y_t = C_t . h_t + D u_t,

@@ -37,6 +37,14 @@ SIGNATURES = {
     "boa_unpack_info": (i32, [vp, sz, C.POINTER(u64), C.POINTER(u64)]),
     "boa_unpack": (i32, [vp, vp, sz, vp, sz, C.POINTER(sz)]),
     "boa_crc32": (C.c_uint32, [vp, sz]),
+    "boa_unpack_shards": (i32, [vp, vp, sz, vp, sz, C.POINTER(sz)]),
+    "boa_stream_open": (i32, [vp, sz, sz, C.POINTER(vp)]),
+    "boa_stream_push": (i32, [vp, vp, sz]),
+    "boa_stream_finish": (i32, [vp]),
+    "boa_stream_available": (sz, [vp]),
+    "boa_stream_read": (i32, [vp, vp, sz, C.POINTER(sz)]),
+    "boa_stream_stats": (i32, [vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)]),
+    "boa_stream_close": (None, [vp]),
     "boa_scan_train_fwd": (i32, [sz, sz, sz, sz, sz] + [vp] * 9),
     "boa_scan_train_bwd": (i32, [sz, sz, sz, sz, sz] + [vp] * 16),
     "boa_profile_enable": (i32, [vp, i32, i32]),

@@ -145,6 +145,15 @@ class Model:
         check(load().boa_unpack(self._h, _p(buf), len(container), _p(out), int(total.value), C.byref(n)))
         return out[:n.value].tobytes()
 
+    def unpack_shards(self, data: bytes) -> bytes:
+        """boa_unpack_shards: containers laid end to end -> original bytes."""
+        buf = np.frombuffer(data, np.uint8) if data else np.zeros(1, np.uint8)
+        n = C.c_size_t()
+        check(load().boa_unpack_shards(self._h, _p(buf), len(data), None, 0, C.byref(n)))
+        out = np.zeros(max(n.value, 1), np.uint8)
+        check(load().boa_unpack_shards(self._h, _p(buf), len(data), _p(out), n.value, C.byref(n)))
+        return out[:n.value].tobytes()
+
     def autotune(self, n_streams: int, stream_len: int) -> dict:
         """boa_autotune: pick the chunk size and the decode scan kernel for this shape."""
         t = _Tuning()
@@ -320,3 +329,51 @@ def compressed_slot_offsets(lens) -> np.ndarray:
 
 
 __all__ = ["decode_cdfs_static", "pack", "slot_offsets", "compressed_slot_offsets", "Model", "BoaError", "encode_cdfs", "decode_cdfs", "quantise", "max_compressed_size", "PREC_FP32", "PREC_BF16", "PREC_TF32X3", "PREC_FP8", "gemm"]
+
+
+class Stream:
+    """boa_stream_*: the double-buffered streaming compressor.  Pushed bytes
+    are cut into sets of set_chunks chunks of chunk_len bytes; each set
+    becomes one container shard.  The model belongs to the pipeline until
+    close()."""
+
+    def __init__(self, model: Model, chunk_len: int = 16384, set_chunks: int = 256):
+        self._model = model
+        self._h = C.c_void_p()
+        check(load().boa_stream_open(model._h, chunk_len, set_chunks, C.byref(self._h)))
+
+    def push(self, data: bytes) -> None:
+        buf = np.frombuffer(data, np.uint8) if data else np.zeros(1, np.uint8)
+        check(load().boa_stream_push(self._h, _p(buf), len(data)))
+
+    def finish(self) -> None:
+        check(load().boa_stream_finish(self._h))
+
+    def read(self) -> bytes:
+        n = int(load().boa_stream_available(self._h))
+        out = np.zeros(max(n, 1), np.uint8)
+        got = C.c_size_t()
+        check(load().boa_stream_read(self._h, _p(out), n, C.byref(got)))
+        return out[:got.value].tobytes()
+
+    def stats(self) -> dict:
+        b, s, p = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        check(load().boa_stream_stats(self._h, C.byref(b), C.byref(s), C.byref(p)))
+        return {"bytes_in": int(b.value), "sets": int(s.value), "preloaded": int(p.value)}
+
+    def close(self) -> None:
+        if self._h:
+            load().boa_stream_close(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -12,12 +12,15 @@
 
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -1586,6 +1589,24 @@ extern "C" boa_status boa_decompress_device(boa_model* m, size_t n, const uint8_
     return decompress_impl(m, n, d_in, in_off, in_sizes, lens, d_out, out_off);
 }
 
+// After compress_impl into m->d_out: the used part of every output slot
+// packed on the device, then one copy back; stream i's bytes land at
+// m->h_out.p + pk[i] (m->h_out holds at least the slots' total capacity).
+static boa_status fetch_compressed(boa_model* m, size_t n, const uint64_t* sizes, std::vector<uint64_t>& pk) {
+    pk.assign(n + 1, 0);
+    for (size_t i = 0; i < n; i++) pk[i + 1] = pk[i] + sizes[i];
+    TRY(m->pack_off.ensure(n + 1));
+    TRY(m->d_pack.ensure(pk[n]));
+    TRY(m->h_pack.ensure(n + 1));
+    memcpy(m->h_pack.p, pk.data(), (n + 1) * 8);
+    CU(cudaMemcpyAsync(m->pack_off.p, m->h_pack.p, (n + 1) * 8, cudaMemcpyHostToDevice, m->stream));
+    k_compact<<<(unsigned)n, 256, 0, m->stream>>>(m->d_out.p, m->out_off.p, m->pack_off.p, m->d_pack.p, (int)n);
+    TRY(check_launch(m, "compact"));
+    CU(cudaMemcpyAsync(m->h_out.p, m->d_pack.p, pk[n], cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    return BOA_OK;
+}
+
 extern "C" boa_status boa_compress(boa_model* m, size_t n, const uint8_t* const* streams, const size_t* lens,
                                    uint8_t* const* out, const size_t* out_caps, size_t* out_sizes) {
     if (!m || (n && (!streams || !lens || !out || !out_caps || !out_sizes))) return fail(BOA_ERR_ARG, "null argument");
@@ -1608,18 +1629,8 @@ extern "C" boa_status boa_compress(boa_model* m, size_t n, const uint8_t* const*
         if (lens[i]) memcpy(m->h_in.p + in_off[i], streams[i], lens[i]);
     CU(cudaMemcpyAsync(m->d_in.p, m->h_in.p, in_off[n], cudaMemcpyHostToDevice, m->stream));
     TRY(compress_impl(m, n, m->d_in.p, in_off.data(), m->d_out.p, out_off.data(), sizes.data()));
-    // Pack the used part of every slot on the device, then one copy back.
-    std::vector<uint64_t> pk(n + 1, 0);
-    for (size_t i = 0; i < n; i++) pk[i + 1] = pk[i] + sizes[i];
-    TRY(m->pack_off.ensure(n + 1));
-    TRY(m->d_pack.ensure(pk[n]));
-    TRY(m->h_pack.ensure(n + 1));
-    memcpy(m->h_pack.p, pk.data(), (n + 1) * 8);
-    CU(cudaMemcpyAsync(m->pack_off.p, m->h_pack.p, (n + 1) * 8, cudaMemcpyHostToDevice, m->stream));
-    k_compact<<<(unsigned)n, 256, 0, m->stream>>>(m->d_out.p, m->out_off.p, m->pack_off.p, m->d_pack.p, (int)n);
-    TRY(check_launch(m, "compact"));
-    CU(cudaMemcpyAsync(m->h_out.p, m->d_pack.p, pk[n], cudaMemcpyDeviceToHost, m->stream));
-    CU(cudaStreamSynchronize(m->stream));
+    std::vector<uint64_t> pk;
+    TRY(fetch_compressed(m, n, sizes.data(), pk));
     for (size_t i = 0; i < n; i++) {
         out_sizes[i] = sizes[i];
         if (sizes[i]) memcpy(out[i], m->h_out.p + pk[i], sizes[i]);
@@ -2253,6 +2264,56 @@ static void put32(uint8_t* p, uint32_t v) { for (int i = 0; i < 4; i++) p[i] = (
 static uint64_t get64(const uint8_t* p) { uint64_t v = 0; for (int i = 7; i >= 0; i--) v = (v << 8) | p[i]; return v; }
 static uint32_t get32(const uint8_t* p) { uint32_t v = 0; for (int i = 3; i >= 0; i--) v = (v << 8) | p[i]; return v; }
 
+// Header of a container whose n index entries already sit at out + 56.
+static void write_container_header(uint8_t* out, uint64_t fingerprint, uint64_t total, uint64_t chunk, uint64_t n,
+                                   uint64_t last) {
+    memcpy(out, "BOA1", 4);
+    put32(out + 4, kBoaVersion);
+    put64(out + 8, fingerprint);
+    put64(out + 16, total);
+    put64(out + 24, chunk);
+    put64(out + 32, n);
+    put64(out + 40, last);
+    put32(out + 48, boa_crc32(out, 48));
+    put32(out + 52, boa_crc32(out + kHeaderBytes, 16 * n));
+}
+
+// One validated container at the start of c (size bytes, possibly followed
+// by more containers): its layout, chunk extents and its own byte length.
+struct ContainerView {
+    uint64_t total = 0, chunk = 0, n = 0, last = 0;
+    const uint8_t* idx = nullptr;
+    const uint8_t* pay = nullptr;
+    size_t bytes = 0;                  // header + index + payload up to the farthest chunk end
+};
+
+static boa_status parse_container(const boa_model* m, const uint8_t* c, size_t size, ContainerView* v) {
+    uint64_t total = 0, fp = 0;
+    TRY(boa_unpack_info(c, size, &total, &fp));
+    if (fp != m->fingerprint) return fail(BOA_ERR_FINGERPRINT, "container was written with a different model");
+    const uint64_t chunk = get64(c + 24), n = get64(c + 32), last = get64(c + 40);
+    if (chunk == 0 || n != (total + chunk - 1) / chunk || (n && last != total - (n - 1) * chunk))
+        return fail(BOA_ERR_CORRUPT, "inconsistent chunk layout");
+    if (n > (size - kHeaderBytes) / 16) return fail(BOA_ERR_CORRUPT, "index runs past the container");
+    const uint8_t* idx = c + kHeaderBytes;
+    if (get32(c + 52) != boa_crc32(idx, 16 * n)) return fail(BOA_ERR_CORRUPT, "index CRC mismatch");
+    const size_t pay_size = size - kHeaderBytes - 16 * n;
+    size_t end = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        const uint64_t o = get64(idx + 16 * i), z = get64(idx + 16 * i + 8);
+        if (o > pay_size || z > pay_size - o) return fail(BOA_ERR_CORRUPT, "chunk %llu lies outside the payload", (unsigned long long)i);
+        end = std::max<size_t>(end, o + z);
+    }
+    v->total = total;
+    v->chunk = chunk;
+    v->n = n;
+    v->last = last;
+    v->idx = idx;
+    v->pay = idx + 16 * n;
+    v->bytes = kHeaderBytes + 16 * n + end;
+    return BOA_OK;
+}
+
 extern "C" size_t boa_pack_bound(size_t len, size_t chunk_len) {
     if (chunk_len == 0) return 0;
     const size_t n = (len + chunk_len - 1) / chunk_len;
@@ -2291,15 +2352,7 @@ extern "C" boa_status boa_pack(boa_model* m, const uint8_t* data, size_t len, si
         w += sizes[i];
         pay += sizes[i];
     }
-    memcpy(out, "BOA1", 4);
-    put32(out + 4, kBoaVersion);
-    put64(out + 8, m->fingerprint);
-    put64(out + 16, len);
-    put64(out + 24, chunk_len);
-    put64(out + 32, n);
-    put64(out + 40, n ? lens[n - 1] : 0);
-    put32(out + 48, boa_crc32(out, 48));
-    put32(out + 52, boa_crc32(idx, 16 * n));
+    write_container_header(out, m->fingerprint, len, chunk_len, n, n ? lens[n - 1] : 0);
     *out_size = w;
     return BOA_OK;
 }
@@ -2316,32 +2369,315 @@ extern "C" boa_status boa_unpack_info(const uint8_t* c, size_t size, uint64_t* t
 extern "C" boa_status boa_unpack(boa_model* m, const uint8_t* c, size_t size, uint8_t* out, size_t cap,
                                  size_t* out_len) {
     if (!m || !out_len || (cap && !out)) return fail(BOA_ERR_ARG, "bad argument");
-    uint64_t total = 0, fp = 0;
-    TRY(boa_unpack_info(c, size, &total, &fp));
-    if (fp != m->fingerprint) return fail(BOA_ERR_FINGERPRINT, "container was written with a different model");
-    const uint64_t chunk = get64(c + 24), n = get64(c + 32), last = get64(c + 40);
-    if (chunk == 0 || n != (total + chunk - 1) / chunk || (n && last != total - (n - 1) * chunk))
-        return fail(BOA_ERR_CORRUPT, "inconsistent chunk layout");
-    if (n > (size - kHeaderBytes) / 16) return fail(BOA_ERR_CORRUPT, "index runs past the container");
-    const uint8_t* idx = c + kHeaderBytes;
-    if (get32(c + 52) != boa_crc32(idx, 16 * n)) return fail(BOA_ERR_CORRUPT, "index CRC mismatch");
-    if (cap < total) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "output needs %llu bytes", (unsigned long long)total);
-    const uint8_t* pay = idx + 16 * n;
-    const size_t pay_size = size - kHeaderBytes - 16 * n;
+    ContainerView v;
+    TRY(parse_container(m, c, size, &v));
+    if (cap < v.total) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "output needs %llu bytes", (unsigned long long)v.total);
+    const size_t n = v.n;
     std::vector<const uint8_t*> ptrs(n);
     std::vector<size_t> sizes(n), lens(n);
     std::vector<uint8_t*> outs(n);
-    for (uint64_t i = 0; i < n; i++) {
-        const uint64_t o = get64(idx + 16 * i), z = get64(idx + 16 * i + 8);
-        if (o > pay_size || z > pay_size - o) return fail(BOA_ERR_CORRUPT, "chunk %llu lies outside the payload", (unsigned long long)i);
-        ptrs[i] = pay + o;
-        sizes[i] = z;
-        lens[i] = i + 1 < n ? chunk : last;
-        outs[i] = out + i * chunk;
+    for (size_t i = 0; i < n; i++) {
+        ptrs[i] = v.pay + get64(v.idx + 16 * i);
+        sizes[i] = get64(v.idx + 16 * i + 8);
+        lens[i] = i + 1 < n ? v.chunk : v.last;
+        outs[i] = out + i * v.chunk;
     }
     if (n) TRY(boa_decompress(m, n, ptrs.data(), sizes.data(), lens.data(), outs.data()));
+    *out_len = v.total;
+    return BOA_OK;
+}
+
+// Every container in data[0, size), one after another, decoded with one
+// batched decompression of all their chunks.
+extern "C" boa_status boa_unpack_shards(boa_model* m, const uint8_t* data, size_t size, uint8_t* out, size_t cap,
+                                        size_t* out_len) {
+    if (!m || !out_len || (size && !data) || (cap && !out)) return fail(BOA_ERR_ARG, "bad argument");
+    if (!out) {                                  // size query: validate and sum the lengths
+        size_t at = 0, total = 0;
+        while (at < size) {
+            ContainerView v;
+            TRY(parse_container(m, data + at, size - at, &v));
+            total += v.total;
+            at += v.bytes;
+        }
+        *out_len = total;
+        return BOA_OK;
+    }
+    std::vector<const uint8_t*> ptrs;
+    std::vector<size_t> sizes, lens;
+    std::vector<uint8_t*> outs;
+    size_t at = 0, total = 0;
+    while (at < size) {
+        ContainerView v;
+        TRY(parse_container(m, data + at, size - at, &v));
+        if (cap < total || cap - total < v.total)
+            return fail(BOA_ERR_OUTPUT_TOO_SMALL, "output needs more than %zu bytes", cap);
+        for (uint64_t i = 0; i < v.n; i++) {
+            ptrs.push_back(v.pay + get64(v.idx + 16 * i));
+            sizes.push_back(get64(v.idx + 16 * i + 8));
+            lens.push_back(i + 1 < v.n ? v.chunk : v.last);
+            outs.push_back(out + total + i * v.chunk);
+        }
+        total += v.total;
+        at += v.bytes;
+    }
+    if (!ptrs.empty()) TRY(boa_decompress(m, ptrs.size(), ptrs.data(), sizes.data(), lens.data(), outs.data()));
     *out_len = total;
     return BOA_OK;
+}
+
+// ------------------------------------------------------------ streaming pipeline
+//
+// The caller's thread cuts pushed bytes into sets (set_chunks chunks of
+// chunk_len bytes) in two pinned buffers; a full set is copied to its device
+// buffer on the pipeline's copy stream and queued.  The worker thread takes
+// sets in order, waits for the copy, compresses the set as one batch of
+// streams (compress_impl on the device copy), fetches the coded bytes and
+// appends the set's container to the output.  A set buffer is reused only
+// after the worker has finished with it, so at most two sets are in flight:
+// one compressing, one filling / preloading.
+
+struct boa_stream {
+    boa_model* m = nullptr;
+    size_t chunk = 0, per_set = 0, set_bytes = 0;
+    HostBuf<uint8_t> host[2];
+    DevBuf<uint8_t> dev[2];
+    cudaStream_t copy = nullptr;
+    cudaEvent_t loaded[2] = {nullptr, nullptr};
+    int cur = 0;                  // set buffer being filled (caller's thread)
+    size_t fill = 0;
+    bool finished = false;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::pair<int, size_t>> jobs;   // (set buffer, bytes)
+    bool busy[2] = {false, false};
+    bool running = false;         // worker is compressing a set
+    bool stop = false;
+    boa_status err = BOA_OK;
+    std::string err_msg;
+    std::vector<uint8_t> shards;  // finished containers, in input order
+    size_t read_at = 0;
+    uint64_t sets = 0, preloaded = 0, bytes_in = 0;
+};
+
+// One set (device buffer b, bytes long) into a container appended to shards.
+static boa_status stream_compress_set(boa_stream* s, int b, size_t bytes, std::vector<uint8_t>& shard) {
+    boa_model* m = s->m;
+    const size_t n = (bytes + s->chunk - 1) / s->chunk;
+    std::vector<uint64_t> in_off(n + 1), out_off(n + 1), sizes(n);
+    in_off[0] = out_off[0] = 0;
+    for (size_t i = 0; i < n; i++) {
+        in_off[i + 1] = std::min(bytes, (i + 1) * s->chunk);
+        out_off[i + 1] = out_off[i] + boa_max_compressed_size(in_off[i + 1] - in_off[i]);
+    }
+    TRY(m->d_out.ensure(out_off[n]));
+    TRY(m->h_out.ensure(out_off[n]));
+    TRY(compress_impl(m, n, s->dev[b].p, in_off.data(), m->d_out.p, out_off.data(), sizes.data()));
+    std::vector<uint64_t> pk;
+    TRY(fetch_compressed(m, n, sizes.data(), pk));
+    shard.resize(kHeaderBytes + 16 * n + pk[n]);
+    for (size_t i = 0; i < n; i++) {
+        put64(shard.data() + kHeaderBytes + 16 * i, pk[i]);
+        put64(shard.data() + kHeaderBytes + 16 * i + 8, sizes[i]);
+    }
+    if (pk[n]) memcpy(shard.data() + kHeaderBytes + 16 * n, m->h_out.p, pk[n]);
+    write_container_header(shard.data(), m->fingerprint, bytes, s->chunk, n, in_off[n] - in_off[n - 1]);
+    return BOA_OK;
+}
+
+static void stream_worker(boa_stream* s) {
+    cudaSetDevice(s->m->device);
+    for (;;) {
+        std::pair<int, size_t> job;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] { return s->stop || !s->jobs.empty(); });
+            if (s->jobs.empty()) return;
+            job = s->jobs.front();
+            s->jobs.pop_front();
+            s->running = true;
+        }
+        const int b = job.first;
+        // the set's copy finished while the previous set was compressing
+        const bool early = cudaEventQuery(s->loaded[b]) == cudaSuccess;
+        boa_status st = BOA_OK;
+        std::vector<uint8_t> shard;
+        if (cudaEventSynchronize(s->loaded[b]) != cudaSuccess)
+            st = fail(BOA_ERR_CUDA, "set copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+        bool skip;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            skip = s->err != BOA_OK;
+        }
+        if (st == BOA_OK && !skip) st = stream_compress_set(s, b, job.second, shard);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (st != BOA_OK && s->err == BOA_OK) {
+                s->err = st;
+                s->err_msg = boa_last_error();
+            }
+            if (st == BOA_OK && !skip) {
+                s->shards.insert(s->shards.end(), shard.begin(), shard.end());
+                s->sets++;
+                s->preloaded += early ? 1 : 0;
+            }
+            s->busy[b] = false;
+            s->running = false;
+        }
+        s->cv.notify_all();
+    }
+}
+
+// The worker's first error, re-raised on the caller's thread.
+static boa_status stream_error(boa_stream* s) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->err == BOA_OK) return BOA_OK;
+    return fail(s->err, "streaming pipeline: %s", s->err_msg.c_str());
+}
+
+// Hands the filled set buffer to the worker and switches to the other one.
+static boa_status stream_submit(boa_stream* s) {
+    const int b = s->cur;
+    CU(cudaMemcpyAsync(s->dev[b].p, s->host[b].p, s->fill, cudaMemcpyHostToDevice, s->copy));
+    CU(cudaEventRecord(s->loaded[b], s->copy));
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->busy[b] = true;
+        s->jobs.emplace_back(b, s->fill);
+        s->bytes_in += s->fill;
+    }
+    s->cv.notify_all();
+    s->cur ^= 1;
+    s->fill = 0;
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_stream_open(boa_model* m, size_t chunk_len, size_t set_chunks, boa_stream** out) {
+    if (!m || !out || chunk_len == 0 || set_chunks == 0) return fail(BOA_ERR_ARG, "bad argument");
+    if (set_chunks > (1u << 30) || chunk_len > ((size_t)1 << 40) / set_chunks)
+        return fail(BOA_ERR_ARG, "set of %zu x %zu bytes is too large", set_chunks, chunk_len);
+    *out = nullptr;
+    CU(cudaSetDevice(m->device));
+    auto* s = new boa_stream();
+    s->m = m;
+    s->chunk = chunk_len;
+    s->per_set = set_chunks;
+    s->set_bytes = chunk_len * set_chunks;
+    boa_status st = BOA_OK;
+    for (int b = 0; b < 2 && st == BOA_OK; b++) {
+        st = s->host[b].ensure(s->set_bytes);
+        if (st == BOA_OK) st = s->dev[b].ensure(s->set_bytes);
+        if (st == BOA_OK && cudaEventCreateWithFlags(&s->loaded[b], cudaEventDisableTiming) != cudaSuccess)
+            st = fail(BOA_ERR_CUDA, "cudaEventCreate failed");
+    }
+    if (st == BOA_OK && cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess)
+        st = fail(BOA_ERR_CUDA, "cudaStreamCreate failed");
+    if (st != BOA_OK) {
+        boa_stream_close(s);
+        return st;
+    }
+    s->worker = std::thread(stream_worker, s);
+    *out = s;
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_stream_push(boa_stream* s, const uint8_t* data, size_t len) {
+    if (!s || (len && !data)) return fail(BOA_ERR_ARG, "bad argument");
+    if (s->finished) return fail(BOA_ERR_ARG, "pipeline already finished");
+    TRY(stream_error(s));
+    CU(cudaSetDevice(s->m->device));
+    while (len) {
+        if (s->fill == 0) {
+            // wait until the worker is done with this set buffer
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] { return !s->busy[s->cur] || s->err != BOA_OK; });
+        }
+        TRY(stream_error(s));
+        const size_t take = std::min(len, s->set_bytes - s->fill);
+        memcpy(s->host[s->cur].p + s->fill, data, take);
+        s->fill += take;
+        data += take;
+        len -= take;
+        if (s->fill == s->set_bytes) TRY(stream_submit(s));
+    }
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_stream_finish(boa_stream* s) {
+    if (!s) return fail(BOA_ERR_ARG, "bad argument");
+    if (!s->finished) {
+        s->finished = true;
+        if (s->fill) {
+            {
+                std::unique_lock<std::mutex> lk(s->mu);
+                s->cv.wait(lk, [&] { return !s->busy[s->cur] || s->err != BOA_OK; });
+            }
+            TRY(stream_error(s));
+            CU(cudaSetDevice(s->m->device));
+            TRY(stream_submit(s));
+        }
+    }
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv.wait(lk, [&] { return s->jobs.empty() && !s->running; });
+    }
+    return stream_error(s);
+}
+
+extern "C" size_t boa_stream_available(const boa_stream* s) {
+    if (!s) return 0;
+    auto* w = const_cast<boa_stream*>(s);
+    std::lock_guard<std::mutex> lk(w->mu);
+    return w->shards.size() - w->read_at;
+}
+
+extern "C" boa_status boa_stream_read(boa_stream* s, uint8_t* out, size_t cap, size_t* out_size) {
+    if (!s || !out_size || (cap && !out)) return fail(BOA_ERR_ARG, "bad argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const size_t k = std::min(cap, s->shards.size() - s->read_at);
+    if (k) memcpy(out, s->shards.data() + s->read_at, k);
+    s->read_at += k;
+    if (s->read_at == s->shards.size()) {
+        s->shards.clear();
+        s->read_at = 0;
+    }
+    *out_size = k;
+    return BOA_OK;
+}
+
+extern "C" boa_status boa_stream_stats(const boa_stream* s, uint64_t* bytes_in, uint64_t* sets,
+                                       uint64_t* preloaded) {
+    if (!s) return fail(BOA_ERR_ARG, "bad argument");
+    auto* w = const_cast<boa_stream*>(s);
+    std::lock_guard<std::mutex> lk(w->mu);
+    if (bytes_in) *bytes_in = w->bytes_in;
+    if (sets) *sets = w->sets;
+    if (preloaded) *preloaded = w->preloaded;
+    return BOA_OK;
+}
+
+extern "C" void boa_stream_close(boa_stream* s) {
+    if (!s) return;
+    if (s->worker.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+        }
+        s->cv.notify_all();
+        s->worker.join();           // the worker drains the queued sets first
+    }
+    cudaSetDevice(s->m->device);
+    if (s->copy) {
+        cudaStreamSynchronize(s->copy);
+        cudaStreamDestroy(s->copy);
+    }
+    for (int b = 0; b < 2; b++) {
+        if (s->loaded[b]) cudaEventDestroy(s->loaded[b]);
+        s->host[b].release();
+        s->dev[b].release();
+    }
+    delete s;
 }
 
 // ------------------------------------------------------------ training step

@@ -89,3 +89,19 @@ def test_container_header_checks_without_gpu():
     t, f = C.c_uint64(), C.c_uint64()
     assert lib.boa_unpack_info(junk.ctypes.data_as(C.c_void_p), 100, C.byref(t), C.byref(f)) == 3
     assert lib.boa_unpack_info(junk.ctypes.data_as(C.c_void_p), 10, C.byref(t), C.byref(f)) == 7
+
+
+def test_stream_entry_points_check_arguments():
+    """The streaming pipeline's argument checks need no GPU."""
+    import ctypes as C
+    lib = _lib.load()
+    h = C.c_void_p()
+    assert lib.boa_stream_open(None, 16, 4, C.byref(h)) == 1 and not h.value
+    assert lib.boa_stream_push(None, None, 0) == 1
+    assert lib.boa_stream_finish(None) == 1
+    assert lib.boa_stream_available(None) == 0
+    n = C.c_size_t()
+    assert lib.boa_stream_read(None, None, 0, C.byref(n)) == 1
+    assert lib.boa_stream_stats(None, None, None, None) == 1
+    lib.boa_stream_close(None)
+    assert lib.boa_unpack_shards(None, None, 0, None, 0, C.byref(n)) == 1
