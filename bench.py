@@ -448,8 +448,12 @@ def run_boa(args):
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         v_cpu, dt, nb, threads = oracle_sample(streams[:cores], args.cpu_prefix)
-        cpu = {"value": v_cpu, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {args.cpu_prefix} B of {threads} of the 4096 streams ({nb} B), compress + decompress, {dt:.1f} s"}
+        one = max(args.cpu_prefix // 4, 2)
+        v_1, dt_1, nb_1, _ = oracle_sample(streams[:1], one)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": threads, "kind": "oracle", "nproc": cores,
+               "sample": f"first {args.cpu_prefix} B of {threads} of the 4096 streams ({nb} B), compress + decompress, {dt:.1f} s",
+               "single_thread": {"value": v_1, "unit": UNIT,
+                                 "sample": f"first {one} B of stream 0, one thread, {dt_1:.1f} s"}}
 
     forms = {}
     if world == 1 and args.forms:
