@@ -2448,7 +2448,7 @@ struct boa_stream {
     size_t fill = 0;
     bool finished = false;
     std::thread worker;
-    std::mutex mu;
+    mutable std::mutex mu;
     std::condition_variable cv;
     std::deque<std::pair<int, size_t>> jobs;   // (set buffer, bytes)
     bool busy[2] = {false, false};
@@ -2627,9 +2627,8 @@ extern "C" boa_status boa_stream_finish(boa_stream* s) {
 
 extern "C" size_t boa_stream_available(const boa_stream* s) {
     if (!s) return 0;
-    auto* w = const_cast<boa_stream*>(s);
-    std::lock_guard<std::mutex> lk(w->mu);
-    return w->shards.size() - w->read_at;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return s->shards.size() - s->read_at;
 }
 
 extern "C" boa_status boa_stream_read(boa_stream* s, uint8_t* out, size_t cap, size_t* out_size) {
@@ -2649,11 +2648,10 @@ extern "C" boa_status boa_stream_read(boa_stream* s, uint8_t* out, size_t cap, s
 extern "C" boa_status boa_stream_stats(const boa_stream* s, uint64_t* bytes_in, uint64_t* sets,
                                        uint64_t* preloaded) {
     if (!s) return fail(BOA_ERR_ARG, "bad argument");
-    auto* w = const_cast<boa_stream*>(s);
-    std::lock_guard<std::mutex> lk(w->mu);
-    if (bytes_in) *bytes_in = w->bytes_in;
-    if (sets) *sets = w->sets;
-    if (preloaded) *preloaded = w->preloaded;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (bytes_in) *bytes_in = s->bytes_in;
+    if (sets) *sets = s->sets;
+    if (preloaded) *preloaded = s->preloaded;
     return BOA_OK;
 }
 
