@@ -122,19 +122,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def sources_sha256(paths) -> str | None:
+    """One hash over the given source files, in order (None if one is missing)."""
+    h = hashlib.sha256()
+    for rel in paths:
+        f = os.path.join(ROOT, rel)
+        if not os.path.exists(f):
+            return None
+        h.update(rel.encode() + b"\0" + open(f, "rb").read())
+    return h.hexdigest()
+
+
 def traffic_for(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel's
-    source is unchanged since it was captured (else None)."""
+    """DRAM bytes per launch from a committed ncu summary, if none of the
+    kernel's sources (its file and every header it includes) changed since
+    the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         t = json.load(f)
     ent = t.get(kernel)
-    if not ent:
-        return None
-    src = os.path.join(ROOT, ent["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != ent["source_sha256"]:
+    srcs = ent.get("sources") if isinstance(ent, dict) else None
+    if not srcs or sources_sha256(srcs) != ent.get("sources_sha256"):
         return None
     return ent
 

@@ -105,3 +105,20 @@ def test_stream_entry_points_check_arguments():
     assert lib.boa_stream_stats(None, None, None, None) == 1
     lib.boa_stream_close(None)
     assert lib.boa_unpack_shards(None, None, 0, None, 0, C.byref(n)) == 1
+
+
+def test_bench_traffic_record_is_read_safely(tmp_path, monkeypatch):
+    """bench.traffic_for returns the committed record only while the decode
+    scan's sources hash as recorded, and None (never an exception) for a
+    stale, old-format or missing record."""
+    import json
+    import bench
+    ent = bench.traffic_for("decompress:scan")
+    assert ent is None or ent["bytes_per_launch"] > 0
+    assert bench.traffic_for("no such kernel") is None
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    assert bench.traffic_for("decompress:scan") is None
+    for rec in ({"source": "x.cuh", "source_sha256": "0"}, {"sources": ["x.cuh"], "sources_sha256": "0"}):
+        (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"decompress:scan": rec}))
+        assert bench.traffic_for("decompress:scan") is None
