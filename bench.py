@@ -514,6 +514,68 @@ def run_boa(args):
         dist.destroy_process_group()
 
 
+def run_stream_report(args):
+    """The streaming pipeline (boa_stream_*) on the 64 MiB jet table: bytes
+    pushed from host memory in 4 MiB pieces, one .boa shard per set of
+    --set-chunks x 16 KB chunks (each set compressed while the next one
+    fills and pre-loads), then boa_unpack_shards back to host memory; and
+    boa_pack / boa_unpack of the same bytes as one container, for
+    comparison.  Host clock around the synchronous calls (host buffers at
+    both ends); rank 0 only."""
+    import torch
+    rank, _, local = env_rank()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_2511_11337_b300 import api
+    path = synth.make_model_file(os.path.join(tempfile.mkdtemp(), "paper.boaw"), synth.PAPER_SCALE, seed=2)
+    buf = synth.atlas_workload(args.streams, args.stream_len, seed=2000)
+    model = api.Model(path, device=local, precision=PREC[args.precision], max_rows=args.max_rows)
+    per = args.set_chunks
+    tuned = model.autotune(per, args.stream_len) if args.autotune else None
+    piece = 4 << 20
+
+    def streamed(data):
+        t0 = time.perf_counter()
+        with api.Stream(model, args.stream_len, per) as st:
+            for i in range(0, len(data), piece):
+                st.push(data[i:i + piece])
+            st.finish()
+            blob = st.read()
+            stats = st.stats()
+        t1 = time.perf_counter()
+        out = model.unpack_shards(blob)
+        t2 = time.perf_counter()
+        assert out == data
+        return t1 - t0, t2 - t1, len(blob), stats
+
+    def packed(data):
+        t0 = time.perf_counter()
+        box = model.pack(data, args.stream_len)
+        t1 = time.perf_counter()
+        assert model.unpack(box) == data
+        return t1 - t0, time.perf_counter() - t1
+
+    for _ in range(args.warmup):
+        streamed(buf[:2 * per * args.stream_len])
+    runs = [streamed(buf) for _ in range(args.steps)]
+    tc = statistics.mean(r[0] for r in runs)
+    td = statistics.mean(r[1] for r in runs)
+    pk = [packed(buf) for _ in range(max(1, args.steps // 2))]
+    pc, pd = statistics.mean(r[0] for r in pk), statistics.mean(r[1] for r in pk)
+    mb = len(buf) / 1e6
+    print(json.dumps({
+        "report": "streaming pipeline", "metric": "streamed compress & decompress MB/s on 1 B300, host buffers at both ends",
+        "value": mb / (tc + td), "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}; pushed in 4 MiB pieces, sets of {per} x {args.stream_len} B "
+                               f"({len(buf) // (per * args.stream_len)} shards)", "autotuned": tuned},
+        "compress_MBps": mb / tc, "decompress_MBps": mb / td, "compression_ratio": len(buf) / runs[-1][2],
+        "sets": runs[-1][3]["sets"], "preloaded_sets": runs[-1][3]["preloaded"],
+        "pack_unpack_MBps": mb / (pc + pd), "pack_MBps": mb / pc, "unpack_MBps": mb / pd,
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -523,8 +585,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--streams", type=int, default=N_STREAMS)
     ap.add_argument("--stream-len", type=int, default=STREAM_LEN)
-    ap.add_argument("--workload", default="jet", choices=["jet", "mixed"],
-                    help="jet: the benchmark's 64 MiB jet table; mixed: an uneven ATLAS/CMS mix of log-uniform 1 KB-1 MB streams (--streams sources)")
+    ap.add_argument("--workload", default="jet", choices=["jet", "mixed", "stream"],
+                    help="jet: the benchmark's 64 MiB jet table; mixed: an uneven ATLAS/CMS mix of log-uniform 1 KB-1 MB "
+                         "streams (--streams sources); stream: the jet table through the streaming pipeline (a report)")
+    ap.add_argument("--set-chunks", type=int, default=1024, help="chunks per streaming set (--workload stream)")
     ap.add_argument("--max-rows", type=int, default=0)
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "bf16", "tf32x3", "fp8"])
     ap.add_argument("--forms", default="fp32,bf16,fp8", help="other precision forms to report ('' for none)")
@@ -539,6 +603,8 @@ def main():
         run_reference(args)
     elif args.report == "precision":
         run_precision_report(args)
+    elif args.workload == "stream":
+        run_stream_report(args)
     else:
         run_boa(args)
 
