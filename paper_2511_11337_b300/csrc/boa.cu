@@ -862,7 +862,12 @@ static void launch_t3(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
     const int split = tc_splits(N, K, kT3BK);
     const bool in_cta = (long long)grid.x * grid.y >= m->num_sms;
-    const int chunks = in_cta && split * T3Smem<BN>::kTmemCols <= 512 ? split : 1;
+    // in-CTA chunks while the CTA's TMEM (accumulators + A stages) still
+    // leaves room for the second CTA an SM holds
+    using L = T3Smem<BN>;
+    const uint32_t room = L::kOnePerSm ? 512u : 256u;
+    const int chunks = in_cta && L::pow2_cols((uint32_t)(split * L::kTmemCols + L::kStages * L::kACols)) <= room
+                           ? split : 1;
     const int peers = split / chunks;
     if ((long long)grid.x * grid.y * peers < m->num_sms)
         launch_t3_cfg<BN, EPI, true>(m, grid, peers, chunks, ta, th, tl, bias, C, M, N, K);

@@ -154,6 +154,18 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 16 consecutive 32-bit TMEM columns of the warp's 32 lanes (one lane per
+// thread), the store counterpart of tmem_ld16_nowait.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Epilogue shared by the tensor-core kernels.  Warp q owns accumulator rows
 // (TMEM lanes) 32q .. 32q+31.  Phase 1 (tc_stage_tile): it copies them, 16
 // columns per tcgen05.ld, into its own slice of the (now idle) pipeline
@@ -542,9 +554,11 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 //     A . W^T ~= A_hi W_hi^T + A_hi W_lo^T + A_lo W_hi^T
 // is accumulated in FP32 in TMEM (kind::tf32, K = 8 per instruction), the
 // three products of each K step always in that order.  The weights arrive
-// pre-split; A arrives as FP32 by TMA and four converter warps split each
-// stage in shared memory (in place for hi, a second buffer for lo) before the
-// MMA thread consumes it.  Warps: 0 TMA, 1 MMA, 2-5 converters then epilogue.
+// pre-split (B_hi, B_lo in shared memory by TMA); A arrives as FP32 by TMA,
+// and four converter warps split each stage's rows into A_hi and A_lo in
+// TMEM (each thread its row, in its lane), where the MMAs read their A
+// operand.  TMEM holds the accumulator(s) in its first columns and the A
+// stages after them.  Warps: 0 TMA, 1 MMA, 2-5 converters then epilogue.
 
 constexpr int kT3Threads = 192;
 constexpr int kT3BK = 32;                  // 32 fp32 = 128 bytes = one swizzle atom row
@@ -566,6 +580,17 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint6
         ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// The same MMA with A read from TMEM (row i of A in lane i, one 32-bit
+// column per K element) instead of shared memory.
+__device__ __forceinline__ void umma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -574,16 +599,29 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 template <int BN, bool DEEP = false>
 struct T3Smem {
-    static constexpr int kA = kTcBM * kT3BK * 4;     // 16 KB (fp32 -> hi in place)
+    static constexpr int kA = kTcBM * kT3BK * 4;     // 16 KB: the FP32 A tile as TMA writes it
     static constexpr int kB = BN * kT3BK * 4;
-    static constexpr int kStage = 2 * kA + 2 * kB;   // A_hi, A_lo, B_hi, B_lo
+    static constexpr int kStage = kA + 2 * kB;       // A, B_hi, B_lo (A_hi and A_lo go to TMEM)
     // two CTAs per SM with two stages each where they fit (BN <= 64);
-    // otherwise (deep grids, or BN = 128) one CTA with up to ~200 KB of stages
+    // otherwise (deep grids, or BN >= 128) one CTA with up to ~200 KB of stages
     static constexpr bool kOnePerSm = DEEP || 2 * kStage > 110 * 1024;
-    static constexpr int kStages = kOnePerSm ? ((200 * 1024) / kStage > 8 ? 8 : (200 * 1024) / kStage) : 2;
-    static constexpr int kTmemCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static constexpr int kTmemCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;   // per K chunk
+    static constexpr int kACols = 2 * kT3BK;         // TMEM columns of one stage's A_hi | A_lo
+    static constexpr int kStagesSmem = kOnePerSm ? ((200 * 1024) / kStage > 8 ? 8 : (200 * 1024) / kStage) : 2;
+    static constexpr int kStagesTmem = (512 - kTmemCols) / kACols;
+    static constexpr int kStages = kStagesSmem < kStagesTmem ? kStagesSmem : kStagesTmem;
     static constexpr int kBars = 3 * kStages + 1;    // full, converted, empty, done
-    static constexpr size_t kBytes = 1024 + (size_t)kStages * kStage + 8 * kBars + 16;
+    static constexpr size_t kBytesUsed = 1024 + (size_t)kStages * kStage + 8 * kBars + 16;
+    // Shared memory also caps how many CTAs share an SM's 512 TMEM columns:
+    // a two-per-SM CTA asks for at least 100 KB, so at most two are resident
+    // (each allocating <= 256 columns), and a one-per-SM CTA more than half
+    // the SM.  Without that cap the CTAs of a split-K cluster could wait on
+    // each other while a peer waits in tcgen05.alloc.
+    static constexpr size_t kBytes = kOnePerSm || kBytesUsed >= 100 * 1024 ? kBytesUsed : 100 * 1024;
+    static_assert((size_t)kStages * kStage >= (size_t)kTcBM * BN * 4, "the epilogue stages the tile here");
+    __host__ __device__ static constexpr uint32_t pow2_cols(uint32_t n) {
+        return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512;
+    }
 };
 
 template <int BN, int EPI, bool DEEP = false>
@@ -609,7 +647,8 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     const int nk = K / kT3BK / (int)gridDim.z;           // split K: this CTA's K blocks
     const int kb0 = (int)blockIdx.z * nk;
     const int nkc = nk / chunks;                         // K blocks per TMEM chunk
-    const uint32_t tmem_cols = (uint32_t)(L::kTmemCols * chunks);
+    const uint32_t a_col0 = (uint32_t)(L::kTmemCols * chunks);   // first A stage's TMEM column
+    const uint32_t tmem_cols = L::pow2_cols(a_col0 + (uint32_t)(L::kStages * L::kACols));
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -644,10 +683,10 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 break;
             }
             uint8_t* st = smem + (size_t)s * L::kStage;
-            mbar_expect_tx(&full[s], L::kA + 2 * L::kB);
+            mbar_expect_tx(&full[s], L::kStage);
             tma_load_2d(&tmA, &full[s], st, (kb0 + kb) * kT3BK, m0);
-            tma_load_2d(&tmBhi, &full[s], st + 2 * L::kA, (kb0 + kb) * kT3BK, n0);
-            tma_load_2d(&tmBlo, &full[s], st + 2 * L::kA + L::kB, (kb0 + kb) * kT3BK, n0);
+            tma_load_2d(&tmBhi, &full[s], st + L::kA, (kb0 + kb) * kT3BK, n0);
+            tma_load_2d(&tmBlo, &full[s], st + L::kA + L::kB, (kb0 + kb) * kT3BK, n0);
             armed_last = kb;
         }
     } else if (threadIdx.x == 32) {
@@ -657,44 +696,63 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             const int s = kb % L::kStages;
             if (!mbar_wait(&conv[s], (kb / L::kStages) & 1)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ahi = smem_u32(smem + (size_t)s * L::kStage);
-            const uint32_t alo = ahi + L::kA;
-            const uint32_t bhi = ahi + 2 * L::kA;
+            const uint32_t bhi = smem_u32(smem + (size_t)s * L::kStage + L::kA);
             const uint32_t blo = bhi + L::kB;
+            const uint32_t ahi = tmem + a_col0 + (uint32_t)(s * L::kACols);   // TMEM: A_hi | A_lo
+            const uint32_t alo = ahi + kT3BK;
             const int kc = kb % nkc;                     // K block within its chunk
             const uint32_t d = tmem + (uint32_t)((kb / nkc) * L::kTmemCols);
 #pragma unroll
             for (int k = 0; k < kT3BK / 8; k++) {
-                const uint32_t o = 32 * k;
-                umma_tf32(d, umma_desc_sw128(ahi + o), umma_desc_sw128(bhi + o), idesc, (kc | k) != 0 ? 1u : 0u);
-                umma_tf32(d, umma_desc_sw128(ahi + o), umma_desc_sw128(blo + o), idesc, 1u);
-                umma_tf32(d, umma_desc_sw128(alo + o), umma_desc_sw128(bhi + o), idesc, 1u);
+                const uint32_t o = 32 * k;               // 8 TF32 of K: 32 bytes of B, 8 TMEM columns of A
+                umma_tf32_ta(d, ahi + 8 * k, umma_desc_sw128(bhi + o), idesc, (kc | k) != 0 ? 1u : 0u);
+                umma_tf32_ta(d, ahi + 8 * k, umma_desc_sw128(blo + o), idesc, 1u);
+                umma_tf32_ta(d, alo + 8 * k, umma_desc_sw128(bhi + o), idesc, 1u);
             }
             umma_commit(&empty[s]);
         }
         if (!ok) atomicExch(&abort_flag, 1);
         umma_commit(&done[0]);
     } else if (warp >= 2) {
-        // converters: split each A stage into hi (in place) and lo
-        const int ct = threadIdx.x - 64;
+        // converters: thread (quadrant q = warp % 4, lane) takes A row
+        // 32 q + lane of each stage, splits it into hi and lo, and writes both
+        // into its TMEM lane: A_hi in the stage's columns 0..31, A_lo in 32..63
+        const int q = warp % 4;
+        const int r = 32 * q + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + a_col0;
         for (int kb = 0; kb < nk; kb++) {
             const int s = kb % L::kStages;
             if (!mbar_wait(&full[s], (kb / L::kStages) & 1)) {
                 atomicExch(&abort_flag, 1);
                 break;
             }
-            float4* a = reinterpret_cast<float4*>(smem + (size_t)s * L::kStage);
-            float4* lo = reinterpret_cast<float4*>(smem + (size_t)s * L::kStage + L::kA);
-#pragma unroll 4
-            for (int i = ct; i < L::kA / 16; i += 128) {
-                const float4 v = a[i];
-                float4 h, l;
-                h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
-                l.x = __fsub_rn(v.x, h.x); l.y = __fsub_rn(v.y, h.y); l.z = __fsub_rn(v.z, h.z); l.w = __fsub_rn(v.w, h.w);
-                a[i] = h;
-                lo[i] = l;
+            // the stage's TMEM columns were last read by MMAs that completed
+            // before this stage's loads were issued
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // row r of the 128-byte-swizzled tile: 16-byte chunk c sits at
+            // chunk position c ^ (r % 8)
+            const uint8_t* row = smem + (size_t)s * L::kStage + (size_t)r * 128;
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const int ch = 4 * half + c;
+                    const float4 v = *reinterpret_cast<const float4*>(row + ((ch ^ (r & 7)) << 4));
+                    const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const float h = tf32_rna(x[e]);
+                        hi[4 * c + e] = __float_as_uint(h);
+                        lo[4 * c + e] = __float_as_uint(__fsub_rn(x[e], h));
+                    }
+                }
+                const uint32_t col = trow + (uint32_t)(s * L::kACols + 16 * half);
+                tmem_st16(col, hi);
+                tmem_st16(col + kT3BK, lo);
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tmem_wait_st();
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
         }
     }
