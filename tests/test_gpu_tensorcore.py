@@ -49,8 +49,8 @@ def api():
 
 SHAPES = [(128, 128, 64), (300, 1024, 256), (4096, 48, 512), (1000, 256, 512), (77, 64, 64), (129, 36, 64),
           (513, 256, 1024), (8500, 256, 256), (8300, 1024, 128),   # these two: compression-size 256-wide tiles
-          (20000, 256, 512), (19000, 48, 512), (19000, 128, 256)]  # grids that fill the GPU (3xTF32 x_proj:
-                                                                   # split K inside one CTA's TMEM)
+          (20000, 256, 512), (19000, 48, 512), (19000, 128, 256)]  # grids that fill the GPU (BF16 / FP8
+                                                                   # x_proj: split K inside one CTA's TMEM)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -80,8 +80,9 @@ def test_gemm_rows_independent_of_batch(api, precision, NK):
     """A row's result does not depend on the batch it sits in: under split K
     (its partial sums added in an order fixed by (N, K) alone, whether the
     chunks run on the CTAs of a cluster and meet through distributed shared
-    memory, as in the small slices, or sit in one CTA's TMEM, as in 3xTF32
-    grids that fill the GPU: the 20000-row batch), and across tile widths
+    memory, as in the small slices, or sit in one CTA's TMEM, as in the BF16
+    and FP8 forms' grids that fill the GPU: the 20000-row batch), and across
+    tile widths
     (batches above 8192 rows run 256- or 128-wide tiles, the slices the
     narrower decode-size ones)."""
     N, K = NK
