@@ -61,6 +61,16 @@ def reduce_max(value: float, dist, device) -> float:
     return float(t.item())
 
 
+def reduce_sum(value: float, dist, device) -> float:
+    """Sum over ranks (the bytes the whole job processed)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -382,6 +392,7 @@ def run_boa(args):
     # times below add up to more than the decompression phase)
     phase_ms = {"compress": round(statistics.mean(a.elapsed_time(c) for a, c, _ in evs), 1),
                 "decompress": round(statistics.mean(c.elapsed_time(b) for _, c, b in evs), 1)}
+    job_bytes = reduce_sum(float(total), dist, "cuda") if dist else float(total)
     if dist:
         ms = reduce_max(ms, dist, "cuda")
         dist.barrier()
@@ -403,7 +414,7 @@ def run_boa(args):
         e2e_s = statistics.mean(e2e_times)
         if dist:
             e2e_s = reduce_max(e2e_s, dist, "cuda")      # the job ends with its slowest rank
-        e2e = {"value": world * total / 1e6 / e2e_s, "unit": UNIT,
+        e2e = {"value": job_bytes / 1e6 / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": total + e2e_comp, "d2h_bytes_per_step": e2e_comp + total}
 
     if rank != 0:
@@ -411,7 +422,7 @@ def run_boa(args):
             dist.destroy_process_group()
         return
 
-    value = world * total / 1e6 / (ms / 1e3)
+    value = job_bytes / 1e6 / (ms / 1e3)
     peaks, peak_src = measured_peaks()
     # Per-(phase, class) device time per step: compression launches are all
     # timed; of the decode steps (CUDA graphs of 32) one eager step per graph

@@ -1,5 +1,6 @@
 """The replica path's host logic on two CPU ranks (gloo): every stream goes
-to exactly one rank, and the job time is the slowest rank's."""
+to exactly one rank, the job time is the slowest rank's, and the job's
+bytes are the sum over ranks."""
 import os
 import socket
 import sys
@@ -26,9 +27,10 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     lo, hi = bench.shard_range(8193, rank, world)
     t = bench.reduce_max(10.0 * (rank + 1), dist, "cpu")
+    b = bench.reduce_sum(float(hi - lo), dist, "cpu")
     dist.barrier()
     dist.destroy_process_group()
-    q.put((rank, lo, hi, t))
+    q.put((rank, lo, hi, t, b))
 
 
 @pytest.mark.parametrize("world", [2])
@@ -43,7 +45,8 @@ def test_two_gloo_ranks(world):
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    spans = [(lo, hi) for _, lo, hi, _ in res]
+    spans = [(lo, hi) for _, lo, hi, _, _ in res]
     assert spans[0][0] == 0 and spans[-1][1] == 8193
     assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
-    assert all(t == 10.0 * world for *_, t in res)
+    assert all(t == 10.0 * world for *_, t, _ in res)
+    assert all(b == 8193.0 for *_, b in res)          # every stream counted once
