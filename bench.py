@@ -267,6 +267,10 @@ def run_precision_report(args):
     gap on the whole subset and max |d log2 p| on 16 x 1 KB, against the FP64
     oracle, and round-trip MB/s on the GPU."""
     import torch
+    rank, _, local = env_rank()
+    if rank != 0:                                   # a report: rank 0 alone under torchrun
+        return
+    torch.cuda.set_device(local)
     from oracle import oracle as O
     from paper_2511_11337_b300 import api
     path = synth.make_model_file(os.path.join(tempfile.mkdtemp(), "tiny.boaw"), synth.TINY, seed=1)
