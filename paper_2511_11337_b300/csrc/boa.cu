@@ -842,6 +842,21 @@ static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_
 // grids: decode steps) or sit in one CTA's TMEM (grids that fill the GPU:
 // compression, where a cluster's epilogue exchange costs more than it
 // hides), so both give the same bits.
+// TMEM is never oversubscribed: the 3xTF32 CTAs that shared memory lets
+// onto one SM (228 KB, 1 KB reserved per CTA) allocate at most its 512
+// columns between them (one K chunk each; in-CTA chunks are checked in
+// launch_t3).
+template <int BN, bool DEEP>
+constexpr bool t3_tmem_fits() {
+    using L = T3Smem<BN, DEEP>;
+    return L::pow2_cols((uint32_t)(L::kTmemCols + L::kStages * L::kACols)) *
+               (uint32_t)((228 * 1024) / (L::kBytes + 1024)) <= 512u;
+}
+static_assert(t3_tmem_fits<48, false>() && t3_tmem_fits<48, true>() && t3_tmem_fits<64, false>() &&
+                  t3_tmem_fits<64, true>() && t3_tmem_fits<128, false>() && t3_tmem_fits<128, true>() &&
+                  t3_tmem_fits<256, false>() && t3_tmem_fits<256, true>(),
+              "3xTF32 CTAs sharing an SM would need more than 512 TMEM columns");
+
 template <int BN, int EPI, bool DEEP>
 static void launch_t3_cfg(boa_model* m, dim3 grid, int splits, int chunks, const CUtensorMap& ta,
                           const CUtensorMap& th, const CUtensorMap& tl, const float* bias, float* C, long long M,
