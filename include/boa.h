@@ -18,8 +18,15 @@
  *     boa_free_model).
  *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
  *     global memory on the model's device.
- *   - Calls on one model are serialised on that model's CUDA stream; use one
- *     model object per host thread for concurrency.
+ *   - Calls on one model are re-entrant: any number of host threads may call
+ *     into the same model at once.  Each such call holds the model's lock
+ *     for its whole duration (its workspace, tuning, profiling counters and
+ *     tensor-map cache are shared), so concurrent calls on one model run one
+ *     after another on the model's CUDA stream and give the same bytes as
+ *     the same calls made in sequence.  For calls that run at the same time
+ *     on the GPU, use one model object per host thread: each has its own
+ *     stream and workspace.  boa_free_model must not race with other calls
+ *     on the same model.
  *   - Per-stream byte format: out[0] = the stream's first byte (raw), then
  *     the range coder's bytes including its 4-byte flush.  A stream of
  *     length 0 compresses to 0 bytes and a stream of length 1 to 1 byte.
@@ -414,6 +421,36 @@ boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K, const flo
 boa_status boa_debug_enable_cdf_trace(boa_model* model, int on);
 boa_status boa_debug_read_cdf_trace(boa_model* model, uint64_t* out, size_t n);
 
+/* Microbenchmarks of the units the hot path's rooflines are quoted
+ * against (the paper gives no such figures; its throughput discussion names
+ * GPU matrix multiplications as the bottleneck).  Each runs a fixed stream of
+ * independent operations on every SM of `device` and is timed with CUDA
+ * events; *rate receives the whole GPU's rate:
+ *   BOA_MB_EX2    ex2.approx.ftz.f32 results per second (the MUFU unit that
+ *                 computes the scan's exp(Delta A))
+ *   BOA_MB_FFMA   FP32 FLOP/s of scalar FMAs on the CUDA cores
+ *   BOA_MB_FFMA2  FP32 FLOP/s of packed fma.rn.f32x2 (two FMAs each)
+ *   BOA_MB_L2     bytes/s read (16-byte loads, L2 only) from a 32 MiB buffer
+ *   BOA_MB_MMA    tcgen05.mma FLOP/s (2 per multiply-add) with kind 0 TF32,
+ *                 1 BF16 (kind::f16) or 2 E4M3 (kind::f8f6f4); M 128 or 64;
+ *                 N a multiple of 16 (M 128) or 8 (M 64), at most 256; flags
+ *                 bit 0 A operand from TMEM (TF32, M 128), bit 1 alternate
+ *                 two accumulators (N <= 128), bit 2 descriptors computed
+ *                 once and instructions issued in straight-line code (not
+ *                 with bit 1), bit 3 k-blocks cycling through four operand
+ *                 stages issued by one thread, bit 4 the same issued by a
+ *                 whole warp through one elected lane (bits 2-4 exclusive,
+ *                 3 and 4 without bits 0 and 1).  32 bytes of K per
+ *                 instruction, one CTA per SM issuing back to back.
+ * cycles_per_op (may be NULL): BOA_MB_MMA: SM clock cycles per instruction
+ * in steady state (from %clock64); EX2 / FFMA: warp instructions per SM per
+ * nominal clock cycle; L2: 0.  kind, M, N, flags are ignored except for
+ * BOA_MB_MMA.  The call allocates and frees its own buffers and takes well
+ * under a second.  Errors: BOA_ERR_ARG (unknown test or shape), BOA_ERR_CUDA. */
+enum { BOA_MB_EX2 = 0, BOA_MB_FFMA = 1, BOA_MB_FFMA2 = 2, BOA_MB_L2 = 3, BOA_MB_MMA = 4 };
+boa_status boa_microbench(int device, int test, int kind, int M, int N, int flags, double* rate,
+                          double* cycles_per_op);
+
 /* Allocation-free range decoder.  The paper has no counterpart: this entry
  * exists for callers that must not allocate device memory while running --
  * e.g. a data-acquisition process whose GPU memory budget is fixed at
@@ -423,17 +460,20 @@ boa_status boa_debug_read_cdf_trace(boa_model* model, uint64_t* out, size_t n);
  * sequence i's rows first), d_in (sequence i's coded bytes at d_in + i *
  * in_stride, in_sizes[i] of them), d_syms (sum n_syms symbols out).  n_syms
  * and in_sizes are host arrays.  cuda_stream: cudaStream_t or NULL (legacy
- * default stream); the call returns after that stream is synchronised.
+ * default stream); it must belong to the current device (BOA_ERR_ARG
+ * otherwise).  The call synchronises that stream before it returns (it reads
+ * back a status word), so it can never be recorded into a CUDA graph: do not
+ * call it while that stream is being captured.
  * Scratch (per-sequence offsets, sizes and status words) lives in one
  * statically sized device array of about 1.8 MB that every GPU loading this
  * library holds until the process exits; the call allocates nothing.
  * Limit: at most 65536 sequences per call (BOA_ERR_ARG beyond it).  The first
  * call on each device looks up the array's device address (once, under a
- * lock); make that first call before any stream capture.  All calls share the
- * one array, so calls whose work overlaps on the GPU (different streams or
- * host threads) race and must be serialised by the caller.  Errors:
- * BOA_ERR_ARG, BOA_ERR_CORRUPT (some sequence did not decode cleanly),
- * BOA_ERR_CUDA. */
+ * lock) and keeps it for the life of the process, so the entry point must
+ * not be used on a device after cudaDeviceReset.  All calls share the one
+ * array, so calls whose work overlaps on the GPU (different streams or host
+ * threads) race and must be serialised by the caller.  Errors: BOA_ERR_ARG,
+ * BOA_ERR_CORRUPT (some sequence did not decode cleanly), BOA_ERR_CUDA. */
 boa_status boa_decode_cdfs_static(size_t n_seq, const size_t* n_syms, const uint32_t* d_cdfs,
                                   const uint8_t* d_in, size_t in_stride, const size_t* in_sizes,
                                   uint8_t* d_syms, void* cuda_stream);

@@ -13,8 +13,8 @@
  * Only the test suite, the package smoke check and the benchmark's CPU
  * baseline leg may call this file.  It shares no code with the CUDA library.
  *
- * Readings taken where the paper is silent or loose (same ids as the design
- * notes):
+ * Readings taken where the paper is silent or loose, each with an id that
+ * the tests and the CUDA library's comments also use:
  *   R1  block:  u = x + Mamba(LN_a(x));  x = LN_b(u + FFN(u)) when an FFN is
  *       present (FFN = Linear(d,F) -> exact-erf GELU -> Linear(F,d)), else
  *       x = LN_b(u).  Logits = head(x) after the last block.

@@ -59,6 +59,7 @@ SIGNATURES = {
     "boa_debug_enable_cdf_trace": (i32, [vp, i32]),
     "boa_debug_read_cdf_trace": (i32, [vp, vp, sz]),
     "boa_decode_cdfs_static": (i32, [sz, vp, vp, vp, sz, vp, vp, vp]),
+    "boa_microbench": (i32, [i32, i32, i32, i32, i32, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
 STATUS = {0: "BOA_OK", 1: "BOA_ERR_ARG", 2: "BOA_ERR_IO", 3: "BOA_ERR_FORMAT", 4: "BOA_ERR_CUDA",

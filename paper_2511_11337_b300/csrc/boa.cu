@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <condition_variable>
 #include <cstdarg>
@@ -34,6 +35,7 @@
 #include "kernels.cuh"
 #include "scan_step.cuh"
 #include "scan_train.cuh"
+#include "peaks.cuh"
 #include "train_step.cuh"
 
 using namespace boa;
@@ -221,7 +223,15 @@ struct boa_model {
     TrainState* tr = nullptr;
     std::vector<uint32_t> last_status;   // per-stream flags of the last compress / decompress call
     uint64_t prof_steps[2][2] = {};         // [phase][timed, all] steps of the step loops
+    // Held for the whole of every call that reads or writes the model's
+    // workspace, tuning, profiling counters or tensor-map cache: calls on
+    // one model from several host threads run one after another.
+    // Recursive because container calls go through boa_compress /
+    // boa_decompress.
+    mutable std::recursive_mutex mu;
 };
+
+#define MODEL_LOCK(m) std::lock_guard<std::recursive_mutex> model_lock_((m)->mu)
 
 static uint64_t fnv1a64_update(uint64_t h, const uint8_t* p, size_t n) {
     for (size_t i = 0; i < n; i++) {
@@ -293,12 +303,21 @@ extern "C" size_t boa_max_compressed_size(size_t len) {
 
 extern "C" const char* boa_last_error(void) { return g_err.c_str(); }
 
-extern "C" uint64_t boa_model_fingerprint(const boa_model* m) { return m ? m->fingerprint : 0; }
+extern "C" uint64_t boa_model_fingerprint(const boa_model* m) {
+    if (!m) return 0;
+    MODEL_LOCK(m);                  // a training step replaces it
+    return m->fingerprint;
+}
 
-extern "C" uint64_t boa_last_launch_count(const boa_model* m) { return m ? m->launches : 0; }
+extern "C" uint64_t boa_last_launch_count(const boa_model* m) {
+    if (!m) return 0;
+    MODEL_LOCK(m);
+    return m->launches;
+}
 
 extern "C" boa_status boa_last_stream_status(const boa_model* m, size_t n, uint32_t* status) {
     if (!m || (n && !status)) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     if (n > m->last_status.size()) return fail(BOA_ERR_ARG, "the last call had %zu streams", m->last_status.size());
     if (n) memcpy(status, m->last_status.data(), n * 4);
     return BOA_OK;
@@ -659,6 +678,41 @@ static void launch_k(boa_model* m, void (*kern)(P...), dim3 grid, dim3 block, si
     cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
 }
 
+// Opt-in to more than 48 KB of dynamic shared memory for one kernel.  The
+// attribute belongs to a device's context, so it is set once per (kernel,
+// device ordinal), with that device current (every caller runs after
+// cudaSetDevice(m->device)); a failure is reported, not ignored.
+struct SmemOptIn {
+    std::atomic<uint64_t> done[4] = {};     // bit per device ordinal 0..255
+    std::mutex mu;
+};
+
+// bytes < 0: the most the device allows this kernel beside its static
+// shared memory.
+template <typename Kern>
+static boa_status smem_opt_in(SmemOptIn& o, Kern kern, int bytes, int dev, const char* what) {
+    if (dev < 0 || dev >= 256) return fail(BOA_ERR_CUDA, "device ordinal %d out of range", dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    std::atomic<uint64_t>& word = o.done[dev >> 6];
+    if (word.load(std::memory_order_acquire) & bit) return BOA_OK;
+    std::lock_guard<std::mutex> lock(o.mu);
+    if (word.load(std::memory_order_acquire) & bit) return BOA_OK;
+    cudaError_t e = cudaSuccess;
+    if (bytes < 0) {
+        cudaFuncAttributes fa{};
+        int optin = 0;
+        e = cudaFuncGetAttributes(&fa, kern);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        bytes = optin - (int)fa.sharedSizeBytes;
+    }
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess)
+        return fail(BOA_ERR_CUDA, "%s: dynamic shared memory opt-in (%d bytes) on device %d failed: %s", what, bytes,
+                    dev, cudaGetErrorString(e));
+    word.fetch_or(bit, std::memory_order_acq_rel);
+    return BOA_OK;
+}
+
 template <int EPI>
 static boa_status gemm(boa_model* m, int cls, const float* A, const float* Wt, const float* bias, float* C, long long M,
                        int N, int K) {
@@ -756,34 +810,31 @@ static int tc_splits(int N, int K, int k_elems) {
 
 
 template <int BN, int EPI, int KIND, bool DEEP>
-static void launch_tc_cfg(boa_model* m, dim3 grid, int splits, int chunks, const CUtensorMap& ta,
-                          const CUtensorMap& tb, const float* bias, float* C, __nv_bfloat16* outb, long long M, int N,
-                          int K, const float* rs, const float* cs) {
+static boa_status launch_tc_cfg(boa_model* m, dim3 grid, int splits, int chunks, const CUtensorMap& ta,
+                                const CUtensorMap& tb, const float* bias, float* C, __nv_bfloat16* outb, long long M,
+                                int N, int K, const float* rs, const float* cs) {
     using L = TcSmem<BN, DEEP>;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L::kBytes);
-    });
+    static SmemOptIn optin;
+    TRY((smem_opt_in(optin, k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, (int)L::kBytes, m->device, "tensor-core gemm")));
     launch_k(m, k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, grid, kTcThreads, L::kBytes, splits, ta, tb, bias, C, outb,
              (int)M, N, K, m->err.p, rs, cs, chunks);
+    return BOA_OK;
 }
 
 // Grids smaller than the SM count take the deep-pipeline variant.  Split K
 // runs across a cluster on small grids and in one CTA's TMEM on grids that
 // fill the GPU (the same additions in the same order; see launch_t3).
 template <int BN, int EPI, int KIND>
-static void launch_tc(boa_model* m, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, float* C,
-                      __nv_bfloat16* outb, long long M, int N, int K, const float* rs, const float* cs) {
+static boa_status launch_tc(boa_model* m, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, float* C,
+                            __nv_bfloat16* outb, long long M, int N, int K, const float* rs, const float* cs) {
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
     const int split = tc_splits(N, K, KIND == kKindE4M3 ? 128 : kTcBK);
     const bool in_cta = (long long)grid.x * grid.y >= m->num_sms;
     const int chunks = in_cta && split * TcSmem<BN>::kTmemCols <= 512 ? split : 1;
     const int peers = split / chunks;
     if ((long long)grid.x * grid.y * peers < m->num_sms)
-        launch_tc_cfg<BN, EPI, KIND, true>(m, grid, peers, chunks, ta, tb, bias, C, outb, M, N, K, rs, cs);
-    else
-        launch_tc_cfg<BN, EPI, KIND, false>(m, grid, peers, chunks, ta, tb, bias, C, outb, M, N, K, rs, cs);
+        return launch_tc_cfg<BN, EPI, KIND, true>(m, grid, peers, chunks, ta, tb, bias, C, outb, M, N, K, rs, cs);
+    return launch_tc_cfg<BN, EPI, KIND, false>(m, grid, peers, chunks, ta, tb, bias, C, outb, M, N, K, rs, cs);
 }
 
 template <int EPI>
@@ -799,10 +850,10 @@ static boa_status gemm_tc(boa_model* m, int cls, const __nv_bfloat16* A, const _
     TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, 2, &ta));
     TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 2, &tb));
     switch (BN) {
-        case 48: launch_tc<48, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
-        case 64: launch_tc<64, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
-        case 128: launch_tc<128, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
-        default: launch_tc<256, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr); break;
+        case 48: TRY((launch_tc<48, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr))); break;
+        case 64: TRY((launch_tc<64, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr))); break;
+        case 128: TRY((launch_tc<128, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr))); break;
+        default: TRY((launch_tc<256, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr))); break;
     }
     return check_launch(m, "gemm_tc");
 }
@@ -829,10 +880,10 @@ static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_
     TRY(tmap_2d(m, m->v.a8, (uint64_t)M, (uint64_t)Kp, kTcBM, 1, &ta));
     TRY(tmap_2d(m, W, (uint64_t)N, (uint64_t)Kp, (uint32_t)BN, 1, &tb));
     switch (BN) {
-        case 48: launch_tc<48, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
-        case 64: launch_tc<64, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
-        case 128: launch_tc<128, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
-        default: launch_tc<256, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale); break;
+        case 48: TRY((launch_tc<48, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale))); break;
+        case 64: TRY((launch_tc<64, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale))); break;
+        case 128: TRY((launch_tc<128, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale))); break;
+        default: TRY((launch_tc<256, EPI, kKindE4M3>(m, ta, tb, bias, C, nullptr, M, N, Kp, m->v.a8s, wscale))); break;
     }
     return check_launch(m, "gemm_f8");
 }
@@ -858,22 +909,20 @@ static_assert(t3_tmem_fits<48, false>() && t3_tmem_fits<48, true>() && t3_tmem_f
               "3xTF32 CTAs sharing an SM would need more than 512 TMEM columns");
 
 template <int BN, int EPI, bool DEEP>
-static void launch_t3_cfg(boa_model* m, dim3 grid, int splits, int chunks, const CUtensorMap& ta,
-                          const CUtensorMap& th, const CUtensorMap& tl, const float* bias, float* C, long long M,
-                          int N, int K) {
+static boa_status launch_t3_cfg(boa_model* m, dim3 grid, int splits, int chunks, const CUtensorMap& ta,
+                                const CUtensorMap& th, const CUtensorMap& tl, const float* bias, float* C,
+                                long long M, int N, int K) {
     using L = T3Smem<BN, DEEP>;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(k_gemm_tc_tf32x3<BN, EPI, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L::kBytes);
-    });
+    static SmemOptIn optin;
+    TRY((smem_opt_in(optin, k_gemm_tc_tf32x3<BN, EPI, DEEP>, (int)L::kBytes, m->device, "3xTF32 gemm")));
     launch_k(m, k_gemm_tc_tf32x3<BN, EPI, DEEP>, grid, kT3Threads, L::kBytes, splits, ta, th, tl, bias, C, (int)M,
              N, K, m->err.p, chunks);
+    return BOA_OK;
 }
 
 template <int BN, int EPI>
-static void launch_t3(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th, const CUtensorMap& tl,
-                      const float* bias, float* C, long long M, int N, int K) {
+static boa_status launch_t3(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th, const CUtensorMap& tl,
+                            const float* bias, float* C, long long M, int N, int K) {
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
     const int split = tc_splits(N, K, kT3BK);
     const bool in_cta = (long long)grid.x * grid.y >= m->num_sms;
@@ -885,9 +934,8 @@ static void launch_t3(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th
                            ? split : 1;
     const int peers = split / chunks;
     if ((long long)grid.x * grid.y * peers < m->num_sms)
-        launch_t3_cfg<BN, EPI, true>(m, grid, peers, chunks, ta, th, tl, bias, C, M, N, K);
-    else
-        launch_t3_cfg<BN, EPI, false>(m, grid, peers, chunks, ta, th, tl, bias, C, M, N, K);
+        return launch_t3_cfg<BN, EPI, true>(m, grid, peers, chunks, ta, th, tl, bias, C, M, N, K);
+    return launch_t3_cfg<BN, EPI, false>(m, grid, peers, chunks, ta, th, tl, bias, C, M, N, K);
 }
 
 // FP32-accurate tensor-core GEMM (3xTF32); A is FP32, W pre-split.
@@ -905,10 +953,10 @@ static boa_status gemm_t3(boa_model* m, int cls, const float* A, const float* Wh
     TRY(tmap_2d(m, Whi, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 4, &th));
     TRY(tmap_2d(m, Wlo, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 4, &tl));
     switch (BN) {
-        case 48: launch_t3<48, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
-        case 64: launch_t3<64, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
-        case 128: launch_t3<128, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
-        default: launch_t3<256, EPI>(m, ta, th, tl, bias, C, M, N, K); break;
+        case 48: TRY((launch_t3<48, EPI>(m, ta, th, tl, bias, C, M, N, K))); break;
+        case 64: TRY((launch_t3<64, EPI>(m, ta, th, tl, bias, C, M, N, K))); break;
+        case 128: TRY((launch_t3<128, EPI>(m, ta, th, tl, bias, C, M, N, K))); break;
+        default: TRY((launch_t3<256, EPI>(m, ta, th, tl, bias, C, M, N, K))); break;
     }
     return check_launch(m, "gemm_t3");
 }
@@ -998,21 +1046,9 @@ static boa_status launch_step_bulk(boa_model* m, const DevLayer& L, float* hs, _
     int cps = 1, stages = 2;
     step_bulk_shape(m->E, m->N, m->r, cps, stages);
     const size_t smem = (size_t)stages * 4 * step_stage_floats(m->N, RR, m->E);
-    // opt in to the largest dynamic shared memory this kernel can have
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        cudaFuncAttributes fa{};
-        int dev = 0, optin = 0;
-        attr_err = cudaFuncGetAttributes(&fa, k_scan_step_bulk<16, RR>);
-        if (attr_err == cudaSuccess) attr_err = cudaGetDevice(&dev);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(k_scan_step_bulk<16, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            optin - (int)fa.sharedSizeBytes);
-    });
-    if (attr_err != cudaSuccess) return fail(BOA_ERR_CUDA, "decode scan set-up: %s", cudaGetErrorString(attr_err));
+    // opt in (once per device) to the largest dynamic shared memory this kernel can have
+    static SmemOptIn optin;
+    TRY((smem_opt_in(optin, k_scan_step_bulk<16, RR>, -1, m->device, "decode scan")));
     const int grid = (int)std::min<long long>(S, (long long)m->num_sms * cps);
     launch_k(m, k_scan_step_bulk<16, RR>, dim3((unsigned)grid), dim3((unsigned)(m->E / 2)), smem, 1, m->v.u, m->v.xz,
              m->v.dbc, L.dt_w, L.dt_b, L.A2, L.D, hs, m->v.yg, ygb, m->E, S, stages, m->err.p);
@@ -1597,6 +1633,7 @@ static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, c
 extern "C" boa_status boa_compress_device(boa_model* m, size_t n, const uint8_t* d_in, const uint64_t* in_off,
                                           uint8_t* d_out, const uint64_t* out_off, uint64_t* out_sizes) {
     if (!m || (n && (!d_in || !in_off || !d_out || !out_off || !out_sizes))) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     CU(cudaSetDevice(m->device));
     return compress_impl(m, n, d_in, in_off, d_out, out_off, out_sizes);
 }
@@ -1605,6 +1642,7 @@ extern "C" boa_status boa_decompress_device(boa_model* m, size_t n, const uint8_
                                             const uint64_t* in_sizes, const uint64_t* lens, uint8_t* d_out,
                                             const uint64_t* out_off) {
     if (!m || (n && (!d_in || !in_off || !lens || !d_out || !out_off))) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     CU(cudaSetDevice(m->device));
     return decompress_impl(m, n, d_in, in_off, in_sizes, lens, d_out, out_off);
 }
@@ -1630,6 +1668,7 @@ static boa_status fetch_compressed(boa_model* m, size_t n, const uint64_t* sizes
 extern "C" boa_status boa_compress(boa_model* m, size_t n, const uint8_t* const* streams, const size_t* lens,
                                    uint8_t* const* out, const size_t* out_caps, size_t* out_sizes) {
     if (!m || (n && (!streams || !lens || !out || !out_caps || !out_sizes))) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     if (n == 0) return BOA_OK;
     CU(cudaSetDevice(m->device));
     std::vector<uint64_t> in_off(n + 1), out_off(n + 1), sizes(n);
@@ -1661,6 +1700,7 @@ extern "C" boa_status boa_compress(boa_model* m, size_t n, const uint8_t* const*
 extern "C" boa_status boa_decompress(boa_model* m, size_t n, const uint8_t* const* bitstreams, const size_t* sizes,
                                      const size_t* lens, uint8_t* const* out) {
     if (!m || (n && (!bitstreams || !sizes || !lens || !out))) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     if (n == 0) return BOA_OK;
     CU(cudaSetDevice(m->device));
     std::vector<uint64_t> in_off(n + 1), out_off(n + 1), l64(n);
@@ -1691,6 +1731,7 @@ extern "C" boa_status boa_decompress(boa_model* m, size_t n, const uint8_t* cons
 
 extern "C" boa_status boa_profile_enable(boa_model* m, int on, int stride) {
     if (!m) return fail(BOA_ERR_ARG, "null model");
+    MODEL_LOCK(m);
     m->prof_on = on != 0;
     m->prof_stride = stride > 0 ? stride : 1;
     return BOA_OK;
@@ -1698,6 +1739,7 @@ extern "C" boa_status boa_profile_enable(boa_model* m, int on, int stride) {
 
 extern "C" boa_status boa_profile_reset(boa_model* m) {
     if (!m) return fail(BOA_ERR_ARG, "null model");
+    MODEL_LOCK(m);
     for (int ph = 0; ph < 2; ph++)
         for (int i = 0; i < BOA_KC_COUNT; i++) {
             m->prof_launches[ph][i] = 0;
@@ -1709,6 +1751,7 @@ extern "C" boa_status boa_profile_reset(boa_model* m) {
 
 extern "C" boa_status boa_profile_steps(const boa_model* m, int phase, uint64_t* timed, uint64_t* total) {
     if (!m || phase < 0 || phase > 1) return fail(BOA_ERR_ARG, "bad argument");
+    MODEL_LOCK(m);
     if (timed) *timed = m->prof_steps[phase][0];
     if (total) *total = m->prof_steps[phase][1];
     return BOA_OK;
@@ -1717,11 +1760,154 @@ extern "C" boa_status boa_profile_steps(const boa_model* m, int phase, uint64_t*
 extern "C" boa_status boa_profile_read(const boa_model* m, int phase, int cls, uint64_t* launches,
                                        double* total_ms, double* flops, double* bytes) {
     if (!m || cls < 0 || cls >= BOA_KC_COUNT || phase < 0 || phase > 1) return fail(BOA_ERR_ARG, "bad argument");
+    MODEL_LOCK(m);
     if (launches) *launches = m->prof_launches[phase][cls];
     if (total_ms) *total_ms = m->prof_ms[phase][cls];
     if (flops) *flops = m->prof_flops[phase][cls];
     if (bytes) *bytes = m->prof_bytes[phase][cls];
     return BOA_OK;
+}
+
+// ------------------------------------------------------------ microbenchmarks
+
+extern "C" boa_status boa_microbench(int device, int test, int kind, int M, int N, int flags, double* rate,
+                                     double* cycles_per_op) {
+    if (!rate) return fail(BOA_ERR_ARG, "null argument");
+    CU(cudaSetDevice(device));
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DevBuf<float> out, buf;
+    DevBuf<unsigned long long> cyc;
+    DevBuf<int> err;
+    boa_status s = BOA_OK;
+    auto body = [&]() -> boa_status {
+        CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+        float ms = 0.f;
+        if (test == BOA_MB_EX2 || test == BOA_MB_FFMA || test == BOA_MB_FFMA2) {
+            const int blocks = sms * 8, threads = 256, iters = 4096;
+            TRY(out.ensure((size_t)blocks * threads));
+            auto run = [&]() {
+                if (test == BOA_MB_EX2) k_mb_ex2<<<blocks, threads, 0, st>>>(iters, out.p);
+                else if (test == BOA_MB_FFMA) k_mb_ffma<<<blocks, threads, 0, st>>>(iters, out.p);
+                else k_mb_ffma2<<<blocks, threads, 0, st>>>(iters, out.p);
+            };
+            run();                                    // warm-up
+            CU(cudaEventRecord(e0, st));
+            run();
+            CU(cudaEventRecord(e1, st));
+            CU(cudaEventSynchronize(e1));
+            CU(cudaGetLastError());
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            const double ops = (double)blocks * threads * iters * 8;
+            // results per second (ex2) or FLOP per second (2 per FMA, 4 per packed FMA)
+            *rate = test == BOA_MB_EX2 ? ops / (ms * 1e-3) : ops * (test == BOA_MB_FFMA2 ? 4.0 : 2.0) / (ms * 1e-3);
+            if (cycles_per_op) {
+                int khz = 0;
+                CU(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device));
+                // warp instructions per SM per cycle at the nominal clock
+                *cycles_per_op = (ops / 32.0) / ((double)sms * ms * 1e-3 * khz * 1e3);
+            }
+            return BOA_OK;
+        }
+        if (test == BOA_MB_L2) {
+            const size_t bytes = (size_t)32 << 20;
+            const int passes = 20, blocks = sms * 4, threads = 512;
+            TRY(buf.ensure(bytes / 4));
+            TRY(out.ensure((size_t)blocks * threads));
+            CU(cudaMemsetAsync(buf.p, 0, bytes, st));
+            k_mb_l2<<<blocks, threads, 0, st>>>(reinterpret_cast<const float4*>(buf.p), bytes / 16, 1, out.p);
+            CU(cudaEventRecord(e0, st));
+            k_mb_l2<<<blocks, threads, 0, st>>>(reinterpret_cast<const float4*>(buf.p), bytes / 16, passes, out.p);
+            CU(cudaEventRecord(e1, st));
+            CU(cudaEventSynchronize(e1));
+            CU(cudaGetLastError());
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            *rate = (double)bytes * passes / (ms * 1e-3);
+            if (cycles_per_op) *cycles_per_op = 0.0;
+            return BOA_OK;
+        }
+        if (test == BOA_MB_MMA) {
+            const bool m_ok = M == 128 || M == 64;
+            const bool n_ok = N >= (M == 64 ? 8 : 16) && N <= 256 && N % (M == 64 ? 8 : 16) == 0;
+            const int modes = ((flags & kMbFlagFastIssue) ? 1 : 0) + ((flags & kMbFlagStages) ? 1 : 0) +
+                              ((flags & kMbFlagStagesWarp) ? 1 : 0);
+            if (kind < 0 || kind > 2 || !m_ok || !n_ok || (flags & ~31) || modes > 1 || (modes && (flags & 2)) ||
+                ((flags & (kMbFlagStages | kMbFlagStagesWarp)) && (flags & kMbFlagATmem)) ||
+                ((flags & kMbFlagATmem) && (kind != 0 || M != 128)) || ((flags & kMbFlagTwoAcc) && N > 128))
+                return fail(BOA_ERR_ARG, "unsupported MMA microbenchmark shape (kind %d, M %d, N %d, flags %d)", kind,
+                            M, N, flags);
+            const bool fast = (flags & kMbFlagFastIssue) != 0;
+            const int reps = 2048;
+            TRY(cyc.ensure((size_t)sms));
+            TRY(err.ensure(1));
+            CU(cudaMemsetAsync(err.p, 0, 4, st));
+            double instr = 4.0 * reps;
+            const bool staged = (flags & (kMbFlagStages | kMbFlagStagesWarp)) != 0;
+            if (staged) {
+                const bool w = (flags & kMbFlagStagesWarp) != 0;
+                void (*kern)(int, int, int, unsigned long long*, int*) =
+                    kind == 0 ? (w ? k_mb_mma_stages<0, true> : k_mb_mma_stages<0, false>)
+                    : kind == 1 ? (w ? k_mb_mma_stages<1, true> : k_mb_mma_stages<1, false>)
+                                : (w ? k_mb_mma_stages<2, true> : k_mb_mma_stages<2, false>);
+                static SmemOptIn opt_st[6];
+                TRY(smem_opt_in(opt_st[2 * kind + (w ? 1 : 0)], kern, kMbStagesSmemBytes, device,
+                                "MMA microbenchmark"));
+                kern<<<sms, 128, kMbStagesSmemBytes, st>>>(M, N, 4, cyc.p, err.p);             // warm-up
+                CU(cudaEventRecord(e0, st));
+                kern<<<sms, 128, kMbStagesSmemBytes, st>>>(M, N, reps, cyc.p, err.p);
+                CU(cudaEventRecord(e1, st));
+            } else if (!fast) {
+                static SmemOptIn optin;
+                TRY(smem_opt_in(optin, k_mb_mma, kMbSmemBytes, device, "MMA microbenchmark"));
+                k_mb_mma<<<sms, 128, kMbSmemBytes, st>>>(kind, M, N, flags, 16, cyc.p, err.p);   // warm-up
+                CU(cudaEventRecord(e0, st));
+                k_mb_mma<<<sms, 128, kMbSmemBytes, st>>>(kind, M, N, flags, reps, cyc.p, err.p);
+                CU(cudaEventRecord(e1, st));
+            } else {
+                // straight-line issue: 16 instructions per iteration plus the first
+                const int freps = reps / 4;
+                instr = 16.0 * freps + 1.0;
+                void (*kern)(int, int, int, unsigned long long*, int*) =
+                    kind == 0 ? ((flags & kMbFlagATmem) ? k_mb_mma_fast<0, true> : k_mb_mma_fast<0, false>)
+                              : kind == 1 ? k_mb_mma_fast<1, false> : k_mb_mma_fast<2, false>;
+                static SmemOptIn opt_fast[4];
+                const int slot = kind == 0 ? ((flags & kMbFlagATmem) ? 1 : 0) : kind + 1;
+                TRY(smem_opt_in(opt_fast[slot], kern, kMbSmemBytes, device, "MMA microbenchmark"));
+                kern<<<sms, 128, kMbSmemBytes, st>>>(M, N, 4, cyc.p, err.p);                 // warm-up
+                CU(cudaEventRecord(e0, st));
+                kern<<<sms, 128, kMbSmemBytes, st>>>(M, N, freps, cyc.p, err.p);
+                CU(cudaEventRecord(e1, st));
+            }
+            CU(cudaEventSynchronize(e1));
+            CU(cudaGetLastError());
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            int h_err = 0;
+            CU(cudaMemcpy(&h_err, err.p, 4, cudaMemcpyDeviceToHost));
+            if (h_err) return fail(BOA_ERR_CUDA, "MMA microbenchmark: a wait timed out");
+            std::vector<unsigned long long> h((size_t)sms);
+            CU(cudaMemcpy(h.data(), cyc.p, (size_t)sms * 8, cudaMemcpyDeviceToHost));
+            const int kelems = kind == 0 ? 8 : kind == 1 ? 16 : 32;     // 32 bytes of K per instruction
+            *rate = (double)sms * instr * 2.0 * M * N * kelems / (ms * 1e-3);
+            if (cycles_per_op) {
+                double c = 0.0;
+                for (auto v : h) c += (double)v;
+                *cycles_per_op = c / sms / instr;
+            }
+            return BOA_OK;
+        }
+        return fail(BOA_ERR_ARG, "unknown microbenchmark %d", test);
+    };
+    s = body();
+    if (st) cudaStreamSynchronize(st);
+    out.release(); buf.release(); cyc.release(); err.release();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return s;
 }
 
 // ------------------------------------------------------------ training scan
@@ -1760,6 +1946,7 @@ extern "C" boa_status boa_scan_train_bwd(size_t Bsz, size_t T, size_t E, size_t 
 
 extern "C" boa_status boa_set_tuning(boa_model* m, const boa_tuning* t) {
     if (!m || !t) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     if (t->max_rows < 1 || t->max_rows > (1u << 24)) return fail(BOA_ERR_ARG, "max_rows %zu out of range", t->max_rows);
     if (t->scan_variant < 0 || t->scan_variant > 3) return fail(BOA_ERR_ARG, "scan_variant %d out of range", t->scan_variant);
     if (t->decode_lanes < 0 || t->decode_lanes > 16) return fail(BOA_ERR_ARG, "decode_lanes %d out of range", t->decode_lanes);
@@ -1771,12 +1958,14 @@ extern "C" boa_status boa_set_tuning(boa_model* m, const boa_tuning* t) {
 
 extern "C" boa_status boa_get_tuning(const boa_model* m, boa_tuning* out) {
     if (!m || !out) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     *out = boa_tuning{m->max_rows, m->scan_variant, m->decode_lanes, 0.0, 0.0};
     return BOA_OK;
 }
 
 extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream_len, boa_tuning* out) {
     if (!m || n_streams == 0 || stream_len < 2) return fail(BOA_ERR_ARG, "bad argument");
+    MODEL_LOCK(m);
     CU(cudaSetDevice(m->device));
     const size_t len = std::min<size_t>(stream_len, 512);   // a short sample of every stream
     const size_t n = std::min(n_streams, m->max_slots);
@@ -1963,6 +2152,7 @@ extern "C" boa_status boa_debug_quantise(size_t n_rows, const float* p, uint32_t
 
 extern "C" boa_status boa_debug_logprobs(boa_model* m, const uint8_t* stream, size_t len, float* out) {
     if (!m || (len && (!stream || !out))) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     if (len < 2) return BOA_OK;
     CU(cudaSetDevice(m->device));
     const size_t T = len - 1;
@@ -2009,6 +2199,7 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
         return fail(BOA_ERR_ARG, "epilogue needs a bias");
     if ((epilogue == kEpiResid || epilogue == kEpiBiasResid) && !C_in) return fail(BOA_ERR_ARG, "epilogue needs C_in");
     if (precision < BOA_PREC_FP32 || precision > BOA_PREC_FP8) return fail(BOA_ERR_ARG, "bad precision");
+    CU(cudaSetDevice(0));
     boa_model t;
     t.precision = precision;
     cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, 0);
@@ -2133,12 +2324,14 @@ extern "C" boa_status boa_debug_gemm(int precision, size_t M, size_t N, size_t K
 
 extern "C" boa_status boa_debug_enable_cdf_trace(boa_model* m, int on) {
     if (!m) return fail(BOA_ERR_ARG, "null model");
+    MODEL_LOCK(m);
     m->trace_on = on != 0;
     return BOA_OK;
 }
 
 extern "C" boa_status boa_debug_read_cdf_trace(boa_model* m, uint64_t* out, size_t n) {
     if (!m || (n && !out)) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     if (n > m->trace_n) return fail(BOA_ERR_ARG, "trace holds %zu entries, asked for %zu", m->trace_n, n);
     if (n == 0) return BOA_OK;
     CU(cudaSetDevice(m->device));
@@ -2201,10 +2394,17 @@ static unsigned char* g_static_ptr[256];   // per device ordinal, set once
 
 // Once per device, with that device current: the device address of the
 // scratch array (host code cannot use the symbol itself as an address).
-static boa_status static_scratch(unsigned char** out) {
-    int dev = -1;
+// The stream must belong to the current device, whose array the call uses.
+// The address is kept for the life of the process, so the entry point is
+// not for use after cudaDeviceReset on that device.
+static boa_status static_scratch(cudaStream_t st, unsigned char** out) {
+    int dev = -1, sdev = -1;
     CU(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) return fail(BOA_ERR_CUDA, "device ordinal %d out of range", dev);
+    CU(cudaStreamGetDevice(st, &sdev));
+    if (sdev != dev)
+        return fail(BOA_ERR_ARG, "boa_decode_cdfs_static: the stream belongs to device %d, the current device is %d",
+                    sdev, dev);
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (!g_static_ptr[dev]) {
         void* p = nullptr;
@@ -2226,9 +2426,9 @@ extern "C" boa_status boa_decode_cdfs_static(size_t n_seq, const size_t* n_syms,
     if (!n_syms || !d_cdfs || !d_in || !in_sizes || !d_syms) return fail(BOA_ERR_ARG, "null argument");
     for (size_t i = 0; i < n_seq; i++)
         if (in_sizes[i] > in_stride) return fail(BOA_ERR_ARG, "in_sizes[%zu] > in_stride", i);
-    unsigned char* base = nullptr;
-    TRY(static_scratch(&base));
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    unsigned char* base = nullptr;
+    TRY(static_scratch(st, &base));
     uint64_t* counts = reinterpret_cast<uint64_t*>(base + kStaticCountsOff);
     uint64_t* sym_off = reinterpret_cast<uint64_t*>(base + kStaticSymOffOff);
     uint64_t* sizes = reinterpret_cast<uint64_t*>(base + kStaticSizesOff);
@@ -2345,6 +2545,7 @@ extern "C" size_t boa_pack_bound(size_t len, size_t chunk_len) {
 extern "C" boa_status boa_pack(boa_model* m, const uint8_t* data, size_t len, size_t chunk_len, uint8_t* out,
                                size_t cap, size_t* out_size) {
     if (!m || (len && !data) || !out || !out_size || chunk_len == 0) return fail(BOA_ERR_ARG, "bad argument");
+    MODEL_LOCK(m);
     if (cap < boa_pack_bound(len, chunk_len)) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "capacity below boa_pack_bound");
     const size_t n = (len + chunk_len - 1) / chunk_len;
     std::vector<const uint8_t*> ptrs(n);
@@ -2389,6 +2590,7 @@ extern "C" boa_status boa_unpack_info(const uint8_t* c, size_t size, uint64_t* t
 extern "C" boa_status boa_unpack(boa_model* m, const uint8_t* c, size_t size, uint8_t* out, size_t cap,
                                  size_t* out_len) {
     if (!m || !out_len || (cap && !out)) return fail(BOA_ERR_ARG, "bad argument");
+    MODEL_LOCK(m);
     ContainerView v;
     TRY(parse_container(m, c, size, &v));
     if (cap < v.total) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "output needs %llu bytes", (unsigned long long)v.total);
@@ -2412,6 +2614,7 @@ extern "C" boa_status boa_unpack(boa_model* m, const uint8_t* c, size_t size, ui
 extern "C" boa_status boa_unpack_shards(boa_model* m, const uint8_t* data, size_t size, uint8_t* out, size_t cap,
                                         size_t* out_len) {
     if (!m || !out_len || (size && !data) || (cap && !out)) return fail(BOA_ERR_ARG, "bad argument");
+    MODEL_LOCK(m);
     if (!out) {                                  // size query: validate and sum the lengths
         size_t at = 0, total = 0;
         while (at < size) {
@@ -2484,6 +2687,7 @@ struct boa_stream {
 // One set (device buffer b, bytes long) into a container appended to shards.
 static boa_status stream_compress_set(boa_stream* s, int b, size_t bytes, std::vector<uint8_t>& shard) {
     boa_model* m = s->m;
+    MODEL_LOCK(m);
     const size_t n = (bytes + s->chunk - 1) / s->chunk;
     std::vector<uint64_t> in_off(n + 1), out_off(n + 1), sizes(n);
     in_off[0] = out_off[0] = 0;
@@ -2977,6 +3181,8 @@ static boa_status read_loss(boa_model* m, size_t rows, float* loss_out) {
 
 extern "C" boa_status boa_train_step(boa_model* m, const uint8_t* batch, size_t n_seq, size_t seqlen, float lr,
                                      float* loss_out) {
+    if (!m) return fail(BOA_ERR_ARG, "null model");
+    MODEL_LOCK(m);
     TRY(train_batch(m, batch, n_seq, seqlen));
     TrainState& t = *m->tr;
     t.step++;
@@ -3000,6 +3206,8 @@ extern "C" boa_status boa_train_step(boa_model* m, const uint8_t* batch, size_t 
 
 extern "C" boa_status boa_debug_train_grad(boa_model* m, const uint8_t* batch, size_t n_seq, size_t seqlen,
                                            float* grad_out, float* loss_out) {
+    if (!m) return fail(BOA_ERR_ARG, "null model");
+    MODEL_LOCK(m);
     TRY(train_batch(m, batch, n_seq, seqlen));
     TRY(read_loss(m, n_seq * (seqlen - 1), loss_out));
     if (grad_out) {
@@ -3013,6 +3221,7 @@ extern "C" size_t boa_model_param_count(const boa_model* m) { return m ? m->n_pa
 
 extern "C" boa_status boa_save_model(const boa_model* m, const char* path) {
     if (!m || !path) return fail(BOA_ERR_ARG, "null argument");
+    MODEL_LOCK(m);
     FILE* fp = fopen(path, "wb");
     if (!fp) return fail(BOA_ERR_IO, "cannot open %s for writing", path);
     bool ok = fwrite("BOAW", 1, 4, fp) == 4 && fwrite(m->header, 4, 9, fp) == 9 &&

@@ -5,8 +5,9 @@
 //   - thread 0 streams K-blocks of A and W into a ring of shared-memory
 //     stages with TMA (cp.async.bulk.tensor, 128-byte swizzle), signalling
 //     "full" mbarriers;
-//   - thread 32 issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction)
-//     into a TMEM accumulator and frees each stage with tcgen05.commit;
+//   - warp 1 walks the K blocks and one elected lane issues tcgen05.mma
+//     (M = 128, N = BN, K = 16 per instruction) into a TMEM accumulator and
+//     frees each stage with tcgen05.commit;
 //   - all four warps then read their 32 TMEM lanes (rows) with tcgen05.ld and
 //     apply the epilogue.
 // Every output element sees the same instruction sequence (same K order,
@@ -67,6 +68,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     while (!mbar_try(bar, parity))
         if (globaltimer() - t0 > kWaitNs) return false;
     return true;
+}
+
+// One lane of the (converged) warp: the MMA issuers below run their loop on
+// the whole warp, so the waits and descriptor arithmetic are warp-uniform
+// (the uniform datapath), and only the elected lane issues instructions.
+// Measured on B300: a stream of tcgen05.mma issued this way runs at the
+// tensor pipe's own rate (about max(46, N / 2) SM cycles per instruction for
+// M = 128 and 32 bytes of K, any operand kind), against about 72 cycles per
+// instruction when one thread computes every descriptor itself.
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred = 0;
+    asm volatile("{\n .reg .pred p;\n elect.sync _|p, 0xffffffff;\n selp.u32 %0, 1, 0, p;\n}\n" : "=r"(pred));
+    return pred != 0;
 }
 
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
@@ -499,31 +513,39 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             tma_load_2d(&tmB, &full[s], sa + L::kA, (kb0 + kb) * kElemK, n0);
             armed_last = kb;
         }
-    } else if (threadIdx.x == 32) {
-        // MMA issuer
+    } else if (warp == 1) {
+        // MMA issuer: the whole warp walks the K blocks, one lane issues
         constexpr uint32_t idesc = KIND == kKindE4M3 ? umma_idesc_e4m3(kTcBM, BN) : umma_idesc_bf16(kTcBM, BN);
+        const bool leader = elect_one();
+        // descriptors of stage 0's first 32 bytes of K; stage s and K step k
+        // add (s * kStage + 32 k) / 16 to the start-address field
+        const uint64_t da0 = umma_desc_sw128(smem_u32(smem));
+        const uint64_t db0 = umma_desc_sw128(smem_u32(smem + L::kA));
         bool ok = true;
-        for (int kb = 0; kb < nk && ok; kb++) {
+        for (int kb = 0; kb < nk; kb++) {
             const int s = kb % L::kStages;
-            if (!mbar_wait(&full[s], (kb / L::kStages) & 1)) { ok = false; break; }
+            ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (kb / L::kStages) & 1));
+            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_u32(smem + (size_t)s * L::kStage);
-            const uint32_t sb = sa + L::kA;
+            const uint64_t so = (uint64_t)((s * L::kStage) >> 4);
             const int kc = kb % nkc;                     // K block within its chunk
             const uint32_t d = tmem + (uint32_t)((kb / nkc) * L::kTmemCols);
+            if (leader) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) {   // 32 bytes of K per instruction: 16 BF16 or 32 E4M3
-                if (KIND == kKindE4M3)
-                    umma_e4m3(d, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
-                              (kc | k) != 0 ? 1u : 0u);
-                else
-                    umma_bf16(d, umma_desc_sw128(sa + 32 * k), umma_desc_sw128(sb + 32 * k), idesc,
-                              (kc | k) != 0 ? 1u : 0u);
+                for (int k = 0; k < 4; k++) {   // 32 bytes of K per instruction: 16 BF16 or 32 E4M3
+                    if (KIND == kKindE4M3)
+                        umma_e4m3(d, da0 + so + 2 * k, db0 + so + 2 * k, idesc, (kc | k) != 0 ? 1u : 0u);
+                    else
+                        umma_bf16(d, da0 + so + 2 * k, db0 + so + 2 * k, idesc, (kc | k) != 0 ? 1u : 0u);
+                }
+                umma_commit(&empty[s]);
             }
-            umma_commit(&empty[s]);
+            __syncwarp();
         }
-        if (!ok) atomicExch(&abort_flag, 1);
-        umma_commit(&done[0]);
+        if (leader) {
+            if (!ok) atomicExch(&abort_flag, 1);
+            umma_commit(&done[0]);
+        }
     }
 
     // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31
@@ -558,7 +580,8 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 // and four converter warps split each stage's rows into A_hi and A_lo in
 // TMEM (each thread its row, in its lane), where the MMAs read their A
 // operand.  TMEM holds the accumulator(s) in its first columns and the A
-// stages after them.  Warps: 0 TMA, 1 MMA, 2-5 converters then epilogue.
+// stages after them.  Warps: 0 TMA, 1 MMA (one elected lane issues), 2-5
+// converters then epilogue.
 
 constexpr int kT3Threads = 192;
 constexpr int kT3BK = 32;                  // 32 fp32 = 128 bytes = one swizzle atom row
@@ -689,30 +712,41 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             tma_load_2d(&tmBlo, &full[s], st + L::kA + L::kB, (kb0 + kb) * kT3BK, n0);
             armed_last = kb;
         }
-    } else if (threadIdx.x == 32) {
+    } else if (warp == 1) {
+        // MMA issuer: the whole warp walks the K blocks, one lane issues
         constexpr uint32_t idesc = umma_idesc_tf32(kTcBM, BN);
+        const bool leader = elect_one();
+        // B_hi descriptor of stage 0's first 32 bytes of K; stage s, B_lo and
+        // K step k add (s * kStage [+ kB] + 32 k) / 16 to the start address
+        const uint64_t dh0 = umma_desc_sw128(smem_u32(smem + L::kA));
         bool ok = true;
-        for (int kb = 0; kb < nk && ok; kb++) {
+        for (int kb = 0; kb < nk; kb++) {
             const int s = kb % L::kStages;
-            if (!mbar_wait(&conv[s], (kb / L::kStages) & 1)) { ok = false; break; }
+            ok = __all_sync(0xffffffffu, mbar_wait(&conv[s], (kb / L::kStages) & 1));
+            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t bhi = smem_u32(smem + (size_t)s * L::kStage + L::kA);
-            const uint32_t blo = bhi + L::kB;
+            const uint64_t dh = dh0 + (uint64_t)((s * L::kStage) >> 4);
+            const uint64_t dl = dh + (uint64_t)(L::kB >> 4);
             const uint32_t ahi = tmem + a_col0 + (uint32_t)(s * L::kACols);   // TMEM: A_hi | A_lo
             const uint32_t alo = ahi + kT3BK;
             const int kc = kb % nkc;                     // K block within its chunk
             const uint32_t d = tmem + (uint32_t)((kb / nkc) * L::kTmemCols);
+            if (leader) {
 #pragma unroll
-            for (int k = 0; k < kT3BK / 8; k++) {
-                const uint32_t o = 32 * k;               // 8 TF32 of K: 32 bytes of B, 8 TMEM columns of A
-                umma_tf32_ta(d, ahi + 8 * k, umma_desc_sw128(bhi + o), idesc, (kc | k) != 0 ? 1u : 0u);
-                umma_tf32_ta(d, ahi + 8 * k, umma_desc_sw128(blo + o), idesc, 1u);
-                umma_tf32_ta(d, alo + 8 * k, umma_desc_sw128(bhi + o), idesc, 1u);
+                for (int k = 0; k < kT3BK / 8; k++) {
+                    // 8 TF32 of K: 32 bytes of B (2 descriptor units), 8 TMEM columns of A
+                    umma_tf32_ta(d, ahi + 8 * k, dh + 2 * k, idesc, (kc | k) != 0 ? 1u : 0u);
+                    umma_tf32_ta(d, ahi + 8 * k, dl + 2 * k, idesc, 1u);
+                    umma_tf32_ta(d, alo + 8 * k, dh + 2 * k, idesc, 1u);
+                }
+                umma_commit(&empty[s]);
             }
-            umma_commit(&empty[s]);
+            __syncwarp();
         }
-        if (!ok) atomicExch(&abort_flag, 1);
-        umma_commit(&done[0]);
+        if (leader) {
+            if (!ok) atomicExch(&abort_flag, 1);
+            umma_commit(&done[0]);
+        }
     } else if (warp >= 2) {
         // converters: thread (quadrant q = warp % 4, lane) takes A row
         // 32 q + lane of each stage, splits it into hi and lo, and writes both
