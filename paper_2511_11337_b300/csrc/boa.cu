@@ -915,8 +915,8 @@ static boa_status launch_t3_cfg(boa_model* m, dim3 grid, int splits, int chunks,
     using L = T3Smem<BN, DEEP>;
     static SmemOptIn optin;
     TRY((smem_opt_in(optin, k_gemm_tc_tf32x3<BN, EPI, DEEP>, (int)L::kBytes, m->device, "3xTF32 gemm")));
-    launch_k(m, k_gemm_tc_tf32x3<BN, EPI, DEEP>, grid, kT3Threads, L::kBytes, splits, ta, th, tl, bias, C, (int)M,
-             N, K, m->err.p, chunks);
+    launch_k(m, k_gemm_tc_tf32x3<BN, EPI, DEEP>, grid, t3_threads(DEEP), L::kBytes, splits, ta, th, tl, bias, C,
+             (int)M, N, K, m->err.p, chunks);
     return BOA_OK;
 }
 

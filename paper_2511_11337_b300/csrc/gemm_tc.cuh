@@ -83,6 +83,12 @@ __device__ __forceinline__ bool elect_one() {
     return pred != 0;
 }
 
+// Bring a tensor map (a __grid_constant__ kernel parameter) into the TMA
+// unit's descriptor cache before its first use.
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
@@ -480,6 +486,8 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint32_t tmem_cols = (uint32_t)(L::kTmemCols * chunks);
 
     if (threadIdx.x == 0) {
+        tma_prefetch_map(&tmA);
+        tma_prefetch_map(&tmB);
         abort_flag = 0;
         for (int i = 0; i < L::kBars; i++) mbar_init(&bars[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -494,8 +502,16 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    // the set-up above overlaps the previous kernel; inputs are read below
+    // The set-up above overlaps the previous kernel.  B (the weights) is
+    // never written by the kernel that precedes a projection, so the first
+    // stages' B tiles are requested before waiting for it; A only after.
     pdl_launch_next();
+    const int pre = nk < L::kStages ? nk : L::kStages;
+    if (threadIdx.x == 0)
+        for (int kb = 0; kb < pre; kb++) {
+            mbar_expect_tx(&full[kb], L::kStage);
+            tma_load_2d(&tmB, &full[kb], smem + (size_t)kb * L::kStage + L::kA, (kb0 + kb) * kElemK, n0);
+        }
     pdl_wait_prev();
 
     int armed_last = -1;   // producer: last K-block whose loads were issued
@@ -503,14 +519,16 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         // TMA producer
         for (int kb = 0; kb < nk; kb++) {
             const int s = kb % L::kStages;
-            if (kb >= L::kStages && !mbar_wait(&empty[s], ((kb / L::kStages) - 1) & 1)) {
-                atomicExch(&abort_flag, 1);
-                break;
-            }
             uint8_t* sa = smem + (size_t)s * L::kStage;
-            mbar_expect_tx(&full[s], L::kStage);
+            if (kb >= pre) {
+                if (!mbar_wait(&empty[s], ((kb / L::kStages) - 1) & 1)) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                mbar_expect_tx(&full[s], L::kStage);
+                tma_load_2d(&tmB, &full[s], sa + L::kA, (kb0 + kb) * kElemK, n0);
+            }
             tma_load_2d(&tmA, &full[s], sa, (kb0 + kb) * kElemK, m0);
-            tma_load_2d(&tmB, &full[s], sa + L::kA, (kb0 + kb) * kElemK, n0);
             armed_last = kb;
         }
     } else if (warp == 1) {
@@ -522,14 +540,14 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint64_t da0 = umma_desc_sw128(smem_u32(smem));
         const uint64_t db0 = umma_desc_sw128(smem_u32(smem + L::kA));
         bool ok = true;
+        int kc = 0, chunk = 0;                           // K block within its TMEM chunk, chunk index
         for (int kb = 0; kb < nk; kb++) {
             const int s = kb % L::kStages;
             ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (kb / L::kStages) & 1));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t so = (uint64_t)((s * L::kStage) >> 4);
-            const int kc = kb % nkc;                     // K block within its chunk
-            const uint32_t d = tmem + (uint32_t)((kb / nkc) * L::kTmemCols);
+            const uint32_t d = tmem + (uint32_t)(chunk * L::kTmemCols);
             if (leader) {
 #pragma unroll
                 for (int k = 0; k < 4; k++) {   // 32 bytes of K per instruction: 16 BF16 or 32 E4M3
@@ -541,6 +559,10 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 umma_commit(&empty[s]);
             }
             __syncwarp();
+            if (++kc == nkc) {
+                kc = 0;
+                chunk++;
+            }
         }
         if (leader) {
             if (!ok) atomicExch(&abort_flag, 1);
@@ -581,9 +603,13 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 // TMEM (each thread its row, in its lane), where the MMAs read their A
 // operand.  TMEM holds the accumulator(s) in its first columns and the A
 // stages after them.  Warps: 0 TMA, 1 MMA (one elected lane issues), 2-5
-// converters then epilogue.
+// converters (with DEEP also 6-9: then 2-5 take the even K blocks and 6-9
+// the odd ones), then 2-5 run the epilogue.
 
-constexpr int kT3Threads = 192;
+// Warps: 0 TMA, 1 MMA, then 4 converter warps per converter set.  A CTA
+// alone on its SM (DEEP, decode-size grids) runs two sets so that two stages
+// are converted at once; two CTAs sharing an SM run one set each.
+__host__ __device__ constexpr int t3_threads(bool deep) { return deep ? 320 : 192; }
 constexpr int kT3BK = 32;                  // 32 fp32 = 128 bytes = one swizzle atom row
 
 __host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
@@ -648,7 +674,7 @@ struct T3Smem {
 };
 
 template <int BN, int EPI, bool DEEP = false>
-__global__ void __launch_bounds__(kT3Threads)
+__global__ void __launch_bounds__(t3_threads(DEEP))
 k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
                  const __grid_constant__ CUtensorMap tmBlo, const float* __restrict__ bias, float* __restrict__ Cm,
                  int M, int N, int K, int* __restrict__ err, int chunks) {
@@ -674,6 +700,9 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     const uint32_t tmem_cols = L::pow2_cols(a_col0 + (uint32_t)(L::kStages * L::kACols));
 
     if (threadIdx.x == 0) {
+        tma_prefetch_map(&tmA);
+        tma_prefetch_map(&tmBhi);
+        tma_prefetch_map(&tmBlo);
         abort_flag = 0;
         for (int i = 0; i < L::kStages; i++) {
             mbar_init(&full[i], 1);
@@ -693,23 +722,36 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    // the set-up above overlaps the previous kernel; inputs are read below
+    // The set-up above overlaps the previous kernel.  B_hi / B_lo (the
+    // weights) are never written by the kernel that precedes a projection,
+    // so the first stages' B tiles are requested before waiting for it; A
+    // only after.
     pdl_launch_next();
+    const int pre = nk < L::kStages ? nk : L::kStages;
+    if (threadIdx.x == 0)
+        for (int kb = 0; kb < pre; kb++) {
+            uint8_t* st = smem + (size_t)kb * L::kStage;
+            mbar_expect_tx(&full[kb], L::kStage);
+            tma_load_2d(&tmBhi, &full[kb], st + L::kA, (kb0 + kb) * kT3BK, n0);
+            tma_load_2d(&tmBlo, &full[kb], st + L::kA + L::kB, (kb0 + kb) * kT3BK, n0);
+        }
     pdl_wait_prev();
 
     int armed_last = -1;
     if (threadIdx.x == 0) {
         for (int kb = 0; kb < nk; kb++) {
             const int s = kb % L::kStages;
-            if (kb >= L::kStages && !mbar_wait(&empty[s], ((kb / L::kStages) - 1) & 1)) {
-                atomicExch(&abort_flag, 1);
-                break;
-            }
             uint8_t* st = smem + (size_t)s * L::kStage;
-            mbar_expect_tx(&full[s], L::kStage);
+            if (kb >= pre) {
+                if (!mbar_wait(&empty[s], ((kb / L::kStages) - 1) & 1)) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                mbar_expect_tx(&full[s], L::kStage);
+                tma_load_2d(&tmBhi, &full[s], st + L::kA, (kb0 + kb) * kT3BK, n0);
+                tma_load_2d(&tmBlo, &full[s], st + L::kA + L::kB, (kb0 + kb) * kT3BK, n0);
+            }
             tma_load_2d(&tmA, &full[s], st, (kb0 + kb) * kT3BK, m0);
-            tma_load_2d(&tmBhi, &full[s], st + L::kA, (kb0 + kb) * kT3BK, n0);
-            tma_load_2d(&tmBlo, &full[s], st + L::kA + L::kB, (kb0 + kb) * kT3BK, n0);
             armed_last = kb;
         }
     } else if (warp == 1) {
@@ -720,6 +762,7 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         // K step k add (s * kStage [+ kB] + 32 k) / 16 to the start address
         const uint64_t dh0 = umma_desc_sw128(smem_u32(smem + L::kA));
         bool ok = true;
+        int kc = 0, chunk = 0;                           // K block within its TMEM chunk, chunk index
         for (int kb = 0; kb < nk; kb++) {
             const int s = kb % L::kStages;
             ok = __all_sync(0xffffffffu, mbar_wait(&conv[s], (kb / L::kStages) & 1));
@@ -729,8 +772,7 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             const uint64_t dl = dh + (uint64_t)(L::kB >> 4);
             const uint32_t ahi = tmem + a_col0 + (uint32_t)(s * L::kACols);   // TMEM: A_hi | A_lo
             const uint32_t alo = ahi + kT3BK;
-            const int kc = kb % nkc;                     // K block within its chunk
-            const uint32_t d = tmem + (uint32_t)((kb / nkc) * L::kTmemCols);
+            const uint32_t d = tmem + (uint32_t)(chunk * L::kTmemCols);
             if (leader) {
 #pragma unroll
                 for (int k = 0; k < kT3BK / 8; k++) {
@@ -742,6 +784,10 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 umma_commit(&empty[s]);
             }
             __syncwarp();
+            if (++kc == nkc) {
+                kc = 0;
+                chunk++;
+            }
         }
         if (leader) {
             if (!ok) atomicExch(&abort_flag, 1);
@@ -749,12 +795,15 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         }
     } else if (warp >= 2) {
         // converters: thread (quadrant q = warp % 4, lane) takes A row
-        // 32 q + lane of each stage, splits it into hi and lo, and writes both
-        // into its TMEM lane: A_hi in the stage's columns 0..31, A_lo in 32..63
+        // 32 q + lane of each of its stages (with two sets, warps 2-5 the
+        // even K blocks and 6-9 the odd ones), splits it into hi and lo, and
+        // writes both into its TMEM lane: A_hi in the stage's columns 0..31,
+        // A_lo in 32..63
+        constexpr int kSets = (t3_threads(DEEP) - 64) / 128;
         const int q = warp % 4;
         const int r = 32 * q + lane;
         const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + a_col0;
-        for (int kb = 0; kb < nk; kb++) {
+        for (int kb = (warp - 2) / 4; kb < nk; kb += kSets) {
             const int s = kb % L::kStages;
             if (!mbar_wait(&full[s], (kb / L::kStages) & 1)) {
                 atomicExch(&abort_flag, 1);
@@ -801,8 +850,8 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             mbar_wait(&full[kb % L::kStages], (kb / L::kStages) & 1);
         if (!finished) mbar_wait(&done[0], 0);
     }
-    tc_epilogue<BN, EPI>(warp >= 2, bad, &bad_flag, tmem, warp % 4, lane, m0, n0, M, N, bias, Cm, nullptr,
-                         reinterpret_cast<float*>(smem), nullptr, nullptr, chunks, L::kTmemCols);
+    tc_epilogue<BN, EPI>(warp >= 2 && warp < 6, bad, &bad_flag, tmem, warp % 4, lane, m0, n0, M, N, bias, Cm,
+                         nullptr, reinterpret_cast<float*>(smem), nullptr, nullptr, chunks, L::kTmemCols);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
