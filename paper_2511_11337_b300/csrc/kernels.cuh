@@ -201,10 +201,26 @@ k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ wt,
 // A2t = (A * log2 e) stored [N][E] and dtwt = W_dt stored [R][E] (channel
 // innermost, so the per-channel loads coalesce); exp(Delta A) = 2^(Delta A2).
 // A CTA covers 128 channels of G consecutive streams and loads the weights
-// once; the rows it visits (stream-major) are staged 32 at a time.  Six CTAs
-// per SM (80 registers): measured 3 % faster than five at compression sizes.
+// once (before waiting for the previous kernel: they are not its outputs).
+// Six CTAs per SM (80 registers).
+//
+// Chunks of more than one step (compression) stage the rows a CTA visits
+// (stream-major) through shared memory in batches of kScanRB rows: the
+// batch's u and z values of the CTA's channels and its [delta|B|C] rows,
+// double buffered with cp.async, so the next batch is in flight while the
+// current one is computed.  The per-channel arithmetic is the same sequence
+// of operations in every path (and in the decode-step kernels).
 constexpr int kScanThreads = 128;
-constexpr int kScanRowsSmem = 32;
+constexpr int kScanRowsSmem = 32;          // single-step path: up to 32 streams' [delta|B|C] rows
+constexpr int kScanRB = 8;                 // chunked path: rows per staged batch
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int NS, int R, int G>
 __global__ void __launch_bounds__(kScanThreads, 6)
@@ -212,14 +228,17 @@ k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* _
        const float* __restrict__ dtwt, const float* __restrict__ dt_b, const float* __restrict__ A2t,
        const float* __restrict__ Dv, float* __restrict__ hstate, float* __restrict__ yg,
        __nv_bfloat16* __restrict__ yg_b, int E, int S, int Tc) {
-    pdl_launch_next();
-    pdl_wait_prev();
     constexpr int W = R + 2 * NS;   // dbc row width
     static_assert(R % 4 == 0 && NS % 4 == 0, "rows are read as float4");
-    __shared__ __align__(16) float sm[kScanRowsSmem][W];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    // staging: [2][kScanRB][128] u, the same for z, [2][kScanRB][W] dbc
+    // (chunked path); [kScanRowsSmem][W] dbc (single-step path)
+    constexpr int kStageF = 2 * kScanRB * (2 * kScanThreads + W);
+    constexpr int kSmemF = kStageF > kScanRowsSmem * W ? kStageF : kScanRowsSmem * W;
+    __shared__ __align__(16) float sbuf[kSmemF];
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * blockDim.x;
+    const int c = c0 + tid;
     const int s_first = blockIdx.y * G;
-    const int n_streams = min(G, S - s_first);
     const bool live = c < E;
     float a2[NS], wdt[R];
     float bdt = 0.f, dv = 0.f;
@@ -231,6 +250,9 @@ k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* _
         bdt = dt_b[c];
         dv = Dv[c];
     }
+    pdl_launch_next();
+    pdl_wait_prev();                             // u, z, dbc and the state come from earlier kernels
+    const int n_streams = min(G, S - s_first);
     const int total = n_streams * Tc;       // rows this CTA visits, stream-major
     const size_t row0 = (size_t)s_first * Tc;
     float h[NS];
@@ -238,8 +260,8 @@ k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* _
         // One step per stream (decompression): the next stream's state is
         // fetched before the current one is computed, so state loads stay in
         // flight during the arithmetic.
-        __syncthreads();
-        for (int i = threadIdx.x; i < total * W; i += blockDim.x) sm[i / W][i % W] = dbc[(row0 + i / W) * W + i % W];
+        float (*sm)[W] = reinterpret_cast<float (*)[W]>(sbuf);
+        for (int i = tid; i < total * W; i += blockDim.x) sm[i / W][i % W] = dbc[(row0 + i / W) * W + i % W];
         __syncthreads();
         if (!live) return;
         float hn[NS];
@@ -277,51 +299,80 @@ k_scan(const float* __restrict__ u, const float* __restrict__ xz, const float* _
         }
         return;
     }
-    for (int r0 = 0; r0 < total; r0 += kScanRowsSmem) {
-        const int nr = min(kScanRowsSmem, total - r0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
-            const int rr = i / W, j = i % W;
-            sm[rr][j] = dbc[(row0 + r0 + rr) * W + j];
+    // chunked path: every thread takes part in the copies (the 128 channels
+    // of a CTA are 512 contiguous bytes of a row: 32 16-byte pieces)
+    float* su = sbuf;                                    // [2][kScanRB][128]
+    float* sz = su + 2 * kScanRB * kScanThreads;         // [2][kScanRB][128]
+    float* sd = sz + 2 * kScanRB * kScanThreads;         // [2][kScanRB][W]
+    const int n_batches = (total + kScanRB - 1) / kScanRB;
+    const int cw = E - c0 < kScanThreads ? E - c0 : kScanThreads;   // channels of this CTA (multiple of 4)
+    auto issue = [&](int b) {
+        const int r_beg = b * kScanRB;
+        const int nr = min(kScanRB, total - r_beg);
+        const int buf = b & 1;
+        for (int i = tid; i < nr * 32; i += kScanThreads) {
+            const int rr = i / 32, q = 4 * (i % 32);
+            if (q < cw) {
+                const size_t row = row0 + r_beg + rr;
+                cp_async16(su + (buf * kScanRB + rr) * kScanThreads + q, u + row * E + c0 + q);
+                cp_async16(sz + (buf * kScanRB + rr) * kScanThreads + q, xz + row * 2 * E + E + c0 + q);
+            }
         }
-        __syncthreads();
-        if (!live) continue;
-        size_t row = row0 + r0;
-        float uc = u[row * E + c];
-        float z = xz[row * 2 * E + E + c];
-        for (int rr = 0; rr < nr; rr++, row++) {
-            const int tau = (r0 + rr) % Tc;
-            const int s = s_first + (r0 + rr) / Tc;
-            if (tau == 0) {
-#pragma unroll
-                for (int n = 0; n < NS; n++) h[n] = hstate[((size_t)s * NS + n) * E + c];
-            }
-            const bool more = rr + 1 < nr;
-            const float u_next = more ? u[(row + 1) * E + c] : 0.f;
-            const float z_next = more ? xz[(row + 1) * 2 * E + E + c] : 0.f;
-            float pre = 0.f;
-#pragma unroll
-            for (int j = 0; j < R; j++) pre = __fmaf_rn(wdt[j], sm[rr][j], pre);
-            const float delta = softplus_f(__fadd_rn(pre, bdt));
-            const float du = __fmul_rn(delta, uc);
-            float y = 0.f;
-#pragma unroll
-            for (int n = 0; n < NS; n++) {
-                const float da = ex2_approx(__fmul_rn(delta, a2[n]));
-                h[n] = __fmaf_rn(da, h[n], __fmul_rn(du, sm[rr][R + n]));
-                y = __fmaf_rn(sm[rr][R + NS + n], h[n], y);
-            }
-            y = __fmaf_rn(dv, uc, y);
-            const float o = __fmul_rn(y, silu_f(z));
-            if (yg_b) yg_b[row * E + c] = __float2bfloat16_rn(o);
-            else yg[row * E + c] = o;
-            if (tau == Tc - 1) {
-#pragma unroll
-                for (int n = 0; n < NS; n++) hstate[((size_t)s * NS + n) * E + c] = h[n];
-            }
-            uc = u_next;
-            z = z_next;
+        for (int i = tid; i < nr * (W / 4); i += kScanThreads) {
+            const int rr = i / (W / 4), q = 4 * (i % (W / 4));
+            cp_async16(sd + (buf * kScanRB + rr) * W + q, dbc + (row0 + r_beg + rr) * W + q);
         }
+        cp_async_commit();
+    };
+    issue(0);
+    int tau = 0, s = s_first;                            // step within the stream, stream of the current row
+    for (int b = 0; b < n_batches; b++) {
+        if (b + 1 < n_batches) {
+            issue(b + 1);
+            cp_async_wait<1>();                          // this thread's copies of batch b have landed
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();                                 // ... and every thread's
+        const int buf = b & 1;
+        const int nr = min(kScanRB, total - b * kScanRB);
+        if (live) {
+            for (int rr = 0; rr < nr; rr++) {
+                const size_t row = row0 + (size_t)b * kScanRB + rr;
+                if (tau == 0) {
+#pragma unroll
+                    for (int n = 0; n < NS; n++) h[n] = hstate[((size_t)s * NS + n) * E + c];
+                }
+                const float* d = sd + (buf * kScanRB + rr) * W;
+                const float uc = su[(buf * kScanRB + rr) * kScanThreads + tid];
+                const float z = sz[(buf * kScanRB + rr) * kScanThreads + tid];
+                float pre = 0.f;
+#pragma unroll
+                for (int j = 0; j < R; j++) pre = __fmaf_rn(wdt[j], d[j], pre);
+                const float delta = softplus_f(__fadd_rn(pre, bdt));
+                const float du = __fmul_rn(delta, uc);
+                float y = 0.f;
+#pragma unroll
+                for (int n = 0; n < NS; n++) {
+                    const float da = ex2_approx(__fmul_rn(delta, a2[n]));
+                    h[n] = __fmaf_rn(da, h[n], __fmul_rn(du, d[R + n]));
+                    y = __fmaf_rn(d[R + NS + n], h[n], y);
+                }
+                y = __fmaf_rn(dv, uc, y);
+                const float o = __fmul_rn(y, silu_f(z));
+                if (yg_b) yg_b[row * E + c] = __float2bfloat16_rn(o);
+                else yg[row * E + c] = o;
+                if (tau == Tc - 1) {
+#pragma unroll
+                    for (int n = 0; n < NS; n++) hstate[((size_t)s * NS + n) * E + c] = h[n];
+                    tau = 0;
+                    s++;
+                } else {
+                    tau++;
+                }
+            }
+        }
+        __syncthreads();                                 // batch b's buffer is free for batch b + 2
     }
 }
 
