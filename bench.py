@@ -159,6 +159,83 @@ def traffic_for(kernel: str):
     return ent
 
 
+# ---------------------------------------------------------------- rooflines per phase
+
+def unit_peaks(device: int) -> dict:
+    """Rates of the units the phases are bound by, measured on this GPU with
+    the library's microbenchmarks (boa_microbench, CUDA-event timed): MUFU
+    ex2 results/s, FP32 FMA FLOP/s, L2 read GB/s, and dense tcgen05 rates
+    (M 128, N 256, warp-issued) for TF32, BF16 and E4M3."""
+    import ctypes as C
+    from paper_2511_11337_b300._lib import check, load
+    lib = load()
+
+    def mb(test, kind=0, N=256, flags=0):
+        r, a = C.c_double(), C.c_double()
+        check(lib.boa_microbench(device, test, kind, 128, N, flags, C.byref(r), C.byref(a)))
+        return r.value
+
+    best = lambda f: max(f() for _ in range(3))
+    return {"mufu_ex2_per_s": best(lambda: mb(0)), "ffma_tflops": best(lambda: mb(1)) / 1e12,
+            "l2_read_gbs": best(lambda: mb(3)) / 1e9,
+            "tf32_tflops": best(lambda: mb(4, 0, 256, 5)) / 1e12,      # A from TMEM, straight-line issue
+            "bf16_tflops": best(lambda: mb(4, 1, 256, 4)) / 1e12,
+            "e4m3_tflops": best(lambda: mb(4, 2, 256, 4)) / 1e12,
+            "how": "boa_microbench: best of 3, CUDA events; tensor rates M 128 N 256 K 32 bytes per instruction, "
+                   "one CTA per SM issuing back to back"}
+
+
+def work_per_byte(shape) -> dict:
+    """Algorithmic work per uncompressed byte of the predictor + coder path
+    (one predicted byte per input byte)."""
+    d, E, N, K, r, nl, F = (shape.d_model, shape.d_inner, shape.d_state, shape.d_conv, shape.dt_rank,
+                            shape.n_layer, shape.d_model * shape.ffn_mult)
+    # the tensor-core projections: in_proj, x_proj, out_proj, FFN, head
+    # (dt_proj, 2 r E per layer, runs on the CUDA cores inside the scan)
+    gemm = 2 * nl * (d * 2 * E + E * (r + 2 * N) + E * d + 2 * d * F) + 2 * d * 256
+    # exp(Delta A) per (channel, state); softplus (ex2 + lg2), the conv's and
+    # the gate's SiLU (ex2 + rcp each) per channel; softmax ex2 per symbol
+    mufu = nl * (E * N + 6 * E) + 256
+    # decode step, state in HBM: each layer reads and writes h (N x E) and
+    # reads the conv window (K - 1 rows of E), writing one row of it
+    state = nl * (2 * N * E * 4 + (K - 1) * E * 4 + E * 4)
+    return {"gemm_flop": gemm, "mufu_ops": mufu, "decode_state_bytes": state}
+
+
+def phase_rooflines(shape, precision: str, comp_mbps: float, dec_mbps: float, peaks: dict, hbm_gbs: float) -> dict:
+    """Each phase's achieved rate against the roofs that bound it."""
+    w = work_per_byte(shape)
+    # tensor (or FP32 FMA) roof for the projections, in the form's own FLOPs
+    # per FP32-equivalent FLOP: 3xTF32 issues three TF32 products
+    if precision == "tf32x3":
+        gemm_peak, gemm_src = peaks["tf32_tflops"] / 3.0, "measured TF32 rate / 3 (three TF32 products per FP32 product)"
+    elif precision == "bf16":
+        gemm_peak, gemm_src = peaks["bf16_tflops"], "measured BF16 rate"
+    elif precision == "fp8":
+        gemm_peak, gemm_src = peaks["e4m3_tflops"], "measured E4M3 rate"
+    else:
+        gemm_peak, gemm_src = peaks["ffma_tflops"], "measured FP32 FMA rate (CUDA cores)"
+    gemm_roof_mbps = gemm_peak * 1e12 / w["gemm_flop"] / 1e6
+    mufu_roof_mbps = peaks["mufu_ex2_per_s"] / w["mufu_ops"] / 1e6
+    state_roof_mbps = hbm_gbs * 1e9 / w["decode_state_bytes"] / 1e6
+    return {
+        "work_per_byte": w,
+        "compress": {"MBps": comp_mbps,
+                     "tensor": {"roof_MBps": gemm_roof_mbps, "frac": comp_mbps / gemm_roof_mbps,
+                                "achieved_tflops": comp_mbps * 1e6 * w["gemm_flop"] / 1e12, "peak_tflops": gemm_peak,
+                                "peak_source": gemm_src},
+                     "mufu": {"roof_MBps": mufu_roof_mbps, "frac": comp_mbps / mufu_roof_mbps,
+                              "achieved_ops_per_s": comp_mbps * 1e6 * w["mufu_ops"],
+                              "peak_ops_per_s": peaks["mufu_ex2_per_s"], "peak_source": "measured ex2 rate"}},
+        "decompress": {"MBps": dec_mbps,
+                       "hbm_state": {"roof_MBps": state_roof_mbps, "frac": dec_mbps / state_roof_mbps,
+                                     "bytes_per_byte": w["decode_state_bytes"], "peak_gbs": hbm_gbs,
+                                     "peak_source": "hbm_gbs (MEASURED_PEAKS.json)"},
+                       "tensor": {"roof_MBps": gemm_roof_mbps, "frac": dec_mbps / gemm_roof_mbps},
+                       "mufu": {"roof_MBps": mufu_roof_mbps, "frac": dec_mbps / mufu_roof_mbps}},
+    }
+
+
 # ---------------------------------------------------------------- oracle leg
 
 def oracle_sample(streams: list[bytes], prefix: int):
@@ -220,31 +297,38 @@ def form_accuracy(streams, forms, path, n_lp=4, lp_len=256, n_gap=16, gap_len=20
     from oracle import oracle as O
     from paper_2511_11337_b300 import api
     om = O.Model(path)
-    lp_ref = [om.logprobs(s[:lp_len]) for s in streams[:n_lp]]
-    gap_in = [s[:gap_len] for s in streams[:n_gap]]
+    # streams spread evenly over the list (an uneven mix is not ordered by kind)
+    pick = lambda n: [streams[i] for i in np.linspace(0, len(streams) - 1, min(n, len(streams))).astype(int)]
+    lp_in = [s[:lp_len] for s in pick(n_lp) if len(s) >= 2]
+    lp_ref = [om.logprobs(s) for s in lp_in]
+    gap_in = [s[:gap_len] for s in pick(n_gap)]
     ref_total = sum(map(len, om.compress_batch(gap_in, n_threads=min(len(gap_in), os.cpu_count() or 1))))
     out = {}
     for f in forms:
         m = api.Model(path, precision=PREC[f])
-        err = max(float(np.abs(m.logprobs(s[:lp_len]) - r).max()) for s, r in zip(streams[:n_lp], lp_ref))
-        got = sum(map(len, m.compress(gap_in)))
+        err = max(float(np.abs(m.logprobs(s) - r).max()) for s, r in zip(lp_in, lp_ref))
+        comp = m.compress(gap_in)
+        lossless = m.decompress(comp, [len(s) for s in gap_in]) == gap_in
+        got = sum(map(len, comp))
         m.close()
         out[f] = {"form": FORM_DESC[f], "max_abs_dlog2p": err, "code_length_gap": (got - ref_total) / ref_total,
-                  "accuracy_sample": f"log2 p: first {lp_len} B of {n_lp} streams; gap: first {gap_len} B of {n_gap} streams"}
+                  "sample_lossless": lossless,
+                  "accuracy_sample": f"log2 p: first {lp_len} B of {len(lp_in)} streams; gap: first {gap_len} B of "
+                                     f"{len(gap_in)} streams, both spread evenly over the workload's streams"}
     return out
 
 
-def form_speed(form, path, d_in, in_off, d_out, out_off, d_dec, lens, stream, autotune=True):
-    """One warm-up and one timed step of another precision form (autotuned
-    like the headline form)."""
+def form_speed(form, path, d_in, in_off, d_out, out_off, d_dec, lens, stream, autotune=True, timed=3):
+    """One warm-up and `timed` timed steps (mean) of another precision form
+    (autotuned like the headline form)."""
     import torch
     from paper_2511_11337_b300 import api
     m = api.Model(path, cuda_stream=stream.cuda_stream, precision=PREC[form])
     if autotune:
         m.autotune(len(lens), int(max(lens)))
     total = int(in_off[-1])
-    res = {}
-    for k in range(2):
+    tcs, tds, lossless = [], [], True
+    for k in range(1 + timed):
         a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         torch.cuda.synchronize()
         a.record(stream)
@@ -253,12 +337,15 @@ def form_speed(form, path, d_in, in_off, d_out, out_off, d_dec, lens, stream, au
         m.decompress_device(d_out.data_ptr(), out_off, lens, d_dec.data_ptr(), in_off, in_sizes=sizes)
         c.record(stream)
         torch.cuda.synchronize()
-        if k == 1:
-            tc, td = a.elapsed_time(b) / 1e3, b.elapsed_time(c) / 1e3
-            res = {"round_trip_MBps": total / 1e6 / (tc + td), "compress_MBps": total / 1e6 / tc,
-                   "decompress_MBps": total / 1e6 / td, "lossless": bool(torch.equal(d_dec, d_in))}
+        lossless = lossless and bool(torch.equal(d_dec, d_in))
+        if k >= 1:
+            tcs.append(a.elapsed_time(b) / 1e3)
+            tds.append(b.elapsed_time(c) / 1e3)
     m.close()
-    return res
+    tc, td = statistics.mean(tcs), statistics.mean(tds)
+    return {"round_trip_MBps": total / 1e6 / (tc + td), "compress_MBps": total / 1e6 / tc,
+            "decompress_MBps": total / 1e6 / td, "lossless": lossless, "timed_steps": timed,
+            "round_trip_MBps_per_step": [total / 1e6 / (x + y) for x, y in zip(tcs, tds)]}
 
 
 def run_precision_report(args):
@@ -466,6 +553,15 @@ def run_boa(args):
         roof["traffic"] = tr["bytes_per_launch"] if tr else None
         roof["avg_launch_ms"] = p["ms"] / p["launches"]
         roof["algorithmic_per_launch"] = (p["flops"] if dom[1].startswith("gemm") else p["bytes"]) / p["launches"]
+    if roof is not None and world == 1:
+        try:
+            up = unit_peaks(local)
+            roof["unit_peaks_measured"] = up
+            roof["phases"] = phase_rooflines(
+                synth.PAPER_SCALE, args.precision, total / 1e6 / (phase_ms["compress"] / 1e3),
+                total / 1e6 / (phase_ms["decompress"] / 1e3), up, peaks["hbm_gbs"])
+        except Exception as e:                       # a report, never a reason to lose the bench line
+            roof["phases"] = {"error": str(e)}
     breakdown = {f"{ph}:{k}": {"launches_timed": v["launches"], "ms_per_step": round(v["ms_step"], 2),
                                "share": round(v["ms_step"] / step_est, 4) if step_est else None}
                  for (ph, k), v in sorted(est.items(), key=lambda kv: -kv[1]["ms_step"])}
@@ -484,7 +580,9 @@ def run_boa(args):
                                  "sample": f"first {one} B of stream 0, one thread, {dt_1:.1f} s"}}
 
     forms = {}
-    if world == 1 and args.forms:
+    if world == 1:
+        # the headline form's accuracy against the oracle on a sample is
+        # always reported; the other forms' accuracy and speed on request
         names = [f for f in args.forms.split(",") if f and f != args.precision]
         acc = form_accuracy(streams, [args.precision] + names, path)
         forms[args.precision] = dict(acc[args.precision], round_trip_MBps=value,
