@@ -860,19 +860,21 @@ static boa_status gemm_tc(boa_model* m, int cls, const __nv_bfloat16* A, const _
 
 // FP8 projection: quantise the FP32 activation rows (one warp per row), then
 // the E4M3 tensor-core kernel with the row and weight scales in its epilogue.
+// prequant: the kernel that produced A already wrote its E4M3 copy and row
+// scales into the view's FP8 scratch (f8_out), so no quantisation launch.
 template <int EPI>
 static boa_status gemm_f8(boa_model* m, int cls, const float* A, const __nv_fp8_e4m3* W, const float* wscale,
-                          const float* bias, float* C, long long M, int N, int K) {
+                          const float* bias, float* C, long long M, int N, int K, bool prequant = false) {
     if (M <= 0) return BOA_OK;
     if (N % 4 != 0 || K % 16 != 0 || K > 1024) return fail(BOA_ERR_FORMAT, "fp8 gemm shape N=%d K=%d unsupported", N, K);
     const int Kp = (K + 127) / 128 * 128;     // W is stored with the same zero padding
     if (!m->v.a8 || (size_t)Kp > m->kp8) return fail(BOA_ERR_ARG, "FP8 activation scratch not sized for K=%d", K);
-    {
+    if (!prequant) {
         ProfScope pq(m, BOA_KC_OTHER, 3.0 * M * K, 5.0 * M * K + 4.0 * M);
         launch_k(m, k_quant_rows_e4m3, dim3((unsigned)((M + 7) / 8)), 256, 0, 1, A,
                  reinterpret_cast<__nv_fp8_e4m3*>(m->v.a8), m->v.a8s, M, K, Kp);
+        TRY(check_launch(m, "quant_rows"));
     }
-    TRY(check_launch(m, "quant_rows"));
     const bool resid = EPI == kEpiResid || EPI == kEpiBiasResid;
     ProfScope ps(m, cls, 2.0 * M * N * K, ((double)M * K + (double)K * N) + 4.0 * (double)M * N * (resid ? 2 : 1));
     const int BN = tc_bn(N, M);
@@ -961,12 +963,27 @@ static boa_status gemm_t3(boa_model* m, int cls, const float* A, const float* Wh
     return check_launch(m, "gemm_t3");
 }
 
+// FP8 form: the E4M3 copy (and per-row scales) of a projection's A operand
+// with K inputs, in the view's FP8 scratch, which the producing kernel
+// writes itself (gemm_f8 with prequant then skips its quantisation launch).
+static F8Out f8_out(const boa_model* m, int K) {
+    if (m->precision != BOA_PREC_FP8) return F8Out{nullptr, nullptr, 0};
+    return F8Out{reinterpret_cast<__nv_fp8_e4m3*>(m->v.a8), m->v.a8s, (K + 127) / 128 * 128};
+}
+
+// The conv kernel writes the FP8 copy of u when one CTA holds a whole row.
+static bool conv_writes_f8(const boa_model* m) { return m->precision == BOA_PREC_FP8 && m->E <= 512; }
+// The decode-step scan writes the FP8 copy of its output rows (variant 0).
+static bool scan_writes_f8(const boa_model* m, int Tc) {
+    return m->precision == BOA_PREC_FP8 && Tc == 1 && m->scan_variant == 0;
+}
+
 template <int VPT>
 static void launch_embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc, const DevLayer& L0) {
     const long long rows = (long long)S * Tc;
     const bool tc = m->precision == BOA_PREC_BF16;
     launch_k(m, k_embed_ln<VPT>, dim3((unsigned)((rows + 7) / 8)), 256, 0, 1, ts, S, Tc, m->embed, L0.ln_a_w,
-             L0.ln_a_b, m->v.x, m->v.xn, tc ? m->v.xn_b : nullptr);
+             L0.ln_a_b, m->v.x, m->v.xn, tc ? m->v.xn_b : nullptr, f8_out(m, m->d));
 }
 
 template <int VPT>
@@ -974,8 +991,10 @@ static void launch_ln_ln(boa_model* m, long long rows, const DevLayer& L, const 
     const bool tc = m->precision == BOA_PREC_BF16;
     // the BF16 copy of x feeds the head (last block) or the next block's FFN
     __nv_bfloat16* xb = (tc && (!next || m->F)) ? m->v.x_b : nullptr;
+    // FP8: the next block's in_proj input xn, or the head's input x (both K = d)
     launch_k(m, k_ln_ln<VPT>, dim3((unsigned)((rows + 7) / 8)), 256, 0, 1, rows, m->v.x, L.ln_b_w, L.ln_b_b,
-             next ? next->ln_a_w : nullptr, next ? next->ln_a_b : nullptr, m->v.xn, xb, tc ? m->v.xn_b : nullptr);
+             next ? next->ln_a_w : nullptr, next ? next->ln_a_b : nullptr, m->v.xn, xb, tc ? m->v.xn_b : nullptr,
+             f8_out(m, m->d));
 }
 
 static boa_status embed_ln(boa_model* m, const TokenSrc& ts, int S, int Tc) {
@@ -1010,9 +1029,10 @@ static boa_status conv(boa_model* m, int l, int S, int Tc) {
     ProfScope ps(m, BOA_KC_CONV, rows * m->E * (2.0 * m->K + 4),
                  4.0 * (2 * rows * m->E + (double)S * ((m->K - 1) + std::min(Tc, m->K - 1)) * m->E));
     __nv_bfloat16* ub = m->precision == BOA_PREC_BF16 ? m->v.u_b : nullptr;
+    const F8Out f8 = conv_writes_f8(m) ? f8_out(m, m->E) : F8Out{nullptr, nullptr, 0};
 #define CONV_CASE(KK, GG) \
     launch_k(m, k_conv_silu<KK, GG>, grid, 128, 0, 1, m->v.xz, m->E, L.conv_w, L.conv_b, win, \
-             (const SlotState*)m->v.slots, m->v.u, ub, S, Tc)
+             (const SlotState*)m->v.slots, m->v.u, ub, S, Tc, f8)
     if (G == 8) {
         switch (m->K) { case 2: CONV_CASE(2, 8); break; case 3: CONV_CASE(3, 8); break; default: CONV_CASE(4, 8); break; }
     } else {
@@ -1051,7 +1071,8 @@ static boa_status launch_step_bulk(boa_model* m, const DevLayer& L, float* hs, _
     TRY((smem_opt_in(optin, k_scan_step_bulk<16, RR>, -1, m->device, "decode scan")));
     const int grid = (int)std::min<long long>(S, (long long)m->num_sms * cps);
     launch_k(m, k_scan_step_bulk<16, RR>, dim3((unsigned)grid), dim3((unsigned)(m->E / 2)), smem, 1, m->v.u, m->v.xz,
-             m->v.dbc, L.dt_w, L.dt_b, L.A2, L.D, hs, m->v.yg, ygb, m->E, S, stages, m->err.p);
+             m->v.dbc, L.dt_w, L.dt_b, L.A2, L.D, hs, m->v.yg, ygb, m->E, S, stages, m->err.p,
+             scan_writes_f8(m, 1) ? f8_out(m, m->E) : F8Out{nullptr, nullptr, 0});
     return BOA_OK;
 }
 
@@ -1120,12 +1141,17 @@ static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc, bool 
                 TRY(gemm_tc<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->v.hid_b, B.w2, L.b2, m->v.x, nullptr, rows, d, m->F));
             }
         } else if (m->precision == BOA_PREC_FP8) {
+            // the LayerNorm kernels (and the decoder's next-step embedding)
+            // write in_proj's FP8 input, conv x_proj's, the decode-step scan
+            // out_proj's; the chunked scan and the FFN are quantised here
             const auto& Q = m->qlayers[l];
-            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_IN, m->v.xn, Q.in_w, Q.in_s, nullptr, m->v.xz, rows, 2 * E, d));
+            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_IN, m->v.xn, Q.in_w, Q.in_s, nullptr, m->v.xz, rows, 2 * E, d, true));
             TRY(conv(m, l, S, Tc));
-            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_X, m->v.u, Q.x_w, Q.x_s, nullptr, m->v.dbc, rows, m->R2, E));
+            TRY(gemm_f8<kEpiStore>(m, BOA_KC_GEMM_X, m->v.u, Q.x_w, Q.x_s, nullptr, m->v.dbc, rows, m->R2, E,
+                                   conv_writes_f8(m)));
             TRY(scan(m, l, S, Tc));
-            TRY(gemm_f8<kEpiResid>(m, BOA_KC_GEMM_OUT, m->v.yg, Q.out_w, Q.out_s, nullptr, m->v.x, rows, d, E));
+            TRY(gemm_f8<kEpiResid>(m, BOA_KC_GEMM_OUT, m->v.yg, Q.out_w, Q.out_s, nullptr, m->v.x, rows, d, E,
+                                   scan_writes_f8(m, Tc)));
             if (m->F) {
                 TRY(gemm_f8<kEpiBiasGelu>(m, BOA_KC_GEMM_FFN, m->v.x, Q.w1, Q.w1_s, L.b1, m->v.hid, rows, m->F, d));
                 TRY(gemm_f8<kEpiBiasResid>(m, BOA_KC_GEMM_FFN, m->v.hid, Q.w2, Q.w2_s, L.b2, m->v.x, rows, d, m->F));
@@ -1157,8 +1183,9 @@ static boa_status forward(boa_model* m, const TokenSrc& ts, int S, int Tc, bool 
     if (tc) return gemm_tc<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->v.x_b, m->head_wb, m->head_b, m->v.logits, nullptr, rows, 256, d);
     if (m->precision == BOA_PREC_TF32X3)
         return gemm_t3<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->v.x, m->head_hi, m->head_lo, m->head_b, m->v.logits, rows, 256, d);
-    if (m->precision == BOA_PREC_FP8)
-        return gemm_f8<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->v.x, m->head_w8, m->head_s, m->head_b, m->v.logits, rows, 256, d);
+    if (m->precision == BOA_PREC_FP8)    // the last LayerNorm wrote the head's FP8 input
+        return gemm_f8<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->v.x, m->head_w8, m->head_s, m->head_b, m->v.logits, rows, 256,
+                                 d, true);
     return gemm<kEpiBias>(m, BOA_KC_GEMM_HEAD, m->v.x, m->head_wt, m->head_b, m->v.logits, rows, 256, d);
 }
 
@@ -1213,7 +1240,10 @@ static boa_status ensure_workspace(boa_model* m, size_t S, size_t rows) {
 }
 
 // Point the launchers at slots [s0, ...) of an S_all-slot batch with Tc rows
-// per slot, launching on stream st.
+// per slot, launching on stream st.  The FP8 scratch (a8, a8s) of a view
+// starts at row s0 Tc with room for kp8 bytes per row, but its rows are laid
+// out with the stride of the projection that reads them (its K padded to
+// 128), so a writer and the projection reading its rows use the same view.
 static void bind_view(boa_model* m, size_t s0, size_t Tc, size_t S_all, cudaStream_t st) {
     View& v = m->v;
     const size_t r0 = s0 * Tc;
@@ -1516,19 +1546,28 @@ static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, c
     // the next step's input rows of the bound view's slots
     auto next_embed = [&] {
         return NextEmbed{m->embed, L0.ln_a_w, L0.ln_a_b, m->v.x, m->v.xn,
-                         m->precision == BOA_PREC_BF16 ? m->v.xn_b : nullptr};
+                         m->precision == BOA_PREC_BF16 ? m->v.xn_b : nullptr, f8_out(m, m->d)};
     };
     const int tb128 = 128;
     k_dec_trivial<<<(unsigned)((n + tb128 - 1) / tb128), tb128, 0, m->stream>>>((int)n, d_in, tb, d_out);
     TRY(check_launch(m, "dec_trivial"));
     if (sc.S > 0) {
-        const NextEmbed ne0 = next_embed();
-        switch (m->d) {
-            case 64: launch_dec_init<2>(m, S, d_in, tb, d_out, ne0); break;
-            case 128: launch_dec_init<4>(m, S, d_in, tb, d_out, ne0); break;
-            default: launch_dec_init<8>(m, S, d_in, tb, d_out, ne0); break;
+        // Each lane's slots start through that lane's view, like its steps:
+        // the FP8 form's input rows sit in the view's FP8 scratch with the
+        // consuming projection's row stride, so a lane's rows are valid only
+        // when written through the same view that reads them.
+        for (int p = 0; p < P; p++) {
+            const int s0 = (int)((long long)S * p / P), n_p = (int)((long long)S * (p + 1) / P) - s0;
+            bind_view(m, s0, 1, S, m->stream);
+            const NextEmbed ne0 = next_embed();
+            switch (m->d) {
+                case 64: launch_dec_init<2>(m, n_p, d_in, tb, d_out, ne0); break;
+                case 128: launch_dec_init<4>(m, n_p, d_in, tb, d_out, ne0); break;
+                default: launch_dec_init<8>(m, n_p, d_in, tb, d_out, ne0); break;
+            }
+            TRY(check_launch(m, "dec_init"));
         }
-        TRY(check_launch(m, "dec_init"));
+        bind_view(m, 0, 1, S, m->stream);
         // One decode step of lane p (slots [S p / P, S (p + 1) / P)) on stream ls.
         auto lane_step = [&](int p, cudaStream_t ls) -> boa_status {
             const int s0 = (int)((long long)S * p / P), n_p = (int)((long long)S * (p + 1) / P) - s0;
@@ -2024,12 +2063,16 @@ extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream
         if (st == BOA_OK && ms < best.decompress_ms) { best.decompress_ms = ms; best.scan_variant = g; best.decode_lanes = 1; }
     }
     m->scan_variant = best.scan_variant;
+    // More lanes are taken only when they win clearly on the short sample:
+    // a few hundred steps cannot resolve a 1-2 % difference, and at full
+    // length extra lanes contend for the SMs (measured on the 64 MiB jet
+    // table: 2 lanes 4779 ms, 3 lanes 4822 ms, 4 lanes 4930 ms of decoding).
     for (int p : {2, 4}) {
         if (st != BOA_OK || (size_t)p > n) break;
         m->decode_lanes = p;
         double ms = 0;
         st = time_decode(ms);
-        if (st == BOA_OK && ms < best.decompress_ms) { best.decompress_ms = ms; best.decode_lanes = p; }
+        if (st == BOA_OK && ms < 0.97 * best.decompress_ms) { best.decompress_ms = ms; best.decode_lanes = p; }
     }
     m->decode_lanes = best.decode_lanes;
     m->prof_on = prof;

@@ -40,6 +40,42 @@ __device__ __forceinline__ void warp_layernorm(const float (&x)[VPT], const floa
     }
 }
 
+// ------------------------------------------------------ FP8 activation rows
+//
+// The E4M3 projections' A operand: per row, scale = amax / 448 and
+// q[k] = e4m3(a[k] * (448 / amax)), rounded to nearest and saturated, with
+// amax = max_k |a[k]| (scale 1 for an all-zero row); rows of Kp >= K bytes
+// (the consumer GEMM's K rounded up to its 128-wide K blocks), the padding
+// zero.  k_quant_rows_e4m3 writes it from any FP32 matrix; a kernel that
+// holds whole rows (LayerNorm, conv + SiLU, the decode-step scan) writes it
+// itself through the same functions.  The maximum does not depend on the
+// order it is taken in, so both give the same bytes and scales.
+struct F8Out {
+    __nv_fp8_e4m3* q;     // [rows][Kp]; nullptr: no FP8 copy
+    float* scale;         // [rows]
+    int Kp;
+};
+
+__device__ __forceinline__ float e4m3_row_inv(float amax) { return amax > 0.f ? __fdiv_rn(448.0f, amax) : 1.0f; }
+__device__ __forceinline__ float e4m3_row_scale(float amax) { return amax > 0.f ? __fdiv_rn(amax, 448.0f) : 1.0f; }
+__device__ __forceinline__ __nv_fp8_e4m3 e4m3_of(float v, float inv) { return __nv_fp8_e4m3(__fmul_rn(v, inv)); }
+
+// One warp's row of d = 32 VPT values, lane holding columns lane + 32 i.
+template <int VPT>
+__device__ __forceinline__ void warp_write_f8(const F8Out& f8, size_t row, const float (&y)[VPT], int lane) {
+    constexpr int d = VPT * 32;
+    float amax = 0.f;
+#pragma unroll
+    for (int i = 0; i < VPT; i++) amax = fmaxf(amax, fabsf(y[i]));
+    amax = warp_max(amax);
+    const float inv = e4m3_row_inv(amax);
+    if (lane == 0) f8.scale[row] = e4m3_row_scale(amax);
+    __nv_fp8_e4m3* o = f8.q + row * (size_t)f8.Kp;
+#pragma unroll
+    for (int i = 0; i < VPT; i++) o[lane + 32 * i] = e4m3_of(y[i], inv);
+    for (int k = d + lane; k < f8.Kp; k += 32) o[k] = __nv_fp8_e4m3(0.0f);
+}
+
 // Streams run in a fixed pool of slots (row block s of every launch belongs
 // to slot s).  A slot works through its own list of streams, one after the
 // other; t is the position in the current stream: the first step of the
@@ -69,7 +105,8 @@ __device__ __forceinline__ int row_token(const TokenSrc& ts, int s, int tau) {
 template <int VPT>
 __global__ void k_embed_ln(TokenSrc ts, int S, int Tc, const float* __restrict__ embed,
                            const float* __restrict__ g, const float* __restrict__ b,
-                           float* __restrict__ x, float* __restrict__ xn, __nv_bfloat16* __restrict__ xn_b) {
+                           float* __restrict__ x, float* __restrict__ xn, __nv_bfloat16* __restrict__ xn_b,
+                           F8Out f8) {
     pdl_launch_next();
     pdl_wait_prev();
     constexpr int d = VPT * 32;
@@ -86,18 +123,21 @@ __global__ void k_embed_ln(TokenSrc ts, int S, int Tc, const float* __restrict__
     for (int i = 0; i < VPT; i++) {
         x[(size_t)row * d + lane + 32 * i] = v[i];
         if (xn_b) xn_b[(size_t)row * d + lane + 32 * i] = __float2bfloat16_rn(y[i]);
-        else xn[(size_t)row * d + lane + 32 * i] = y[i];
+        else if (!f8.q) xn[(size_t)row * d + lane + 32 * i] = y[i];
     }
+    if (f8.q) warp_write_f8<VPT>(f8, (size_t)row, y, lane);
 }
 
 // x = LN_b(x); then, when another block follows, xn = LN_a'(x).
 // Optional BF16 copies for the tensor-core path: x_b (input of the head or the
 // FFN) and xn_b (input of the next in_proj, replacing xn).
+// f8: the FP8 copy of the next projection's input: xn when another block
+// follows (its in_proj), else x (the head).
 template <int VPT>
 __global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __restrict__ gb,
                         const float* __restrict__ bb, const float* __restrict__ ga,
                         const float* __restrict__ ba, float* __restrict__ xn,
-                        __nv_bfloat16* __restrict__ x_b, __nv_bfloat16* __restrict__ xn_b) {
+                        __nv_bfloat16* __restrict__ x_b, __nv_bfloat16* __restrict__ xn_b, F8Out f8) {
     pdl_launch_next();
     pdl_wait_prev();
     constexpr int d = VPT * 32;
@@ -119,12 +159,82 @@ __global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __re
 #pragma unroll
         for (int i = 0; i < VPT; i++) {
             if (xn_b) xn_b[(size_t)row * d + lane + 32 * i] = __float2bfloat16_rn(z[i]);
-            else xn[(size_t)row * d + lane + 32 * i] = z[i];
+            else if (!f8.q) xn[(size_t)row * d + lane + 32 * i] = z[i];
         }
+        if (f8.q) warp_write_f8<VPT>(f8, (size_t)row, z, lane);
+    } else if (f8.q) {
+        warp_write_f8<VPT>(f8, (size_t)row, y, lane);
     }
 }
 
 // ---------------------------------------------------- causal conv1d + SiLU
+
+// The per-channel conv + SiLU of k_conv_silu (same operations in the same
+// order) for one stream per CTA that covers the whole row (the FP8 form):
+// after each row the CTA takes the row's maximum and writes its E4M3 copy
+// (f8) besides u.  Threads past the row's end take part in the barriers.
+template <int K>
+__device__ __forceinline__ void conv_silu_rows_f8(const float* __restrict__ xz, int E, const float* __restrict__ wt,
+                                                  const float* __restrict__ bconv, float* __restrict__ win,
+                                                  const SlotState* __restrict__ slots, float* __restrict__ u, int S,
+                                                  int Tc, const F8Out& f8, int c) {
+    __shared__ float red[2][4];
+    const int s = blockIdx.y;
+    const bool live = c < E && s < S;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    float4 wv[K], bc = make_float4(0.f, 0.f, 0.f, 0.f), h[K];
+    long long t0 = 0;
+    float* ring = nullptr;
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < K; k++) wv[k] = *reinterpret_cast<const float4*>(wt + (size_t)k * E + c);
+        bc = *reinterpret_cast<const float4*>(bconv + c);
+        t0 = slots[s].t;
+        ring = win + (size_t)s * (K - 1) * E + c;
+#pragma unroll
+        for (int k = 0; k < K - 1; k++) h[k] = *reinterpret_cast<const float4*>(ring + (size_t)((t0 + k) % (K - 1)) * E);
+    }
+    size_t row = (size_t)s * Tc;
+    for (int tau = 0; tau < Tc; tau++, row++) {
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+        if (live) {
+            const float4 xi = *reinterpret_cast<const float4*>(xz + row * 2 * E + c);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float acc = reinterpret_cast<const float*>(&bc)[j];
+#pragma unroll
+                for (int k = 0; k < K - 1; k++)
+                    acc = __fmaf_rn(reinterpret_cast<const float*>(&wv[k])[j], reinterpret_cast<const float*>(&h[k])[j], acc);
+                acc = __fmaf_rn(reinterpret_cast<const float*>(&wv[K - 1])[j], reinterpret_cast<const float*>(&xi)[j], acc);
+                o[j] = silu_f(acc);
+            }
+#pragma unroll
+            for (int k = 0; k + 1 < K - 1; k++) h[k] = h[k + 1];
+            h[K - 2] = xi;
+            *reinterpret_cast<float4*>(u + row * E + c) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        float a = fmaxf(fmaxf(fabsf(o[0]), fabsf(o[1])), fmaxf(fabsf(o[2]), fabsf(o[3])));
+        a = warp_max(a);
+        if (lane == 0) red[tau & 1][warp] = a;
+        __syncthreads();
+        const float amax = fmaxf(fmaxf(red[tau & 1][0], red[tau & 1][1]), fmaxf(red[tau & 1][2], red[tau & 1][3]));
+        if (live) {
+            const float inv = e4m3_row_inv(amax);
+            if (c == 0) f8.scale[row] = e4m3_row_scale(amax);
+            __nv_fp8_e4m3* q = f8.q + row * (size_t)f8.Kp + c;
+#pragma unroll
+            for (int j = 0; j < 4; j++) q[j] = e4m3_of(o[j], inv);
+        }
+    }
+    if (live) {
+        const long long t1 = t0 + Tc;
+#pragma unroll
+        for (int k = 0; k < K - 1; k++) {
+            const long long pos = t1 - (K - 1) + k;
+            if (pos >= t0) *reinterpret_cast<float4*>(ring + (size_t)(pos % (K - 1)) * E) = h[k];
+        }
+    }
+}
 
 // u[s, t, c] = SiLU(b_c + sum_k w[c][k] xi[s, t-K+1+k, c]); the last K-1
 // inputs of every (stream, channel) persist in win[S][K-1][E] across calls
@@ -134,14 +244,20 @@ __global__ void k_ln_ln(long long rows, float* __restrict__ x, const float* __re
 // this call.  wt is the tap matrix stored [K][E] (channel innermost).  A
 // thread owns four adjacent channels (16-byte loads and stores) of G
 // consecutive streams.
+// f8 (FP8 form, one CTA per row: E <= 4 x 128): the row's E4M3 copy for
+// x_proj, its scale from a CTA-wide maximum per row.
 template <int K, int G>
 __global__ void __launch_bounds__(128)
 k_conv_silu(const float* __restrict__ xz, int E, const float* __restrict__ wt,
             const float* __restrict__ bconv, float* __restrict__ win, const SlotState* __restrict__ slots,
-            float* __restrict__ u, __nv_bfloat16* __restrict__ u_b, int S, int Tc) {
+            float* __restrict__ u, __nv_bfloat16* __restrict__ u_b, int S, int Tc, F8Out f8) {
     pdl_launch_next();
     pdl_wait_prev();
     const int c = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (f8.q) {
+        conv_silu_rows_f8<K>(xz, E, wt, bconv, win, slots, u, S, Tc, f8, c);
+        return;
+    }
     if (c >= E) return;
     float4 wv[K];
 #pragma unroll
@@ -774,6 +890,7 @@ struct NextEmbed {
     float* x;
     float* xn;
     __nv_bfloat16* xn_b;
+    F8Out f8;             // FP8 form: xn's E4M3 copy instead of xn
 };
 
 template <int VPT>
@@ -787,8 +904,9 @@ __device__ __forceinline__ void warp_embed_ln(const NextEmbed& ne, int tok, size
     for (int i = 0; i < VPT; i++) {
         ne.x[row * d + lane + 32 * i] = v[i];
         if (ne.xn_b) ne.xn_b[row * d + lane + 32 * i] = __float2bfloat16_rn(y[i]);
-        else ne.xn[row * d + lane + 32 * i] = y[i];
+        else if (!ne.f8.q) ne.xn[row * d + lane + 32 * i] = y[i];
     }
+    if (ne.f8.q) warp_write_f8<VPT>(ne.f8, row, y, lane);
 }
 
 // Decoder start for the stream now in slot s: raw first byte to the output,
@@ -925,16 +1043,16 @@ __global__ void k_quant_rows_e4m3(const float* __restrict__ A, __nv_fp8_e4m3* __
         amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
     amax = warp_max(amax);
-    const float inv = amax > 0.f ? __fdiv_rn(448.0f, amax) : 1.0f;
-    if (lane == 0) scale[row] = amax > 0.f ? __fdiv_rn(amax, 448.0f) : 1.0f;
+    const float inv = e4m3_row_inv(amax);
+    if (lane == 0) scale[row] = e4m3_row_scale(amax);
     __nv_fp8_e4m3* o = q + row * Kp;
     for (int k = 4 * lane; k < Kp; k += 128) {
         if (k < K) {
             const float4 v = *reinterpret_cast<const float4*>(a + k);
-            o[k + 0] = __nv_fp8_e4m3(__fmul_rn(v.x, inv));
-            o[k + 1] = __nv_fp8_e4m3(__fmul_rn(v.y, inv));
-            o[k + 2] = __nv_fp8_e4m3(__fmul_rn(v.z, inv));
-            o[k + 3] = __nv_fp8_e4m3(__fmul_rn(v.w, inv));
+            o[k + 0] = e4m3_of(v.x, inv);
+            o[k + 1] = e4m3_of(v.y, inv);
+            o[k + 2] = e4m3_of(v.z, inv);
+            o[k + 3] = e4m3_of(v.w, inv);
         } else {
             o[k + 0] = o[k + 1] = o[k + 2] = o[k + 3] = __nv_fp8_e4m3(0.0f);
         }

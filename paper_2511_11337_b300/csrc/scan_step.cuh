@@ -42,11 +42,12 @@ __global__ void __launch_bounds__(512)
 k_scan_step_bulk(const float* __restrict__ u, const float* __restrict__ xz, const float* __restrict__ dbc,
                  const float* __restrict__ dtwt, const float* __restrict__ dt_b, const float* __restrict__ A2t,
                  const float* __restrict__ Dv, float* __restrict__ hstate, float* __restrict__ yg,
-                 __nv_bfloat16* __restrict__ yg_b, int E, int S, int stages, int* __restrict__ err) {
+                 __nv_bfloat16* __restrict__ yg_b, int E, int S, int stages, int* __restrict__ err, F8Out f8) {
     constexpr int W = R + 2 * NS;
     static_assert(W % 4 == 0, "the dbc row is copied in 16-byte units");
     extern __shared__ __align__(128) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[kStepMaxStages];
+    __shared__ float red[2][16];                 // FP8 form: per-warp row maxima (up to 16 warps)
     const int sf = step_stage_floats(NS, R, E);
     float* ring = reinterpret_cast<float*>(smem_raw);
     const int tid = threadIdx.x;
@@ -133,8 +134,24 @@ k_scan_step_bulk(const float* __restrict__ u, const float* __restrict__ xz, cons
         }
         const float o0 = __fmul_rn(__fmaf_rn(dv.x, u2.x, y0), silu_f(z2.x));
         const float o1 = __fmul_rn(__fmaf_rn(dv.y, u2.y, y1), silu_f(z2.y));
-        if (yg_b) *reinterpret_cast<__nv_bfloat162*>(yg_b + (size_t)s * E + c) = __floats2bfloat162_rn(o0, o1);
-        else *reinterpret_cast<float2*>(yg + (size_t)s * E + c) = make_float2(o0, o1);
+        if (f8.q) {
+            // FP8 form: the row's E4M3 copy for out_proj (the CTA holds the
+            // whole row), its scale from the CTA-wide maximum
+            const float a = warp_max(fmaxf(fabsf(o0), fabsf(o1)));
+            if ((tid & 31) == 0) red[k & 1][tid >> 5] = a;
+            __syncthreads();
+            float amax = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) amax = fmaxf(amax, red[k & 1][w]);
+            const float inv = e4m3_row_inv(amax);
+            if (tid == 0) f8.scale[s] = e4m3_row_scale(amax);
+            __nv_fp8_e4m3* q = f8.q + (size_t)s * f8.Kp + c;
+            q[0] = e4m3_of(o0, inv);
+            q[1] = e4m3_of(o1, inv);
+        } else if (yg_b) {
+            *reinterpret_cast<__nv_bfloat162*>(yg_b + (size_t)s * E + c) = __floats2bfloat162_rn(o0, o1);
+        } else {
+            *reinterpret_cast<float2*>(yg + (size_t)s * E + c) = make_float2(o0, o1);
+        }
         __syncthreads();                         // every thread is done with this stage
         if (tid == 0 && issued < mine) issue(issued++);
     }

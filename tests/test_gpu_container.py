@@ -82,7 +82,8 @@ def test_graph_and_eager_decode_agree(api, tiny_model_path):
 
 
 @pytest.mark.parametrize("d_model,expand,prec,d_conv", [(64, 2, 0, 4), (256, 2, 2, 4), (64, 3, 1, 4), (128, 4, 0, 4),
-                                                         (64, 2, 2, 3), (64, 2, 1, 2), (64, 2, 3, 4)])
+                                                         (64, 2, 2, 3), (64, 2, 1, 2), (64, 2, 3, 4), (128, 2, 3, 4),
+                                                         (256, 2, 3, 4)])
 def test_decode_scan_variants_agree(api, tmp_path, d_model, expand, prec, d_conv):
     """Every decode-step scan kernel (persistent bulk-copy fed, four channels
     per thread, one or eight streams per CTA), with the slots split into one
@@ -90,7 +91,10 @@ def test_decode_scan_variants_agree(api, tmp_path, d_model, expand, prec, d_conv
     short streams: more slots than the persistent grid, so its CTAs walk
     several streams, with a ragged last round; model widths cover one to
     eight CTAs per SM and two to four ring stages; conv widths 2 to 4 and
-    every precision form."""
+    every precision form.  FP8 at d_model 128 and 256: in_proj's FP8 rows
+    (K = d) are narrower than the FP8 scratch's per-row room (K = expand d),
+    so a lane that read rows written through another lane's view would
+    decode garbage."""
     shape = synth.ModelShape(d_model=d_model, n_layer=2, expand=expand, d_conv=d_conv)
     path = synth.make_model_file(str(tmp_path / "v.boaw"), shape, seed=7)
     g = np.random.default_rng(d_model + expand)

@@ -19,6 +19,10 @@ from paper_2511_11337_b300 import synth
 pytestmark = pytest.mark.gpu
 
 BF16_LOG2P_TOL = 0.03    # BF16 operands: relative rounding 2^-9 per input, summed over d <= 512 terms
+# E4M3 operands: 3 mantissa bits, relative rounding 2^-4 per input (each row
+# and weight channel scaled to the full E4M3 range first, so no subnormal
+# loss); the same accumulation as BF16 with a unit roundoff 2^5 times larger
+FP8_LOG2P_TOL = BF16_LOG2P_TOL * 2.0 ** 5
 
 
 def bf16_round(x):
@@ -258,6 +262,7 @@ def test_fp8_model(api, model_dir):
     err = np.abs(m.logprobs(streams[0][:1500]) - om.logprobs(streams[0][:1500])).max()
     print(f"FP8 max |dlog2p| = {err:.3e}, code-length gap = {gap:+.3e}")
     assert abs(gap) <= 0.005
+    assert err <= FP8_LOG2P_TOL
     assert m.compress([streams[4]] * 9)[5] == comp[4]
 
 
