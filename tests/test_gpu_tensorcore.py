@@ -52,7 +52,7 @@ def api():
 
 
 SHAPES = [(128, 128, 64), (300, 1024, 256), (4096, 48, 512), (1000, 256, 512), (77, 64, 64), (129, 36, 64),
-          (513, 256, 1024), (8500, 256, 256), (8300, 1024, 128),   # these two: compression-size 256-wide tiles
+          (513, 256, 1024), (8500, 256, 256), (8300, 1024, 128),   # these two: compression-size 128-wide tiles
           (20000, 256, 512), (19000, 48, 512), (19000, 128, 256)]  # grids that fill the GPU (BF16 / FP8
                                                                    # x_proj: split K inside one CTA's TMEM)
 
@@ -87,8 +87,8 @@ def test_gemm_rows_independent_of_batch(api, precision, NK):
     memory, as in the small slices, or sit in one CTA's TMEM, as in the BF16
     and FP8 forms' grids that fill the GPU: the 20000-row batch), and across
     tile widths
-    (batches above 8192 rows run 256- or 128-wide tiles, the slices the
-    narrower decode-size ones)."""
+    (batches above 8192 rows run 128-wide tiles, the slices the decode-size
+    64- and 48-wide ones where N calls for them)."""
     N, K = NK
     g = np.random.default_rng(5)
     A = g.normal(0, 1, (20000, K)).astype(np.float32)
