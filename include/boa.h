@@ -345,8 +345,15 @@ boa_status boa_scan_train_bwd(size_t Bsz, size_t T, size_t E, size_t N, size_t c
  * file's tensor array with learning rate lr.  The model then uses the
  * updated weights (its device copies in every precision form are rebuilt)
  * and its fingerprint becomes that of the file boa_save_model would write.
- * FP32 throughout, sums in a fixed order (the same batch gives the same
- * update bit for bit); the Adam moments live in the model.
+ * Arithmetic follows the model's precision form.  FP32 (and the other
+ * forms except BF16): FP32 on the CUDA cores.  BF16 (BOA_PREC_BF16): the
+ * projections, the input gradients of in_proj, out_proj and the head, and
+ * the weight gradients of in_proj, x_proj, out_proj and the head run on the
+ * tensor cores with BF16 operands and FP32 accumulation (weight gradients in
+ * fixed 4096-row parts added in order); everything else, the FP32 master
+ * weights and AdamW stay FP32.  Either way sums run in a fixed order (the
+ * same batch gives the same update bit for bit); the Adam moments live in
+ * the model.
  * batch: host, n_seq x seqlen bytes, row-major; sequence b predicts its
  * bytes 1..seqlen-1 from their prefixes.  loss_out (host, may be NULL): the
  * loss before the update.  Blocks with an FFN (ffn_mult > 0) are not

@@ -816,12 +816,12 @@ static int tc_splits(int N, int K, int k_elems) {
 template <int BN, int EPI, int KIND, bool DEEP>
 static boa_status launch_tc_cfg(boa_model* m, dim3 grid, int splits, int chunks, const CUtensorMap& ta,
                                 const CUtensorMap& tb, const float* bias, float* C, __nv_bfloat16* outb, long long M,
-                                int N, int K, const float* rs, const float* cs) {
+                                int N, int K, const float* rs, const float* cs, int zpart = 0) {
     using L = TcSmem<BN, DEEP>;
     static SmemOptIn optin;
     TRY((smem_opt_in(optin, k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, (int)L::kBytes, m->device, "tensor-core gemm")));
     launch_k(m, k_gemm_tc_bf16<BN, EPI, KIND, DEEP>, grid, kTcThreads, L::kBytes, splits, ta, tb, bias, C, outb,
-             (int)M, N, K, m->err.p, rs, cs, chunks);
+             (int)M, N, K, m->err.p, rs, cs, chunks, zpart);
     return BOA_OK;
 }
 
@@ -859,6 +859,32 @@ static boa_status gemm_tc(boa_model* m, int cls, const __nv_bfloat16* A, const _
         default: TRY((launch_tc<128, EPI, kKindBF16>(m, ta, tb, bias, C, outb, M, N, K, nullptr, nullptr))); break;
     }
     return check_launch(m, "gemm_tc");
+}
+
+// Weight gradients of a BF16 model's training step on the tensor cores:
+// out[z][M][N] = sum over k in part z of A[m][k] B[n][k] (A [M][K], B [N][K]
+// BF16 rows, K = parts x the part length, a multiple of 64), every part's K
+// blocks accumulated in order by one CTA per output tile.  The caller adds
+// the parts in order (k_tr_reduce), so the result does not depend on the
+// grid.
+static boa_status gemm_tc_parts(boa_model* m, const __nv_bfloat16* A, const __nv_bfloat16* B, float* out, int M,
+                                int N, long long K, int parts) {
+    if (N % 4 != 0 || K % ((long long)parts * kTcBK) != 0)
+        return fail(BOA_ERR_FORMAT, "tensor-core gradient shape N=%d K=%lld parts=%d unsupported", N, K, parts);
+    const int BN = N >= 128 ? 128 : N > 48 ? 64 : 48;
+    CUtensorMap ta, tb;
+    TRY(tmap_2d(m, A, (uint64_t)M, (uint64_t)K, kTcBM, 2, &ta));
+    TRY(tmap_2d(m, B, (uint64_t)N, (uint64_t)K, (uint32_t)BN, 2, &tb));
+    const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kTcBM - 1) / kTcBM), (unsigned)parts);
+    switch (BN) {
+        case 48: TRY((launch_tc_cfg<48, kEpiStore, kKindBF16, false>(m, grid, 1, 1, ta, tb, nullptr, out, nullptr, M, N,
+                                                                     (int)K, nullptr, nullptr, 1))); break;
+        case 64: TRY((launch_tc_cfg<64, kEpiStore, kKindBF16, false>(m, grid, 1, 1, ta, tb, nullptr, out, nullptr, M, N,
+                                                                     (int)K, nullptr, nullptr, 1))); break;
+        default: TRY((launch_tc_cfg<128, kEpiStore, kKindBF16, false>(m, grid, 1, 1, ta, tb, nullptr, out, nullptr, M,
+                                                                      N, (int)K, nullptr, nullptr, 1))); break;
+    }
+    return check_launch(m, "gemm_tc_parts");
 }
 
 // FP8 projection: quantise the FP32 activation rows (one warp per row), then
@@ -2994,7 +3020,22 @@ struct TrainState {
     // shared by the backward
     DevBuf<float> logits, dlogits, loss_rows, loss, dX, dXin, dU, dCPRE, dXZ, dYG, dYS, dDELTA, dDPRE, dDBC, dDL,
         dXN, dyxh, dURES, hs, dA_part, dD_part, dB_part, dC_part, part;
+    // BF16 model: tensor-core operands (A rows, transposed A / B for the
+    // weight gradients, a transposed weight for the input gradients)
+    DevBuf<__nv_bfloat16> ab, tA, tB, wT;
+    size_t rows_pad = 0;             // row count of tA / tB, a multiple of kTrRowsPerPart
     uint64_t step = 0;
+    ~TrainState() {
+        for (auto* v : {&X, &XN, &mA, &rA, &XZ, &CPRE, &U, &DBC, &DPRE, &DELTA, &AN, &BM, &CM, &YS, &HIN, &YG, &URES,
+                        &mB, &rB})
+            for (auto& b : *v) b.release();
+        for (auto* b : {&master, &grad, &m1, &m2, &logits, &dlogits, &loss_rows, &loss, &dX, &dXin, &dU, &dCPRE, &dXZ,
+                        &dYG, &dYS, &dDELTA, &dDPRE, &dDBC, &dDL, &dXN, &dyxh, &dURES, &hs, &dA_part, &dD_part,
+                        &dB_part, &dC_part, &part})
+            b->release();
+        tok.release();
+        ab.release(); tA.release(); tB.release(); wT.release();
+    }
 };
 
 static void free_train_state(boa_model* m) {
@@ -3036,6 +3077,42 @@ static boa_status train_forward_backward(boa_model* m, int bsz, int T, int seqle
         k_tr_reduce<<<blocks(n, 256), 256, 0, st>>>(t.part.p, nparts, (size_t)n, out, 0, nullptr);
     };
     const unsigned warps_grid = blocks(rows, 8);   // one warp per row, 8 per CTA
+    // BF16 model: the projections (forward), the input gradients of in_proj,
+    // out_proj and the head, and the weight gradients of those three and
+    // x_proj run on the tensor cores with BF16 operands and FP32
+    // accumulation; dt_proj (K = r) and x_proj's input gradient (K = r + 2N)
+    // stay on the CUDA cores.  Their operands are written by the kernel just
+    // before them, so these launches go without programmatic dependent
+    // launch (each starts after its predecessor has finished).
+    const bool tc = m->precision == BOA_PREC_BF16;
+    const bool pdl_saved = m->pdl;
+    m->pdl = false;
+    m->v.stream = st;
+    struct PdlRestore { boa_model* m; bool v; ~PdlRestore() { m->pdl = v; } } pdl_restore{m, pdl_saved};
+    auto bf16 = [&](const float* src, size_t n) -> const __nv_bfloat16* {
+        k_tr_bf16<<<blocks((long long)n, 256), 256, 0, st>>>(src, t.ab.p, n);
+        return t.ab.p;
+    };
+    // dst [C][rows_pad] = bf16(src[rows][C])^T (src leading dimension lds)
+    auto bf16_t = [&](const float* src, int lds, int C, __nv_bfloat16* dst) {
+        k_tr_bf16_t<<<dim3((unsigned)(t.rows_pad / 32), blocks(C, 32)), dim3(32, 8), 0, st>>>(src, lds, rows, C,
+                                                                                                (long long)t.rows_pad, dst);
+    };
+    // BF16 W^T ([in][out]) of a master weight stored [out][in]
+    auto weight_t = [&](const float* w, int out, int in) -> const __nv_bfloat16* {
+        k_tr_bf16_t<<<dim3(blocks(out, 32), blocks(in, 32)), dim3(32, 8), 0, st>>>(w, in, out, in, out, t.wT.p);
+        return t.wT.p;
+    };
+    // G[Nn][Kk] = A^T B over all rows (A rows x Nn, B rows x Kk), by parts
+    auto tn_tc = [&](int Nn, int Kk, const float* A, int lda, const float* B, int ldb, float* out) -> boa_status {
+        bf16_t(A, lda, Nn, t.tA.p);
+        bf16_t(B, ldb, Kk, t.tB.p);
+        const int parts = (int)(t.rows_pad / kTrRowsPerPart);
+        TRY(gemm_tc_parts(m, t.tA.p, t.tB.p, t.part.p, Nn, Kk, (long long)t.rows_pad, parts));
+        const size_t cnt = (size_t)Nn * Kk;
+        k_tr_reduce<<<blocks((long long)cnt, 256), 256, 0, st>>>(t.part.p, parts, cnt, out, 0, nullptr);
+        return BOA_OK;
+    };
 
     // ---- forward
     k_tr_embed<<<blocks(rows * d, 256), 256, 0, st>>>(tok, T, seqlen, P + fo.embed, t.X[0].p, rows, d);
@@ -3044,10 +3121,14 @@ static boa_status train_forward_backward(boa_model* m, int bsz, int T, int seqle
         const DevLayer& L = m->layers[l];
         k_tr_ln_fwd<<<warps_grid, 256, 0, st>>>(t.X[l].p, P + o.ln_a_w, P + o.ln_a_b, t.XN[l].p, t.mA[l].p, t.rA[l].p,
                                                 rows, d);
-        nn((int)rows, 2 * E, d, t.XN[l].p, d, L.in_wt, 2 * E, t.XZ[l].p, 2 * E, nullptr, 0);
+        if (tc) TRY(gemm_tc<kEpiStore>(m, BOA_KC_GEMM_IN, bf16(t.XN[l].p, (size_t)rows * d), m->blayers[l].in_w,
+                                       nullptr, t.XZ[l].p, nullptr, rows, 2 * E, d));
+        else nn((int)rows, 2 * E, d, t.XN[l].p, d, L.in_wt, 2 * E, t.XZ[l].p, 2 * E, nullptr, 0);
         k_tr_conv_fwd<<<dim3(blocks(E, 128), bsz), 128, 0, st>>>(t.XZ[l].p, E, P + o.conv_w, P + o.conv_b,
                                                                   t.CPRE[l].p, t.U[l].p, T, K);
-        nn((int)rows, R2, E, t.U[l].p, E, L.x_wt, R2, t.DBC[l].p, R2, nullptr, 0);
+        if (tc) TRY(gemm_tc<kEpiStore>(m, BOA_KC_GEMM_X, bf16(t.U[l].p, (size_t)rows * E), m->blayers[l].x_w, nullptr,
+                                       t.DBC[l].p, nullptr, rows, R2, E));
+        else nn((int)rows, R2, E, t.U[l].p, E, L.x_wt, R2, t.DBC[l].p, R2, nullptr, 0);
         nn((int)rows, E, r, t.DBC[l].p, R2, L.dt_w, E, t.DPRE[l].p, E, P + o.dt_b, 0);
         k_tr_softplus<<<blocks(rows * E, 256), 256, 0, st>>>(t.DPRE[l].p, t.DELTA[l].p, (size_t)rows * E);
         k_tr_neg_exp<<<blocks((long long)E * N, 256), 256, 0, st>>>(P + o.A_log, t.AN[l].p, (size_t)E * N);
@@ -3056,19 +3137,30 @@ static boa_status train_forward_backward(boa_model* m, int bsz, int T, int seqle
             T, E, kTrainChunk, t.U[l].p, t.DELTA[l].p, t.AN[l].p, t.BM[l].p, t.CM[l].p, P + o.D, t.YS[l].p, t.HIN[l].p);
         k_tr_gate_fwd<<<blocks(rows * E, 256), 256, 0, st>>>(t.YS[l].p, t.XZ[l].p, E, t.YG[l].p, rows);
         CU(cudaMemcpyAsync(t.URES[l].p, t.X[l].p, (size_t)rows * d * 4, cudaMemcpyDeviceToDevice, st));
-        nn((int)rows, d, E, t.YG[l].p, E, L.out_wt, d, t.URES[l].p, d, nullptr, 1);
+        if (tc) TRY(gemm_tc<kEpiResid>(m, BOA_KC_GEMM_OUT, bf16(t.YG[l].p, (size_t)rows * E), m->blayers[l].out_w,
+                                       nullptr, t.URES[l].p, nullptr, rows, d, E));
+        else nn((int)rows, d, E, t.YG[l].p, E, L.out_wt, d, t.URES[l].p, d, nullptr, 1);
         k_tr_ln_fwd<<<warps_grid, 256, 0, st>>>(t.URES[l].p, P + o.ln_b_w, P + o.ln_b_b, t.X[l + 1].p, t.mB[l].p,
                                                 t.rB[l].p, rows, d);
     }
-    nn((int)rows, 256, d, t.X[nl].p, d, m->head_wt, 256, t.logits.p, 256, P + fo.head_b, 0);
+    if (tc) TRY(gemm_tc<kEpiBias>(m, BOA_KC_GEMM_HEAD, bf16(t.X[nl].p, (size_t)rows * d), m->head_wb, P + fo.head_b,
+                                  t.logits.p, nullptr, rows, 256, d));
+    else nn((int)rows, 256, d, t.X[nl].p, d, m->head_wt, 256, t.logits.p, 256, P + fo.head_b, 0);
     const float scale = (float)(1.0 / ((double)rows * std::log(256.0)));
     k_tr_xent<<<warps_grid, 256, 0, st>>>(t.logits.p, tok, T, seqlen, t.dlogits.p, t.loss_rows.p, rows, scale);
     k_tr_sum<<<1, kTrBlock, 0, st>>>(t.loss_rows.p, rows, t.loss.p);
 
     // ---- backward
-    tn(256, d, t.dlogits.p, 256, t.X[nl].p, d, G + fo.head_w);
+    if (tc) TRY(tn_tc(256, d, t.dlogits.p, 256, t.X[nl].p, d, G + fo.head_w));
+    else tn(256, d, t.dlogits.p, 256, t.X[nl].p, d, G + fo.head_w);
     colsum(t.dlogits.p, 256, 256, G + fo.head_b);
-    nn((int)rows, d, 256, t.dlogits.p, 256, P + fo.head_w, d, t.dX.p, d, nullptr, 0);
+    if (tc) {
+        const __nv_bfloat16* w = weight_t(P + fo.head_w, 256, d);
+        TRY(gemm_tc<kEpiStore>(m, BOA_KC_OTHER, bf16(t.dlogits.p, (size_t)rows * 256), w, nullptr, t.dX.p, nullptr,
+                               rows, d, 256));
+    } else {
+        nn((int)rows, d, 256, t.dlogits.p, 256, P + fo.head_w, d, t.dX.p, d, nullptr, 0);
+    }
     const int nblk = (E + kTrainThreads - 1) / kTrainThreads;
     for (int l = nl - 1; l >= 0; l--) {
         const auto& o = fo.layers[l];
@@ -3080,8 +3172,15 @@ static boa_status train_forward_backward(boa_model* m, int bsz, int T, int seqle
         // residual: the block input receives dURES directly
         CU(cudaMemcpyAsync(t.dXin.p, t.dURES.p, (size_t)rows * d * 4, cudaMemcpyDeviceToDevice, st));
         // out_proj
-        tn(d, E, t.dURES.p, d, t.YG[l].p, E, G + o.out_w);
-        nn((int)rows, E, d, t.dURES.p, d, P + o.out_w, E, t.dYG.p, E, nullptr, 0);
+        if (tc) {
+            TRY(tn_tc(d, E, t.dURES.p, d, t.YG[l].p, E, G + o.out_w));
+            const __nv_bfloat16* w = weight_t(P + o.out_w, d, E);
+            TRY(gemm_tc<kEpiStore>(m, BOA_KC_OTHER, bf16(t.dURES.p, (size_t)rows * d), w, nullptr, t.dYG.p, nullptr,
+                                   rows, E, d));
+        } else {
+            tn(d, E, t.dURES.p, d, t.YG[l].p, E, G + o.out_w);
+            nn((int)rows, E, d, t.dURES.p, d, P + o.out_w, E, t.dYG.p, E, nullptr, 0);
+        }
         // gate
         k_tr_gate_bwd<<<blocks(rows * E, 256), 256, 0, st>>>(t.dYG.p, t.YS[l].p, t.XZ[l].p, E, t.dYS.p, t.dXZ.p, rows);
         // scan
@@ -3099,7 +3198,8 @@ static boa_status train_forward_backward(boa_model* m, int bsz, int T, int seqle
         // x_proj
         k_tr_assemble_ddbc<<<blocks(rows * R2, 256), 256, 0, st>>>(t.dDL.p, t.dB_part.p, t.dC_part.p, nblk, r, N,
                                                                     t.dDBC.p, rows);
-        tn(R2, E, t.dDBC.p, R2, t.U[l].p, E, G + o.x_w);
+        if (tc) TRY(tn_tc(R2, E, t.dDBC.p, R2, t.U[l].p, E, G + o.x_w));
+        else tn(R2, E, t.dDBC.p, R2, t.U[l].p, E, G + o.x_w);
         nn((int)rows, E, R2, t.dDBC.p, R2, P + o.x_w, E, t.dU.p, E, nullptr, 1);
         // SiLU, conv
         k_tr_silu_bwd<<<blocks(rows * E, 256), 256, 0, st>>>(t.dU.p, t.CPRE[l].p, t.dCPRE.p, (size_t)rows * E);
@@ -3116,8 +3216,15 @@ static boa_status train_forward_backward(boa_model* m, int bsz, int T, int seqle
             CU(cudaMemcpy2DAsync(G + o.conv_b, 4, t.dDL.p + K, (size_t)(K + 1) * 4, 4, E, cudaMemcpyDeviceToDevice, st));
         }
         // in_proj
-        tn(2 * E, d, t.dXZ.p, 2 * E, t.XN[l].p, d, G + o.in_w);
-        nn((int)rows, d, 2 * E, t.dXZ.p, 2 * E, P + o.in_w, d, t.dXN.p, d, nullptr, 0);
+        if (tc) {
+            TRY(tn_tc(2 * E, d, t.dXZ.p, 2 * E, t.XN[l].p, d, G + o.in_w));
+            const __nv_bfloat16* w = weight_t(P + o.in_w, 2 * E, d);
+            TRY(gemm_tc<kEpiStore>(m, BOA_KC_OTHER, bf16(t.dXZ.p, (size_t)rows * 2 * E), w, nullptr, t.dXN.p, nullptr,
+                                   rows, d, 2 * E));
+        } else {
+            tn(2 * E, d, t.dXZ.p, 2 * E, t.XN[l].p, d, G + o.in_w);
+            nn((int)rows, d, 2 * E, t.dXZ.p, 2 * E, P + o.in_w, d, t.dXN.p, d, nullptr, 0);
+        }
         // LN_a (adds into the residual gradient of the block input)
         k_tr_ln_bwd<<<warps_grid, 256, 0, st>>>(t.dXN.p, t.X[l].p, t.mA[l].p, t.rA[l].p, P + o.ln_a_w, t.dXin.p,
                                                 t.dyxh.p, rows, d, 1);
@@ -3200,6 +3307,17 @@ static boa_status ensure_train_state(boa_model* m, int bsz, int T, int seqlen) {
     const size_t nparts = (rows + kTrRowsPerPart - 1) / kTrRowsPerPart;
     const size_t widest = std::max({2 * E * d, d * E, R2 * E, E * r, (size_t)256 * d, E * (K + 1), 2 * E, (size_t)256});
     TRY(t.part.ensure(nparts * widest));
+    if (!m->err.p) {                 // pipeline-timeout code of the tensor-core kernels
+        TRY(m->err.ensure(1));
+        CU(cudaMemset(m->err.p, 0, sizeof(int)));
+    }
+    if (m->precision == BOA_PREC_BF16) {
+        t.rows_pad = nparts * kTrRowsPerPart;
+        TRY(t.ab.ensure(rows * std::max<size_t>(2 * E, 256)));
+        TRY(t.tA.ensure(t.rows_pad * std::max<size_t>(2 * E, 256)));
+        TRY(t.tB.ensure(t.rows_pad * std::max(E, d)));
+        TRY(t.wT.ensure(std::max<size_t>(2 * E * d, (size_t)256 * d)));
+    }
     t.rows = std::max(t.rows, rows);
     return BOA_OK;
 }
@@ -3212,7 +3330,8 @@ static boa_status train_batch(boa_model* m, const uint8_t* batch, size_t n_seq, 
     const int bsz = (int)n_seq, T = (int)seqlen - 1;
     TRY(ensure_train_state(m, bsz, T, (int)seqlen));
     CU(cudaMemcpyAsync(m->tr->tok.p, batch, n_seq * seqlen, cudaMemcpyHostToDevice, m->stream));
-    return train_forward_backward(m, bsz, T, (int)seqlen);
+    TRY(train_forward_backward(m, bsz, T, (int)seqlen));
+    return m->precision == BOA_PREC_BF16 ? check_tc_error(m) : BOA_OK;
 }
 
 static boa_status read_loss(boa_model* m, size_t rows, float* loss_out) {

@@ -407,8 +407,8 @@ __device__ __forceinline__ void tc_epilogue(bool epi, bool bad, int* bad_flag, u
                                             float* __restrict__ Cm, __nv_bfloat16* __restrict__ out_bf16,
                                             float* stage, const float* __restrict__ row_scale = nullptr,
                                             const float* __restrict__ col_scale = nullptr, int chunks = 1,
-                                            int chunk_cols = 0) {
-    const int peers = (int)gridDim.z;
+                                            int chunk_cols = 0, int peers = -1) {
+    if (peers < 0) peers = (int)gridDim.z;
     if (peers == 1) {
         if (epi && !bad) {
             if (chunks > 1) tc_stage_tile_sum<BN>(tmem, q, lane, stage, chunks, chunk_cols);
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kTcThreads)
 k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const float* __restrict__ bias, float* __restrict__ Cm, __nv_bfloat16* __restrict__ out_bf16,
                int M, int N, int K, int* __restrict__ err, const float* __restrict__ row_scale,
-               const float* __restrict__ col_scale, int chunks) {
+               const float* __restrict__ col_scale, int chunks, int zpart) {
     constexpr int kElemK = KIND == kKindE4M3 ? 128 : kTcBK;    // elements per 128-byte stage row
     using L = TcSmem<BN, DEEP>;
     extern __shared__ uint8_t smem_raw[];
@@ -583,8 +583,12 @@ k_gemm_tc_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             mbar_wait(&full[kb % L::kStages], (kb / L::kStages) & 1);
         if (!finished) mbar_wait(&done[0], 0);
     }
+    // zpart: the z slices of the grid are independent parts of the K range,
+    // each written to its own [M][N] output (Cm + z M N), not split K
+    if (zpart) Cm += (size_t)blockIdx.z * M * N;
     tc_epilogue<BN, EPI>(true, bad, &bad_flag, tmem, warp, lane, m0, n0, M, N, bias, Cm, out_bf16,
-                         reinterpret_cast<float*>(smem), row_scale, col_scale, chunks, L::kTmemCols);
+                         reinterpret_cast<float*>(smem), row_scale, col_scale, chunks, L::kTmemCols,
+                         zpart ? 1 : (int)gridDim.z);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)

@@ -14,6 +14,8 @@
 // (r / T, r % T); its input byte is tok[b * seqlen + t], its target byte
 // tok[b * seqlen + t + 1] (seqlen = T + 1).
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace boa {
@@ -287,6 +289,37 @@ __global__ void k_tr_conv_wgrad(const float* __restrict__ dcpre, const float* __
     }
     float* out = part + (size_t)blockIdx.y * E * (K + 1) + (size_t)c * (K + 1);
     for (int k = 0; k <= K; k++) out[k] = s[k];
+}
+
+// BF16 operands of the tensor-core projections in a BF16 model's training
+// step (FP32 master weights; FP32 accumulation in the GEMMs).
+//
+// dst[i] = bf16(src[i]), round to nearest even.
+__global__ void k_tr_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// Transposed copy: dst[c][r] = bf16(src[r][c]) for r < R, c < C (src has
+// leading dimension lds); dst rows hold Rp >= R entries, zero from R on.
+// 32 x 32 tiles through shared memory, so both sides are coalesced; block
+// (32, 8), grid (Rp / 32, ceil(C / 32)).
+__global__ void k_tr_bf16_t(const float* __restrict__ src, int lds, long long R, int C, long long Rp,
+                            __nv_bfloat16* __restrict__ dst) {
+    __shared__ float tile[32][33];
+    const long long r0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const long long r = r0 + i;
+        const int c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < R && c < C) ? src[r * lds + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i;
+        const long long r = r0 + threadIdx.x;
+        if (c < C && r < Rp) dst[(size_t)c * Rp + r] = __float2bfloat16_rn(tile[threadIdx.x][i]);
+    }
 }
 
 // Elementwise pieces.
