@@ -3,7 +3,9 @@ Compression and Cross-Entropy Loss": minimising the base-256 cross-entropy
 minimises the code length).
 
 Two routes.  train_native drives the library's own training step
-(boa_train_step: forward, backward and AdamW in its kernels, FP32).  The
+(boa_train_step: forward, backward and AdamW in its kernels; FP32 on the
+CUDA cores, or for a model loaded in the BF16 form the projections and
+their gradients on the tensor cores with FP32 master weights).  The
 autograd route (TorchPredictor, train) runs the selective scan, forward and
 backward, in the library's hand-written kernels (boa_scan_train_fwd /
 boa_scan_train_bwd) behind a torch.autograd.Function, with states recomputed
@@ -165,17 +167,26 @@ def train(model: TorchPredictor, data: bytes, steps: int, batch: int = 64, seqle
 
 
 def train_native(path: str, data: bytes, steps: int, batch: int, seqlen: int, lr: float, seed: int = 0,
-                 log_every: int = 10):
+                 log_every: int = 10, precision: int = 0, epochs: int = 0):
     """The same loop through the library's own training step (boa_train_step:
     forward, backward and AdamW all in its kernels); returns the model and
-    [(step, loss), ...]."""
+    [(step, loss), ...].  With epochs > 0 the batches walk a shuffled order of
+    the non-overlapping seqlen-byte windows of data, every window once per
+    epoch (steps is then epochs x windows / batch); otherwise each batch
+    draws window starts at random."""
     from . import api
-    m = api.Model(path)
+    m = api.Model(path, precision=precision)
     buf = np.frombuffer(data, np.uint8)
     g = np.random.Generator(np.random.PCG64(seed))
+    order = []
+    if epochs > 0:
+        n_win = len(buf) // seqlen
+        for _ in range(epochs):
+            order.extend((g.permutation(n_win) * seqlen).tolist())
+        steps = len(order) // batch
     hist = []
     for step in range(steps):
-        starts = g.integers(0, len(buf) - seqlen, batch)
+        starts = order[step * batch:(step + 1) * batch] if epochs > 0 else g.integers(0, len(buf) - seqlen, batch)
         loss = m.train_step(np.stack([buf[s:s + seqlen] for s in starts]), lr)
         if step % log_every == 0 or step == steps - 1:
             hist.append((step, loss))
@@ -199,8 +210,15 @@ def main():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--seqlen", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--epochs", type=int, default=0,
+                    help="native route: passes over every window of the training set (overrides --steps)")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
+                    help="native route: the training step's arithmetic (bf16: tensor-core projections)")
+    ap.add_argument("--eval-precision", choices=["fp32", "tf32x3", "bf16", "fp8"], default="tf32x3",
+                    help="the form that compresses the held-out data with the trained weights")
     ap.add_argument("--out", default="")
     args = ap.parse_args()
+    prec = {"fp32": api.PREC_FP32, "tf32x3": api.PREC_TF32X3, "bf16": api.PREC_BF16, "fp8": api.PREC_FP8}
     shape = synth.PAPER_SCALE
     n_train = int(args.train_mb * 1e6)
     stream = synth.cms_records(n_train + int(args.heldout_mb * 1e6), seed=5000)
@@ -211,7 +229,9 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if args.route == "native":
-        nm, hist = train_native(init, train_data, args.steps, args.batch, args.seqlen, args.lr)
+        nm, hist = train_native(init, train_data, args.steps, args.batch, args.seqlen, args.lr,
+                                precision=prec[args.precision], epochs=args.epochs)
+        args.steps = hist[-1][0] + 1
         nm.save(path)
     else:
         model = TorchPredictor(shape, synth.init_weights(shape, seed=2)).cuda()
@@ -219,7 +239,7 @@ def main():
         model.save(path)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    m = api.Model(path)
+    m = api.Model(path, precision=prec[args.eval_precision])
     streams = synth.split_equal(held, max(1, len(held) // 16384))
     flat, in_off = api.pack(streams)
     lens = np.diff(in_off)
@@ -237,7 +257,9 @@ def main():
     ok = bool(torch.equal(d_dec, d_in))
     total = int(len(flat))
     tokens = args.steps * args.batch * (args.seqlen - 1)
-    print(json.dumps({"route": args.route, "train_steps": args.steps, "train_s": t_train,
+    print(json.dumps({"route": args.route, "precision": args.precision, "epochs": args.epochs,
+                      "train_bytes": n_train, "eval_precision": args.eval_precision,
+                      "train_steps": args.steps, "train_s": t_train,
                       "train_tokens_per_s": tokens / t_train, "loss_bytes_per_byte": hist,
                       "heldout_bytes": total, "compressed_bytes": int(sizes.sum()),
                       "compression_ratio": total / int(sizes.sum()), "compress_MBps": total / 1e6 / t_c,
