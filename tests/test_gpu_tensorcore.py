@@ -196,6 +196,27 @@ def test_tf32x3_paper_scale(api, model_dir):
     assert np.abs(m.logprobs(streams[3][:400]) - om.logprobs(streams[3][:400])).max() <= 1e-3
 
 
+def test_tf32x3_paper_scale_lockstep(api, model_dir):
+    """The benchmark model's shape in the 3xTF32 form: the encoder's
+    (compression-size tiles, in-CTA chunks) and the decoder's (decode-size
+    tiles, cluster split K) per-step CDFs are identical, with one and with
+    two decode lanes."""
+    path = synth.make_model_file(os.path.join(model_dir, "paper_t3l.boaw"), synth.PAPER_SCALE, seed=3)
+    m = api.Model(path, precision=api.PREC_TF32X3)
+    streams = synth.split_equal(synth.atlas_workload(300, 700, seed=79), 300) + [b"", b"x", b"ab"]
+    n_steps = sum(max(len(s) - 1, 0) for s in streams)
+    m.enable_cdf_trace(True)
+    try:
+        comp = m.compress(streams)
+        enc = m.read_cdf_trace(n_steps)
+        for lanes in (1, 2):
+            m.set_tuning(1 << 18, 0, lanes)
+            assert m.decompress(comp, [len(s) for s in streams]) == streams
+            assert np.array_equal(m.read_cdf_trace(n_steps), enc), lanes
+    finally:
+        m.enable_cdf_trace(False)
+
+
 # ------------------------------------------------------------------ FP8 E4M3
 
 def e4m3_quant_rows(X):
