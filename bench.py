@@ -550,9 +550,19 @@ def run_boa(args):
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "kernel": name, "peak_source": f"hbm_gbs ({peak_src})"}
         tr = traffic_for(f"{dom[0]}:{dom[1]}")
-        roof["traffic"] = tr["bytes_per_launch"] if tr else None
         roof["avg_launch_ms"] = p["ms"] / p["launches"]
         roof["algorithmic_per_launch"] = (p["flops"] if dom[1].startswith("gemm") else p["bytes"]) / p["launches"]
+        roof["traffic"] = tr["bytes_per_launch"] if tr else None
+        if tr and tr.get("algorithmic_per_launch"):
+            # the capture's launch may process another number of slots: its
+            # DRAM bytes scaled by the ratio of algorithmic bytes (the state
+            # traffic grows in proportion to the slots)
+            scale = roof["algorithmic_per_launch"] / tr["algorithmic_per_launch"]
+            if abs(scale - 1.0) > 1e-6:
+                roof["traffic"] = tr["bytes_per_launch"] * scale
+                roof["traffic_scaled_from"] = {"bytes_per_launch": tr["bytes_per_launch"],
+                                               "algorithmic_per_launch": tr["algorithmic_per_launch"],
+                                               "scale": scale}
     if roof is not None and world == 1:
         try:
             up = unit_peaks(local)

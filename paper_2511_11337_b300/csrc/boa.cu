@@ -2081,25 +2081,30 @@ extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream
         return timed([&] { return decompress_impl(m, n, dout.p, out_off.data(), sizes.data(), lens.data(), ddec.p,
                                                   in_off.data()); }, ms);
     };
-    m->decode_lanes = 1;
+    // Scan variants under the automatic lane count (decode_lanes 0: two
+    // lanes from 2048 slots), then other lane counts, which replace it only
+    // when they win clearly on the short sample: a few hundred steps cannot
+    // resolve a difference of a few per cent, and the automatic rule is the
+    // one measured best at full length on the 64 MiB jet table (decoding 2
+    // lanes 4779 ms, 3 lanes 4822 ms, 4 lanes 4930 ms, 1 lane about 20 %
+    // slower).
+    m->decode_lanes = 0;
+    best.decode_lanes = 0;
     for (int g = 0; g < 4; g++) {
         if (st != BOA_OK) break;
         m->scan_variant = g;
         double ms = 0;
         st = time_decode(ms);
-        if (st == BOA_OK && ms < best.decompress_ms) { best.decompress_ms = ms; best.scan_variant = g; best.decode_lanes = 1; }
+        if (st == BOA_OK && ms < best.decompress_ms) { best.decompress_ms = ms; best.scan_variant = g; }
     }
     m->scan_variant = best.scan_variant;
-    // More lanes are taken only when they win clearly on the short sample:
-    // a few hundred steps cannot resolve a 1-2 % difference, and at full
-    // length extra lanes contend for the SMs (measured on the 64 MiB jet
-    // table: 2 lanes 4779 ms, 3 lanes 4822 ms, 4 lanes 4930 ms of decoding).
-    for (int p : {2, 4}) {
-        if (st != BOA_OK || (size_t)p > n) break;
+    for (int p : {1, 2, 4}) {
+        if (st != BOA_OK || (size_t)p > n || p == decode_lanes(m, (int)n)) continue;
         m->decode_lanes = p;
         double ms = 0;
         st = time_decode(ms);
-        if (st == BOA_OK && ms < 0.97 * best.decompress_ms) { best.decompress_ms = ms; best.decode_lanes = p; }
+        if (st == BOA_OK && ms < 0.95 * best.decompress_ms) { best.decompress_ms = ms; best.decode_lanes = p; }
+        m->decode_lanes = 0;
     }
     m->decode_lanes = best.decode_lanes;
     m->prof_on = prof;
