@@ -42,7 +42,7 @@ UNIT = "MB/s"
 N_STREAMS, STREAM_LEN = 4096, 16384
 WORKLOAD = "ATLAS-like jet table, 64 MiB as 4096 x 16 KB streams; Mamba d_model=256, 3 layers, d_state=16, expand=2 (1.45 M params)"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-PREC = {"fp32": 0, "bf16": 1, "tf32x3": 2, "fp8": 3}
+PREC = {"fp32": 0, "bf16": 1, "tf32x3": 2, "fp8": 3, "fp32_onchip": 0}
 
 
 def shard_range(n: int, rank: int, world: int) -> tuple[int, int]:
@@ -287,7 +287,16 @@ def run_reference(args):
 # ---------------------------------------------------------------- precision forms
 
 FORM_DESC = {"fp32": "plain FP32 on the CUDA cores", "tf32x3": "FP32-accurate 3xTF32 on the tensor cores",
-             "bf16": "BF16 projections on the tensor cores", "fp8": "FP8 E4M3 projections on the tensor cores"}
+             "bf16": "BF16 projections on the tensor cores", "fp8": "FP8 E4M3 projections on the tensor cores",
+             "fp32_onchip": "plain FP32 on the CUDA cores; decompression by the on-chip persistent decoder "
+                            "(one CTA per SM, two streams each, SSM state and conv windows in tensor memory)"}
+
+
+def set_decoder(m, form):
+    """The step-kernel decoder (model state in HBM) for every form but
+    fp32_onchip, which takes the on-chip persistent decoder."""
+    t = m.tuning()
+    m.set_tuning(t["max_rows"], t["scan_variant"], t["decode_lanes"], decoder=int(form == "fp32_onchip"))
 
 
 def form_accuracy(streams, forms, path, n_lp=4, lp_len=256, n_gap=16, gap_len=2048):
@@ -306,6 +315,7 @@ def form_accuracy(streams, forms, path, n_lp=4, lp_len=256, n_gap=16, gap_len=20
     out = {}
     for f in forms:
         m = api.Model(path, precision=PREC[f])
+        set_decoder(m, f)
         err = max(float(np.abs(m.logprobs(s) - r).max()) for s, r in zip(lp_in, lp_ref))
         comp = m.compress(gap_in)
         lossless = m.decompress(comp, [len(s) for s in gap_in]) == gap_in
@@ -326,6 +336,7 @@ def form_speed(form, path, d_in, in_off, d_out, out_off, d_dec, lens, stream, au
     m = api.Model(path, cuda_stream=stream.cuda_stream, precision=PREC[form])
     if autotune:
         m.autotune(len(lens), int(max(lens)))
+    set_decoder(m, form)
     total = int(in_off[-1])
     tcs, tds, lossless = [], [], True
     for k in range(1 + timed):
@@ -442,7 +453,7 @@ def run_boa(args):
     if args.decode_lanes is not None or args.scan_variant is not None:
         t = model.tuning()
         model.set_tuning(t["max_rows"], t["scan_variant"] if args.scan_variant is None else args.scan_variant,
-                         t["decode_lanes"] if args.decode_lanes is None else args.decode_lanes)
+                         t["decode_lanes"] if args.decode_lanes is None else args.decode_lanes, t["decoder"])
         tuning = dict(tuning or {}, **model.tuning(), overridden=True)
     for _ in range(args.warmup):
         step()
@@ -717,7 +728,9 @@ def main():
     ap.add_argument("--set-chunks", type=int, default=1024, help="chunks per streaming set (--workload stream)")
     ap.add_argument("--max-rows", type=int, default=0)
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "bf16", "tf32x3", "fp8"])
-    ap.add_argument("--forms", default="fp32,bf16,fp8", help="other precision forms to report ('' for none)")
+    ap.add_argument("--forms", default="fp32,fp32_onchip,bf16,fp8",
+                    help="other precision forms to report ('' for none); fp32_onchip: the FP32 form decoded by "
+                         "the on-chip persistent decoder")
     ap.add_argument("--report", default="", choices=["", "precision"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--decode-lanes", type=int, default=None, help="override the tuned decode lane count")

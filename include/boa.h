@@ -202,13 +202,21 @@ typedef struct {
                                (0 = automatic: 2 from 2048 slots, else 1) */
     double compress_ms;     /* estimated time for the whole workload */
     double decompress_ms;
+    int decoder;            /* decompression: 0 = one launch sequence per step, model state
+                               in HBM (every form); 1 = the on-chip persistent decoder
+                               (FP32 form; models of at most 3 blocks without FFN,
+                               d_state 16, d_inner <= 512): one launch, one CTA per SM
+                               decoding two streams at a time from first to last byte,
+                               their SSM state and conv windows in the SM's tensor memory
+                               across layers and steps (Alg. 1; App. B: O(1) state per
+                               stream).  Both give the same bytes. */
 } boa_tuning;
 
 /* Time candidate launch configurations on a synthetic batch shaped like the
  * caller's workload (n_streams streams of stream_len bytes; a 512-byte sample
  * of each is run) and keep the fastest in the model: the compression chunk
- * size (max_rows in 2^16 .. 2^19), the decode scan kernel (scan_variant)
- * and the decode lanes (1, 2 or 4).  No knob changes any result: rows are
+ * size (max_rows in 2^16 .. 2^19), the decode scan kernel (scan_variant),
+ * the decode lanes (1, 2 or 4) and, where it runs, the on-chip decoder.  No knob changes any result: rows are
  * computed the same way whatever the chunking, kernel or lane split.  out (host, may be NULL) receives
  * the choice and the extrapolated times.  Allocates and frees a scratch
  * batch on the device.  Errors: BOA_ERR_ARG, BOA_ERR_CUDA, BOA_ERR_OOM. */
@@ -216,8 +224,10 @@ boa_status boa_autotune(boa_model* model, size_t n_streams, size_t stream_len, b
 
 /* Apply a launch configuration (for instance one saved from an earlier
  * boa_autotune): max_rows in 1 .. 2^24, scan_variant in 0 .. 3,
- * decode_lanes in 0 .. 16; the _ms fields are ignored.  Results do not
- * depend on it.  Errors: BOA_ERR_ARG. */
+ * decode_lanes in 0 .. 16, decoder 0 or 1 (1 only where the model and form
+ * allow it); the _ms fields are ignored.  Results do not depend on it.
+ * Errors: BOA_ERR_ARG (out of range, or decoder 1 on a model or form it
+ * does not run; boa_last_error says why). */
 boa_status boa_set_tuning(boa_model* model, const boa_tuning* tuning);
 
 /* The configuration in use (host out; the _ms fields are zero). */

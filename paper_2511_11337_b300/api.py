@@ -34,7 +34,7 @@ class _Opts(C.Structure):
 
 class _Tuning(C.Structure):
     _fields_ = [("max_rows", C.c_size_t), ("scan_variant", C.c_int), ("decode_lanes", C.c_int), ("compress_ms", C.c_double),
-                ("decompress_ms", C.c_double)]
+                ("decompress_ms", C.c_double), ("decoder", C.c_int)]
 
 
 class Model:
@@ -159,7 +159,7 @@ class Model:
         t = _Tuning()
         check(load().boa_autotune(self._h, n_streams, stream_len, C.byref(t)))
         return {"max_rows": int(t.max_rows), "scan_variant": int(t.scan_variant),
-                "decode_lanes": int(t.decode_lanes), "compress_ms_est": t.compress_ms,
+                "decode_lanes": int(t.decode_lanes), "decoder": int(t.decoder), "compress_ms_est": t.compress_ms,
                 "decompress_ms_est": t.decompress_ms}
 
     # ----------------------------------------------------------- training
@@ -187,9 +187,10 @@ class Model:
         """boa_save_model: write the current weights as a weight file."""
         check(load().boa_save_model(self._h, os.fsencode(path)))
 
-    def set_tuning(self, max_rows: int, scan_variant: int, decode_lanes: int = 0) -> None:
-        """boa_set_tuning: apply a launch configuration (results do not depend on it)."""
-        t = _Tuning(max_rows, scan_variant, decode_lanes, 0.0, 0.0)
+    def set_tuning(self, max_rows: int, scan_variant: int, decode_lanes: int = 0, decoder: int = 0) -> None:
+        """boa_set_tuning: apply a launch configuration (results do not depend on it).
+        decoder 1: the on-chip persistent decoder (FP32 form)."""
+        t = _Tuning(max_rows, scan_variant, decode_lanes, 0.0, 0.0, decoder)
         check(load().boa_set_tuning(self._h, C.byref(t)))
 
     def tuning(self) -> dict:
@@ -197,7 +198,7 @@ class Model:
         t = _Tuning()
         check(load().boa_get_tuning(self._h, C.byref(t)))
         return {"max_rows": int(t.max_rows), "scan_variant": int(t.scan_variant),
-                "decode_lanes": int(t.decode_lanes)}
+                "decode_lanes": int(t.decode_lanes), "decoder": int(t.decoder)}
 
     # ----------------------------------------------------------- benchmark hooks
     KERNEL_CLASSES = ["embed_ln", "gemm_in_proj", "conv_silu", "gemm_x_proj", "scan", "gemm_out_proj",

@@ -34,6 +34,7 @@
 #include "gemm_tc.cuh"
 #include "kernels.cuh"
 #include "scan_step.cuh"
+#include "decode_onchip.cuh"
 #include "scan_train.cuh"
 #include "peaks.cuh"
 #include "train_step.cuh"
@@ -212,6 +213,8 @@ struct boa_model {
     bool use_graphs = true;         // decode step loop as CUDA graphs (when not profiling)
     int scan_variant = 0;           // decode-step scan kernel (see scan())
     int decode_lanes = 0;           // independent slot groups per decode step (0 = automatic)
+    int decoder = 0;                // 0: step kernels, state in HBM; 1: on-chip persistent decoder
+    DevBuf<int> oc_next;            // the on-chip decoder's queue head
     bool pdl = true;                // chain kernels with programmatic dependent launch
     size_t kp8 = 0;                 // row stride of the FP8 activation scratch
 
@@ -950,11 +953,29 @@ static boa_status launch_t3_cfg(boa_model* m, dim3 grid, int splits, int chunks,
     return BOA_OK;
 }
 
+// Compression-size projections with 128-wide tiles and no split K (in_proj,
+// out_proj, the head at more than two tiles per SM): one persistent CTA per
+// SM, whose epilogue of one tile overlaps the main loop of the next (same
+// MMAs and epilogue per tile, so the same bits as k_gemm_tc_tf32x3).
+template <int EPI>
+static boa_status launch_t3_persist(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th,
+                                    const CUtensorMap& tl, const float* bias, float* C, long long M, int N, int K,
+                                    long long tiles) {
+    static SmemOptIn optin;
+    TRY((smem_opt_in(optin, k_gemm_t3_persist<EPI>, (int)T3P::kBytes, m->device, "persistent 3xTF32 gemm")));
+    const dim3 grid((unsigned)std::min<long long>(tiles, m->num_sms));
+    launch_k(m, k_gemm_t3_persist<EPI>, grid, T3P::kThreads, T3P::kBytes, 1, ta, th, tl, bias, C, (int)M, N, K,
+             m->err.p);
+    return BOA_OK;
+}
+
 template <int BN, int EPI>
 static boa_status launch_t3(boa_model* m, const CUtensorMap& ta, const CUtensorMap& th, const CUtensorMap& tl,
                             const float* bias, float* C, long long M, int N, int K) {
     dim3 grid((N + BN - 1) / BN, (unsigned)((M + kTcBM - 1) / kTcBM));
     const int split = tc_splits(N, K, kT3BK);
+    if (BN == T3P::BN && split == 1 && (long long)grid.x * grid.y >= 2LL * m->num_sms)
+        return launch_t3_persist<EPI>(m, ta, th, tl, bias, C, M, N, K, (long long)grid.x * grid.y);
     const bool in_cta = (long long)grid.x * grid.y >= m->num_sms;
     // in-CTA chunks while the CTA's TMEM (accumulators + A stages) still
     // leaves room for the second CTA an SM holds
@@ -1226,7 +1247,7 @@ static boa_status check_tc_error(boa_model* m) {
     if (h) {
         cudaMemsetAsync(m->err.p, 0, sizeof(int), m->stream);
         return fail(BOA_ERR_CUDA, "a pipeline wait on the device timed out (code %d: %s)", h,
-                    h == 3 ? "decode scan bulk copy" : "tensor-core GEMM");
+                    h == 3 ? "decode scan bulk copy" : h == 4 ? "on-chip decoder weight stream" : "tensor-core GEMM");
     }
     return BOA_OK;
 }
@@ -1536,6 +1557,125 @@ static void launch_decode(boa_model* m, int S, const uint8_t* cin, const StreamT
              (const int*)m->sched.p, m->v.slot_beg, m->v.slots, m->v.st, cin, tb, out, ne, mem);
 }
 
+// After a decompression's launches: per-stream status back to the host,
+// profiling totals folded in, device-side wait failures and streams that did
+// not decode cleanly reported.
+static boa_status finish_decode(boa_model* m, size_t n) {
+    TRY(m->h_u32.ensure(n));
+    CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, n * 4, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    prof_collect(m);
+    m->last_status.assign(m->h_u32.p, m->h_u32.p + n);
+    TRY(check_tc_error(m));
+    for (size_t i = 0; i < n; i++)
+        if (m->h_u32.p[i]) return fail(BOA_ERR_CORRUPT, "stream %zu did not decode cleanly (flags %u)", i, m->h_u32.p[i]);
+    return BOA_OK;
+}
+
+// Why the on-chip decoder cannot run this model (nullptr: it can).  Its
+// state layout holds kOcSlots streams' SSM state and conv windows for up to
+// kOcMaxLayers blocks in TMEM, and its weight stream covers the Mamba blocks
+// without an FFN.
+static const char* onchip_unsupported(const boa_model* m) {
+    if (m->precision != BOA_PREC_FP32) return "it runs the FP32 form only";
+    if (m->N != kOcNS) return "d_state must be 16";
+    if (m->E > kOcMaxE || m->E % 4) return "d_inner must be a multiple of 4, at most 512";
+    if (m->nl > kOcMaxLayers) return "at most 3 blocks";
+    if (m->F) return "blocks with an FFN are not supported";
+    if (m->K < 2 || m->K > 4) return "conv width must be 2 .. 4";
+    if (m->r != 4 && m->r != 8 && m->r != 16) return "dt_rank must be 4, 8 or 16";
+    if (!supported_d(m->d)) return "d_model must be 64, 128 or 256";
+    if (oc_smem_bytes(m->d, m->E) > 227 * 1024) return "activations do not fit shared memory";
+    auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    if (!al(m->head_wt)) return "weight matrices must be 16-byte aligned";
+    for (const DevLayer& L : m->layers)
+        if (!al(L.in_wt) || !al(L.x_wt) || !al(L.out_wt)) return "weight matrices must be 16-byte aligned";
+    return nullptr;
+}
+
+template <int VPT, int R>
+static boa_status launch_onchip(boa_model* m, const OcModel& M, const OcWork& W, int grid) {
+    static SmemOptIn optin;
+    const size_t smem = oc_smem_bytes(m->d, m->E);
+    TRY((smem_opt_in(optin, k_decode_onchip<VPT, R>, (int)smem, m->device, "on-chip decoder")));
+    launch_k(m, k_decode_onchip<VPT, R>, dim3((unsigned)grid), dim3(kOcBlock), smem, 1, M, W);
+    return BOA_OK;
+}
+
+// Decompression by the on-chip persistent decoder: one launch decodes every
+// stream of two bytes or more (longest first from a device-side queue, one
+// CTA per SM with kOcSlots streams at a time); streams of 0 or 1 bytes as in
+// decompress_impl.
+static boa_status decompress_onchip(boa_model* m, size_t n, const uint8_t* d_in, const uint64_t* in_off,
+                                    const uint64_t* csz, const uint64_t* lens, uint8_t* d_out,
+                                    const uint64_t* out_off) {
+    if (const char* why = onchip_unsupported(m)) return fail(BOA_ERR_ARG, "on-chip decoder: %s", why);
+    m->launches = 0;
+    m->prof_phase = 1;
+    TRY(ensure_workspace(m, 1, 1));
+    TRY(ensure_streams(m, n));
+    TRY(upload_index(m, n, in_off, out_off, lens, csz));
+    bind_view(m, 0, 1, 1, m->stream);
+    StreamTable tb = stream_table(m, true);
+    const int tb128 = 128;
+    k_dec_trivial<<<(unsigned)((n + tb128 - 1) / tb128), tb128, 0, m->stream>>>((int)n, d_in, tb, d_out);
+    TRY(check_launch(m, "dec_trivial"));
+    std::vector<int> order;
+    uint64_t steps = 0;
+    for (size_t i = 0; i < n; i++)
+        if (lens[i] >= 2) {
+            order.push_back((int)i);
+            steps += lens[i] - 1;
+        }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lens[a] > lens[b]; });
+    if (!order.empty()) {
+        TRY(m->h_sched.ensure(order.size()));
+        memcpy(m->h_sched.p, order.data(), order.size() * sizeof(int));
+        CU(cudaMemcpyAsync(m->sched.p, m->h_sched.p, order.size() * sizeof(int), cudaMemcpyHostToDevice, m->stream));
+        TRY(m->oc_next.ensure(1));
+        CU(cudaMemsetAsync(m->oc_next.p, 0, sizeof(int), m->stream));
+        OcModel M{};
+        for (int l = 0; l < m->nl; l++) {
+            const DevLayer& L = m->layers[l];
+            M.L[l] = OcLayer{L.in_wt, L.x_wt, L.out_wt, L.conv_w, L.conv_b, L.dt_w, L.dt_b, L.A2, L.D,
+                             L.ln_a_w, L.ln_a_b, L.ln_b_w, L.ln_b_b};
+        }
+        M.embed = m->embed;
+        M.head_wt = m->head_wt;
+        M.head_b = m->head_b;
+        M.nl = m->nl;
+        M.E = m->E;
+        M.K = m->K;
+        const OcWork W{m->sched.p, (int)order.size(), m->oc_next.p, d_in, tb, d_out, m->err.p};
+        const int grid = (int)std::min<size_t>((size_t)m->num_sms, (order.size() + kOcSlots - 1) / kOcSlots);
+        m->prof_step = true;
+        m->prof_steps[1][0] += steps;
+        m->prof_steps[1][1] += steps;
+        {
+            // per decoded byte: the projections (2 flops per weight) and the
+            // weight bytes one CTA streams per step, shared by its slots
+            const double wfloats = (double)m->nl * (2.0 * m->E * m->d + (double)m->E * m->R2 + (double)m->E * m->d) +
+                                   256.0 * m->d;
+            ProfScope ps(m, BOA_KC_DECODE, 2.0 * wfloats * (double)steps, 4.0 * wfloats * (double)steps / kOcSlots);
+            boa_status st = BOA_OK;
+            switch (m->d * 100 + m->r) {
+                case 6404: st = launch_onchip<2, 4>(m, M, W, grid); break;
+                case 6408: st = launch_onchip<2, 8>(m, M, W, grid); break;
+                case 6416: st = launch_onchip<2, 16>(m, M, W, grid); break;
+                case 12804: st = launch_onchip<4, 4>(m, M, W, grid); break;
+                case 12808: st = launch_onchip<4, 8>(m, M, W, grid); break;
+                case 12816: st = launch_onchip<4, 16>(m, M, W, grid); break;
+                case 25604: st = launch_onchip<8, 4>(m, M, W, grid); break;
+                case 25608: st = launch_onchip<8, 8>(m, M, W, grid); break;
+                default: st = launch_onchip<8, 16>(m, M, W, grid); break;
+            }
+            TRY(st);
+        }
+        TRY(check_launch(m, "decode_onchip"));
+    }
+    return finish_decode(m, n);
+}
+
 static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, const uint64_t* in_off,
                                   const uint64_t* in_sizes, const uint64_t* lens, uint8_t* d_out,
                                   const uint64_t* out_off) {
@@ -1549,6 +1689,7 @@ static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, c
         if (out_off[i + 1] - out_off[i] < lens[i]) return fail(BOA_ERR_OUTPUT_TOO_SMALL, "stream %zu: output slot too small", i);
         if (lens[i] >= 2 && csz[i] < 1) return fail(BOA_ERR_CORRUPT, "stream %zu: empty coded stream", i);
     }
+    if (m->decoder == 1) return decompress_onchip(m, n, d_in, in_off, csz.data(), lens, d_out, out_off);
     m->launches = 0;
     m->prof_phase = 1;
     Schedule sc;
@@ -1683,15 +1824,7 @@ static boa_status decompress_impl(boa_model* m, size_t n, const uint8_t* d_in, c
         m->prof_step = true;
     }
     bind_view(m, 0, 1, S, m->stream);
-    TRY(m->h_u32.ensure(n));
-    CU(cudaMemcpyAsync(m->h_u32.p, m->flags.p, n * 4, cudaMemcpyDeviceToHost, m->stream));
-    CU(cudaStreamSynchronize(m->stream));
-    prof_collect(m);
-    m->last_status.assign(m->h_u32.p, m->h_u32.p + n);
-    TRY(check_tc_error(m));
-    for (size_t i = 0; i < n; i++)
-        if (m->h_u32.p[i]) return fail(BOA_ERR_CORRUPT, "stream %zu did not decode cleanly (flags %u)", i, m->h_u32.p[i]);
-    return BOA_OK;
+    return finish_decode(m, n);
 }
 
 // ------------------------------------------------------------ public API
@@ -2016,16 +2149,20 @@ extern "C" boa_status boa_set_tuning(boa_model* m, const boa_tuning* t) {
     if (t->max_rows < 1 || t->max_rows > (1u << 24)) return fail(BOA_ERR_ARG, "max_rows %zu out of range", t->max_rows);
     if (t->scan_variant < 0 || t->scan_variant > 3) return fail(BOA_ERR_ARG, "scan_variant %d out of range", t->scan_variant);
     if (t->decode_lanes < 0 || t->decode_lanes > 16) return fail(BOA_ERR_ARG, "decode_lanes %d out of range", t->decode_lanes);
+    if (t->decoder < 0 || t->decoder > 1) return fail(BOA_ERR_ARG, "decoder %d out of range", t->decoder);
+    if (t->decoder == 1)
+        if (const char* why = onchip_unsupported(m)) return fail(BOA_ERR_ARG, "on-chip decoder: %s", why);
     m->max_rows = t->max_rows;
     m->scan_variant = t->scan_variant;
     m->decode_lanes = t->decode_lanes;
+    m->decoder = t->decoder;
     return BOA_OK;
 }
 
 extern "C" boa_status boa_get_tuning(const boa_model* m, boa_tuning* out) {
     if (!m || !out) return fail(BOA_ERR_ARG, "null argument");
     MODEL_LOCK(m);
-    *out = boa_tuning{m->max_rows, m->scan_variant, m->decode_lanes, 0.0, 0.0};
+    *out = boa_tuning{m->max_rows, m->scan_variant, m->decode_lanes, 0.0, 0.0, m->decoder};
     return BOA_OK;
 }
 
@@ -2067,7 +2204,8 @@ extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream
         return BOA_OK;
     };
     boa_status st = BOA_OK;
-    boa_tuning best{m->max_rows, m->scan_variant, m->decode_lanes, 1e30, 1e30};
+    boa_tuning best{m->max_rows, m->scan_variant, m->decode_lanes, 1e30, 1e30, 0};
+    m->decoder = 0;
     const size_t rows_cand[] = {1u << 16, 1u << 17, 1u << 18, 1u << 19};
     for (size_t r : rows_cand) {
         if (st != BOA_OK) break;
@@ -2107,6 +2245,15 @@ extern "C" boa_status boa_autotune(boa_model* m, size_t n_streams, size_t stream
         m->decode_lanes = 0;
     }
     m->decode_lanes = best.decode_lanes;
+    // the on-chip persistent decoder, where the model and form allow it,
+    // under the same rule
+    if (st == BOA_OK && !onchip_unsupported(m)) {
+        m->decoder = 1;
+        double ms = 0;
+        st = time_decode(ms);
+        if (st == BOA_OK && ms < 0.95 * best.decompress_ms) { best.decompress_ms = ms; best.decoder = 1; }
+    }
+    m->decoder = best.decoder;
     m->prof_on = prof;
     cudaEventDestroy(a);
     cudaEventDestroy(b);

@@ -209,11 +209,14 @@ struct TileLayout {
     static constexpr int kRowsPerIter = 32 / kLaneSlots;        // rows one warp store covers
 };
 
-template <int BN>
+// ROLLED: one group of four loads in flight at a time (a persistent kernel
+// calls this inside its tile loop, where the unrolled groups would hold
+// 128 registers at once).
+template <int BN, bool ROLLED = false>
 __device__ __forceinline__ void tc_stage_tile(uint32_t tmem, int q, int lane, float* stage) {
     using T = TileLayout<BN>;
     float4* st = reinterpret_cast<float4*>(stage) + (size_t)q * 32 * T::kSlots;
-#pragma unroll
+#pragma unroll (ROLLED ? 1 : (T::kChunks + 3) / 4)
     for (int g0 = 0; g0 < T::kChunks; g0 += 4) {
         uint32_t r[4][16];
 #pragma unroll
@@ -860,6 +863,252 @@ k_gemm_tc_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
+// ------------------------------------------------ persistent 3xTF32 GEMM
+//
+// Compression-size projections without split K (in_proj, out_proj, head):
+// one CTA per SM walks the 128 x 128 output tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (row-block major, so consecutive tiles share
+// their A rows).  The TMA producer, the converters and the MMA issuer stream
+// K blocks across tile boundaries through one ring of stages; the MMAs
+// accumulate tile j in TMEM accumulator j % 2, and four epilogue warps of
+// their own drain the other accumulator through a dedicated staging buffer
+// meanwhile.  Each tile sees the MMA sequence and epilogue arithmetic of
+// k_gemm_tc_tf32x3 (same K order, same 3xTF32 products, same stores), so
+// the bits are the same as the per-tile kernel's.
+//
+// Warps: 0 TMA, 1 MMA (one elected lane issues), 2-5 converters, 6-9
+// epilogue.  Barriers: full / conv / empty per stage as in the per-tile
+// kernel; acc_full[b] (the MMAs of accumulator b's tile have completed) and
+// acc_empty[b] (the epilogue has read accumulator b).  Waits are bounded:
+// on expiry the CTA records the error, lets the copies and MMAs it issued
+// land (bounded again), releases TMEM and returns.
+struct T3P {
+    static constexpr int BN = 128;
+    static constexpr int kA = kTcBM * kT3BK * 4;                 // 16 KB of FP32 A per stage
+    static constexpr int kB = BN * kT3BK * 4;                    // 16 KB each of B_hi, B_lo
+    static constexpr int kStage = kA + 2 * kB;
+    static constexpr int kStages = 3;
+    static constexpr int kStaging = kTcBM * BN * 4;              // 64 KB: the epilogue's tile
+    static constexpr int kACols = 2 * kT3BK;
+    static constexpr uint32_t kAccCols = BN;                     // two accumulators: columns 0, 128
+    static constexpr uint32_t kACol0 = 2 * kAccCols;             // A stages after them
+    static constexpr uint32_t kTmemCols = 512;
+    static constexpr int kBars = 3 * kStages + 4 + 1;            // full, conv, empty; acc_full[2], acc_empty[2]; mma_done
+    static constexpr size_t kBytes = 1024 + (size_t)kStages * kStage + kStaging + 8 * kBars + 16;
+    static constexpr int kThreads = 320;
+    static_assert(kACol0 + kStages * kACols <= kTmemCols, "accumulators and A stages fit the SM's TMEM");
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(T3P::kThreads, 1)
+k_gemm_t3_persist(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+                  const __grid_constant__ CUtensorMap tmBlo, const float* __restrict__ bias, float* __restrict__ Cm,
+                  int M, int N, int K, int* __restrict__ err) {
+    using L = T3P;
+    constexpr int S = L::kStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    float* staging = reinterpret_cast<float*>(smem + (size_t)S * L::kStage);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * L::kStage + L::kStaging);
+    uint64_t* full = bars;
+    uint64_t* conv = bars + S;
+    uint64_t* empty = bars + 2 * S;
+    uint64_t* acc_full = bars + 3 * S;
+    uint64_t* acc_empty = bars + 3 * S + 2;
+    uint64_t* mma_done = bars + 3 * S + 4;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::kBars);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int tiles_n = (N + L::BN - 1) / L::BN;
+    const int n_tiles = tiles_n * ((M + kTcBM - 1) / kTcBM);
+    const int nk = K / kT3BK;
+
+    if (threadIdx.x == 0) {
+        tma_prefetch_map(&tmA);
+        tma_prefetch_map(&tmBhi);
+        tma_prefetch_map(&tmBlo);
+        abort_flag = 0;
+        for (int i = 0; i < S; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&conv[i], 128);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+        }
+        mbar_init(mma_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(L::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    pdl_launch_next();
+    pdl_wait_prev();
+
+    int issued = 0;                                // producer: K blocks whose loads went out
+    if (threadIdx.x == 0) {
+        // TMA producer
+        int g = 0;
+#pragma unroll 1
+        for (int t = blockIdx.x; t < n_tiles && !*(volatile int*)&abort_flag; t += gridDim.x) {
+            const int m0 = (t / tiles_n) * kTcBM, n0 = (t % tiles_n) * L::BN;
+#pragma unroll 1
+            for (int kb = 0; kb < nk; kb++, g++) {
+                const int s = g % S;
+                if (g >= S && !mbar_wait(&empty[s], (uint32_t)(((g / S) - 1) & 1))) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                uint8_t* st = smem + (size_t)s * L::kStage;
+                mbar_expect_tx(&full[s], L::kStage);
+                tma_load_2d(&tmA, &full[s], st, kb * kT3BK, m0);
+                tma_load_2d(&tmBhi, &full[s], st + L::kA, kb * kT3BK, n0);
+                tma_load_2d(&tmBlo, &full[s], st + L::kA + L::kB, kb * kT3BK, n0);
+                issued = g + 1;
+            }
+        }
+    } else if (warp >= 2 && warp < 6) {
+        // converters: thread (quadrant q, lane) splits row 32 q + lane of
+        // every stage into A_hi / A_lo in its TMEM lane
+        const int q = warp % 4;
+        const int r = 32 * q + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + L::kACol0;
+        int g = 0;
+        bool ok = true;
+#pragma unroll 1
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+#pragma unroll 1
+            for (int kb = 0; kb < nk; kb++, g++) {
+                const int s = g % S;
+                if (!mbar_wait(&full[s], (uint32_t)((g / S) & 1))) {
+                    atomicExch(&abort_flag, 1);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint8_t* row = smem + (size_t)s * L::kStage + (size_t)r * 128;
+#pragma unroll
+                for (int half = 0; half < 2; half++) {
+                    uint32_t hi[16], lo[16];
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        const int ch = 4 * half + c;
+                        const float4 v = *reinterpret_cast<const float4*>(row + ((ch ^ (r & 7)) << 4));
+                        const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const float h = tf32_rna(x[e]);
+                            hi[4 * c + e] = __float_as_uint(h);
+                            lo[4 * c + e] = __float_as_uint(__fsub_rn(x[e], h));
+                        }
+                    }
+                    const uint32_t col = trow + (uint32_t)(s * L::kACols + 16 * half);
+                    tmem_st16(col, hi);
+                    tmem_st16(col + kT3BK, lo);
+                }
+                tmem_wait_st();
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
+            }
+        }
+    }
+    else if (warp == 1) {
+        // MMA issuer: tile j accumulates in accumulator j % 2, after the
+        // epilogue has read that accumulator's previous tile (j - 2)
+        constexpr uint32_t idesc = umma_idesc_tf32(kTcBM, L::BN);
+        const bool leader = elect_one();
+        const uint64_t dh0 = umma_desc_sw128(smem_u32(smem + L::kA));
+        bool ok = true;
+        int g = 0;
+        int j = 0;
+#pragma unroll 1
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, j++) {
+            const int b = j & 1;
+            if (j >= 2) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&acc_empty[b], (uint32_t)(((j >> 1) - 1) & 1)));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            const uint32_t d = tmem + (uint32_t)b * L::kAccCols;
+#pragma unroll 1
+            for (int kb = 0; kb < nk; kb++, g++) {
+                const int s = g % S;
+                ok = __all_sync(0xffffffffu, mbar_wait(&conv[s], (uint32_t)((g / S) & 1)));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t dh = dh0 + (uint64_t)((s * L::kStage) >> 4);
+                const uint64_t dl = dh + (uint64_t)(L::kB >> 4);
+                const uint32_t ahi = tmem + L::kACol0 + (uint32_t)(s * L::kACols);
+                const uint32_t alo = ahi + kT3BK;
+                if (leader) {
+#pragma unroll
+                    for (int k = 0; k < kT3BK / 8; k++) {
+                        umma_tf32_ta(d, ahi + 8 * k, dh + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                        umma_tf32_ta(d, ahi + 8 * k, dl + 2 * k, idesc, 1u);
+                        umma_tf32_ta(d, alo + 8 * k, dh + 2 * k, idesc, 1u);
+                    }
+                    umma_commit(&empty[s]);
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+            if (leader) umma_commit(&acc_full[b]);
+            __syncwarp();
+        }
+        if (leader) {
+            if (!ok) atomicExch(&abort_flag, 1);
+            umma_commit(mma_done);
+        }
+        __syncwarp();
+    } else if (warp >= 6) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of the
+        // accumulator, stages them in its own rows of the staging tile and
+        // stores them; the accumulator is released as soon as it is read
+        const int q = warp % 4;
+        int j = 0;
+#pragma unroll 1
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, j++) {
+            const int b = j & 1;
+            if (!mbar_wait(&acc_full[b], (uint32_t)((j >> 1) & 1))) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_stage_tile<L::BN, true>(tmem + (uint32_t)b * L::kAccCols, q, lane, staging);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+            __syncwarp();
+            tc_store_rows<L::BN, EPI>(32 * q, 32, lane, (t / tiles_n) * kTcBM, (t % tiles_n) * L::BN, M, N, bias,
+                                      Cm, nullptr, staging, 1, nullptr, nullptr);
+            __syncwarp();
+        }
+    }
+
+    const bool finished = mbar_wait(mma_done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((!finished || abort_flag) && threadIdx.x == 0) {
+        atomicExch(err, 1);
+        // let the last loads of every stage land before the CTA leaves
+        for (int g = issued - 1; g >= 0 && g >= issued - S; g--)
+            mbar_wait(&full[g % S], (uint32_t)((g / S) & 1));
+        if (!finished) mbar_wait(mma_done, 0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kTmemCols));
 }
 
 }  // namespace boa

@@ -106,7 +106,7 @@ def test_decode_scan_variants_agree(api, tmp_path, d_model, expand, prec, d_conv
     comp = m.compress(streams)
     for v, lanes in ((0, 1), (0, 3), (1, 2), (2, 1), (3, 4)):
         m.set_tuning(1 << 18, v, lanes)
-        assert m.tuning() == {"max_rows": 1 << 18, "scan_variant": v, "decode_lanes": lanes}
+        assert m.tuning() == {"max_rows": 1 << 18, "scan_variant": v, "decode_lanes": lanes, "decoder": 0}
         assert m.decompress(comp, [len(s) for s in streams]) == streams, (v, lanes)
     with pytest.raises(api.BoaError):
         m.set_tuning(1 << 18, 4)
