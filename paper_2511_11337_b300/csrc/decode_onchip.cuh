@@ -83,8 +83,14 @@ struct OcWork {
     int* err;
 };
 
+// Component q (compile-time after unrolling) of a float4.
+__device__ __forceinline__ float f4_at(const float4& v, int q) {
+    return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+}
+
 // Rows of a K-major matrix with `cols` columns that one stage holds (a
-// multiple of 4).
+// multiple of 4; every matrix has a multiple of 4 rows, so every stage
+// does).
 __host__ __device__ inline int oc_rpc(int rows, int cols) {
     const int r = (kOcStage / 4 / cols) & ~3;
     return r < rows ? r : rows;
@@ -347,16 +353,26 @@ __global__ void __launch_bounds__(kOcBlock, 1) k_decode_onchip(const OcModel M, 
                     for (int p = 0; p < P; p++) acc[p][0] = acc[p][1] = acc[p][2] = acc[p][3] = 0.f;
                     ok = oc_consume(d, cols, gc, full, empty, ring, vabort, lane, [&](const float* st, int k0, int nr) {
                         if (!on) return;
-                        for (int r = 0; r < nr; r++) {
-                            const float4 w = *reinterpret_cast<const float4*>(st + (size_t)r * cols + 4 * tid);
+                        // four rows at a time: each slot's four inputs in one load
+#pragma unroll 2
+                        for (int r = 0; r < nr; r += 4) {
+                            float4 xa[P], w[4];
 #pragma unroll
-                            for (int p = 0; p < P; p++) {
-                                const float a = act[p * APS + d + k0 + r];
-                                acc[p][0] = __fmaf_rn(a, w.x, acc[p][0]);
-                                acc[p][1] = __fmaf_rn(a, w.y, acc[p][1]);
-                                acc[p][2] = __fmaf_rn(a, w.z, acc[p][2]);
-                                acc[p][3] = __fmaf_rn(a, w.w, acc[p][3]);
-                            }
+                            for (int p = 0; p < P; p++)
+                                xa[p] = *reinterpret_cast<const float4*>(act + p * APS + d + k0 + r);
+#pragma unroll
+                            for (int q = 0; q < 4; q++)
+                                w[q] = *reinterpret_cast<const float4*>(st + (size_t)(r + q) * cols + 4 * tid);
+#pragma unroll
+                            for (int q = 0; q < 4; q++)
+#pragma unroll
+                                for (int p = 0; p < P; p++) {
+                                    const float a = f4_at(xa[p], q);
+                                    acc[p][0] = __fmaf_rn(a, w[q].x, acc[p][0]);
+                                    acc[p][1] = __fmaf_rn(a, w[q].y, acc[p][1]);
+                                    acc[p][2] = __fmaf_rn(a, w[q].z, acc[p][2]);
+                                    acc[p][3] = __fmaf_rn(a, w[q].w, acc[p][3]);
+                                }
                         }
                     });
                     if (on)
@@ -419,7 +435,14 @@ __global__ void __launch_bounds__(kOcBlock, 1) k_decode_onchip(const OcModel M, 
                     ok = oc_consume(E, R2, gc, full, empty, ring, vabort, lane, [&](const float* st, int k0, int nr) {
                         if (!on) return;
 #pragma unroll 4
-                        for (int r = 0; r < nr; r++) acc = __fmaf_rn(up[k0 + r], st[(size_t)r * R2 + n], acc);
+                        for (int r = 0; r < nr; r += 4) {
+                            const float4 ua = *reinterpret_cast<const float4*>(up + k0 + r);
+                            float w[4];
+#pragma unroll
+                            for (int q = 0; q < 4; q++) w[q] = st[(size_t)(r + q) * R2 + n];
+#pragma unroll
+                            for (int q = 0; q < 4; q++) acc = __fmaf_rn(f4_at(ua, q), w[q], acc);
+                        }
                     });
                     if (on) act[p * APS + oDBC + n] = acc;
                 }
@@ -498,10 +521,19 @@ __global__ void __launch_bounds__(kOcBlock, 1) k_decode_onchip(const OcModel M, 
                     for (int p = 0; p < P; p++) acc[p] = 0.f;
                     ok = oc_consume(E, d, gc, full, empty, ring, vabort, lane, [&](const float* st, int k0, int nr) {
                         if (!on) return;
-                        for (int r = 0; r < nr; r++) {
-                            const float w = st[(size_t)r * d + tid];
+#pragma unroll 2
+                        for (int r = 0; r < nr; r += 4) {
+                            float4 ya[P];
+                            float w[4];
 #pragma unroll
-                            for (int p = 0; p < P; p++) acc[p] = __fmaf_rn(act[p * APS + oYG + k0 + r], w, acc[p]);
+                            for (int p = 0; p < P; p++)
+                                ya[p] = *reinterpret_cast<const float4*>(act + p * APS + oYG + k0 + r);
+#pragma unroll
+                            for (int q = 0; q < 4; q++) w[q] = st[(size_t)(r + q) * d + tid];
+#pragma unroll
+                            for (int q = 0; q < 4; q++)
+#pragma unroll
+                                for (int p = 0; p < P; p++) acc[p] = __fmaf_rn(f4_at(ya[p], q), w[q], acc[p]);
                         }
                     });
                     if (on)
@@ -536,10 +568,18 @@ __global__ void __launch_bounds__(kOcBlock, 1) k_decode_onchip(const OcModel M, 
 #pragma unroll
                 for (int p = 0; p < P; p++) acc[p] = 0.f;
                 ok = oc_consume(d, 256, gc, full, empty, ring, vabort, lane, [&](const float* st, int k0, int nr) {
-                    for (int r = 0; r < nr; r++) {
-                        const float w = st[(size_t)r * 256 + tid];
+#pragma unroll 2
+                    for (int r = 0; r < nr; r += 4) {
+                        float4 xa[P];
+                        float w[4];
 #pragma unroll
-                        for (int p = 0; p < P; p++) acc[p] = __fmaf_rn(act[p * APS + k0 + r], w, acc[p]);
+                        for (int p = 0; p < P; p++) xa[p] = *reinterpret_cast<const float4*>(act + p * APS + k0 + r);
+#pragma unroll
+                        for (int q = 0; q < 4; q++) w[q] = st[(size_t)(r + q) * 256 + tid];
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+#pragma unroll
+                            for (int p = 0; p < P; p++) acc[p] = __fmaf_rn(f4_at(xa[p], q), w[q], acc[p]);
                     }
                 });
                 const float hb = M.head_b[tid];
