@@ -45,8 +45,14 @@ namespace boa {
 constexpr int kOcSlots = 2;                        // streams per CTA
 constexpr int kOcThreads = 256;                    // compute threads
 constexpr int kOcBlock = kOcThreads + 32;          // + the weight-streaming warp
-constexpr int kOcStage = 32768;                    // bytes per ring stage
-constexpr int kOcStages = 6;
+// Ring: three 64 KB stages.  Each stage costs every compute warp a wait and
+// a release, so fewer, larger stages are cheaper: measured per decode step
+// of 2 x 148 streams, 6 x 32 KB 75.8 us, 3 x 64 KB 64.9 us (sixteen compute
+// warps with one channel each: 83.9 / 72.6 us).  Sharing one weight stream
+// across a cluster by multicast copies was slower still (2 CTAs 102 us,
+// 4 CTAs 118 us): each chunk then waits for every CTA's release.
+constexpr int kOcStage = 65536;                    // bytes per ring stage
+constexpr int kOcStages = 3;
 constexpr int kOcMaxLayers = 3;
 constexpr int kOcNS = 16;                          // d_state
 constexpr int kOcMaxE = 2 * kOcThreads;
