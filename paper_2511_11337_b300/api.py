@@ -79,7 +79,7 @@ class Model:
         bufs = [np.frombuffer(s, np.uint8) if len(s) else np.zeros(1, np.uint8) for s in streams]
         lens = np.array([len(s) for s in streams], np.uintp)
         caps = np.array([max_compressed_size(len(s)) for s in streams], np.uintp)
-        outs = [np.zeros(max(int(c), 1), np.uint8) for c in caps]
+        outs = [np.empty(max(int(c), 1), np.uint8) for c in caps]      # the library writes sizes[i] bytes
         in_ptrs = np.array([b.ctypes.data for b in bufs], np.uintp)
         out_ptrs = np.array([o.ctypes.data for o in outs], np.uintp)
         sizes = np.zeros(n, np.uintp)
@@ -93,7 +93,7 @@ class Model:
         bufs = [np.frombuffer(c, np.uint8) if len(c) else np.zeros(1, np.uint8) for c in comps]
         sizes = np.array([len(c) for c in comps], np.uintp)
         l = np.array(lens, np.uintp)
-        outs = [np.zeros(max(int(x), 1), np.uint8) for x in lens]
+        outs = [np.empty(max(int(x), 1), np.uint8) for x in lens]      # the library writes lens[i] bytes
         in_ptrs = np.array([b.ctypes.data for b in bufs], np.uintp)
         out_ptrs = np.array([o.ctypes.data for o in outs], np.uintp)
         check(load().boa_decompress(self._h, n, _p(in_ptrs), _p(sizes), _p(l), _p(out_ptrs)))
