@@ -106,3 +106,17 @@ def test_refused_where_it_does_not_run(api, tiny_model_path, model_dir):
     with pytest.raises(Exception):
         onchip(mf)
     assert mf.tuning()["decoder"] == 0
+
+
+def test_autotune_weighs_the_onchip_decoder(api, tiny_model_path):
+    """boa_autotune times the on-chip decoder beside the step kernels for an
+    FP32 model (its choice is reported in the tuning) and the model decodes
+    correctly with whichever it keeps; for another form it never picks it."""
+    m = api.Model(tiny_model_path, precision=api.PREC_FP32)
+    t = m.autotune(16, 1024)
+    assert t["decoder"] in (0, 1) and m.tuning()["decoder"] == t["decoder"]
+    streams = [synth.records_stream(300 + i, 1024 + 37 * i) for i in range(16)]
+    comp = m.compress(streams)
+    assert m.decompress(comp, [len(s) for s in streams]) == streams
+    t3 = api.Model(tiny_model_path, precision=api.PREC_TF32X3)
+    assert t3.autotune(16, 1024)["decoder"] == 0
