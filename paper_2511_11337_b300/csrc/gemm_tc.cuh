@@ -1111,4 +1111,187 @@ k_gemm_t3_persist(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kTmemCols));
 }
 
+// ------------------------------------------ persistent BF16 / E4M3 GEMM
+//
+// The compression-size projections of the BF16 and FP8 forms without split
+// K, the same way as k_gemm_t3_persist: one CTA per SM walks the 128 x 128
+// output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; the TMA warp and
+// the MMA warp stream K blocks across tile boundaries through one ring of
+// stages (A and B both by TMA, 128-byte rows: 64 BF16 or 128 E4M3 of K);
+// tile j accumulates in TMEM accumulator j % 2 while four epilogue warps
+// drain the other one through a staging buffer of their own.  Each tile
+// sees the MMA sequence and epilogue arithmetic of k_gemm_tc_bf16 with
+// BN = 128, so the bits are the same.  Warps: 0 TMA, 1 MMA, 2-5 epilogue.
+struct TcP {
+    static constexpr int BN = 128;
+    static constexpr int kA = kTcBM * 128;                       // 16 KB
+    static constexpr int kB = BN * 128;                          // 16 KB
+    static constexpr int kStage = kA + kB;
+    static constexpr int kStages = 4;
+    static constexpr int kStaging = kTcBM * BN * 4;              // 64 KB
+    static constexpr uint32_t kAccCols = BN;
+    static constexpr uint32_t kTmemCols = 2 * kAccCols;
+    static constexpr int kBars = 2 * kStages + 4 + 1;            // full, empty; acc_full[2], acc_empty[2]; mma_done
+    static constexpr size_t kBytes = 1024 + (size_t)kStages * kStage + kStaging + 8 * kBars + 16;
+    static constexpr int kThreads = 192;
+};
+
+template <int EPI, int KIND>
+__global__ void __launch_bounds__(TcP::kThreads, 1)
+k_gemm_tc_persist(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const float* __restrict__ bias, float* __restrict__ Cm, __nv_bfloat16* __restrict__ out_bf16,
+                  int M, int N, int K, int* __restrict__ err, const float* __restrict__ row_scale,
+                  const float* __restrict__ col_scale) {
+    using L = TcP;
+    constexpr int S = L::kStages;
+    constexpr int kElemK = KIND == kKindE4M3 ? 128 : kTcBK;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    float* staging = reinterpret_cast<float*>(smem + (size_t)S * L::kStage);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * L::kStage + L::kStaging);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + S;
+    uint64_t* acc_full = bars + 2 * S;
+    uint64_t* acc_empty = bars + 2 * S + 2;
+    uint64_t* mma_done = bars + 2 * S + 4;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::kBars);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int tiles_n = (N + L::BN - 1) / L::BN;
+    const int n_tiles = tiles_n * ((M + kTcBM - 1) / kTcBM);
+    const int nk = K / kElemK;
+
+    if (threadIdx.x == 0) {
+        tma_prefetch_map(&tmA);
+        tma_prefetch_map(&tmB);
+        abort_flag = 0;
+        for (int i = 0; i < S; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+        }
+        mbar_init(mma_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(L::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    pdl_launch_next();
+    pdl_wait_prev();
+
+    int issued = 0;
+    if (threadIdx.x == 0) {
+        // TMA producer
+        int g = 0;
+#pragma unroll 1
+        for (int t = blockIdx.x; t < n_tiles && !*(volatile int*)&abort_flag; t += gridDim.x) {
+            const int m0 = (t / tiles_n) * kTcBM, n0 = (t % tiles_n) * L::BN;
+#pragma unroll 1
+            for (int kb = 0; kb < nk; kb++, g++) {
+                const int s = g % S;
+                if (g >= S && !mbar_wait(&empty[s], (uint32_t)(((g / S) - 1) & 1))) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                uint8_t* st = smem + (size_t)s * L::kStage;
+                mbar_expect_tx(&full[s], L::kStage);
+                tma_load_2d(&tmA, &full[s], st, kb * kElemK, m0);
+                tma_load_2d(&tmB, &full[s], st + L::kA, kb * kElemK, n0);
+                issued = g + 1;
+            }
+        }
+    } else if (warp == 1) {
+        // MMA issuer: tile j accumulates in accumulator j % 2, after the
+        // epilogue has read that accumulator's previous tile (j - 2)
+        constexpr uint32_t idesc = KIND == kKindE4M3 ? umma_idesc_e4m3(kTcBM, L::BN) : umma_idesc_bf16(kTcBM, L::BN);
+        const bool leader = elect_one();
+        const uint64_t da0 = umma_desc_sw128(smem_u32(smem));
+        const uint64_t db0 = umma_desc_sw128(smem_u32(smem + L::kA));
+        bool ok = true;
+        int g = 0, j = 0;
+#pragma unroll 1
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, j++) {
+            const int b = j & 1;
+            if (j >= 2) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&acc_empty[b], (uint32_t)(((j >> 1) - 1) & 1)));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            const uint32_t d = tmem + (uint32_t)b * L::kAccCols;
+#pragma unroll 1
+            for (int kb = 0; kb < nk; kb++, g++) {
+                const int s = g % S;
+                ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)((g / S) & 1)));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t so = (uint64_t)((s * L::kStage) >> 4);
+                if (leader) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {   // 32 bytes of K per instruction
+                        if (KIND == kKindE4M3)
+                            umma_e4m3(d, da0 + so + 2 * k, db0 + so + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                        else
+                            umma_bf16(d, da0 + so + 2 * k, db0 + so + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                    }
+                    umma_commit(&empty[s]);
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+            if (leader) umma_commit(&acc_full[b]);
+            __syncwarp();
+        }
+        if (leader) {
+            if (!ok) atomicExch(&abort_flag, 1);
+            umma_commit(mma_done);
+        }
+        __syncwarp();
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        const int q = warp % 4;
+        int j = 0;
+#pragma unroll 1
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, j++) {
+            const int b = j & 1;
+            if (!mbar_wait(&acc_full[b], (uint32_t)((j >> 1) & 1))) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_stage_tile<L::BN, true>(tmem + (uint32_t)b * L::kAccCols, q, lane, staging);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+            __syncwarp();
+            tc_store_rows<L::BN, EPI>(32 * q, 32, lane, (t / tiles_n) * kTcBM, (t % tiles_n) * L::BN, M, N, bias,
+                                      Cm, out_bf16, staging, 1, row_scale, col_scale);
+            __syncwarp();
+        }
+    }
+
+    const bool finished = mbar_wait(mma_done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((!finished || abort_flag) && threadIdx.x == 0) {
+        atomicExch(err, 1);
+        for (int g = issued - 1; g >= 0 && g >= issued - S; g--)
+            mbar_wait(&full[g % S], (uint32_t)((g / S) & 1));
+        if (!finished) mbar_wait(mma_done, 0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kTmemCols));
+}
+
 }  // namespace boa
