@@ -120,3 +120,25 @@ def test_autotune_weighs_the_onchip_decoder(api, tiny_model_path):
     assert m.decompress(comp, [len(s) for s in streams]) == streams
     t3 = api.Model(tiny_model_path, precision=api.PREC_TF32X3)
     assert t3.autotune(16, 1024)["decoder"] == 0
+
+
+@pytest.mark.parametrize("d_model,n_layer,d_conv", [(128, 3, 4), (64, 1, 2), (128, 2, 3)])
+def test_other_shapes_and_conv_widths(api, model_dir, d_model, n_layer, d_conv):
+    """The decoder's other shapes: d_model 128 (d_inner 256, dt_rank 8), one
+    block, and conv widths 2 and 3 (a window of one or two values)."""
+    shape = synth.ModelShape(d_model=d_model, n_layer=n_layer, d_conv=d_conv)
+    path = synth.make_model_file(os.path.join(model_dir, f"oc_{d_model}_{n_layer}_{d_conv}.boaw"), shape, seed=11)
+    m = api.Model(path, precision=api.PREC_FP32)
+    streams = [synth.records_stream(500 + i, n) for i, n in enumerate([900, 2, 1, 0, 333, 1500, 64] * 3)]
+    n_steps = sum(max(len(s) - 1, 0) for s in streams)
+    m.enable_cdf_trace(True)
+    try:
+        comp = m.compress(streams)
+        enc = m.read_cdf_trace(n_steps)
+        onchip(m)
+        out = m.decompress(comp, [len(s) for s in streams])
+        dec = m.read_cdf_trace(n_steps)
+    finally:
+        m.enable_cdf_trace(False)
+        hbm(m)
+    assert out == streams and np.array_equal(enc, dec)
